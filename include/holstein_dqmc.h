@@ -1,0 +1,166 @@
+/*
+ * holstein_dqmc.h -- C ABI of the GB300 DQMC fermion-weight engine for the 2D Holstein model.
+ *
+ * Model and method: Li, Dee, Khatami, Johnston, arXiv:1905.07440.
+ *   "Model": H = H0 + H_lat + H_e-ph on an N = nx*ny periodic square lattice, hopping t,
+ *            chemical potential mu, ion mass M, phonon frequency Omega, coupling g X_i n_i.
+ *   "Determinant quantum Monte Carlo": L = beta/dtau imaginary-time slices; the phonon
+ *            field X(i,l) is sampled with weight W(X) = exp(-dtau S_ph) det(M_up) det(M_dn),
+ *            M = I + B_L ... B_1, S_ph = M/(2 dtau^2) sum (X_{i,l+1}-X_{i,l})^2
+ *            + M Omega^2/2 sum X_{i,l}^2; local moves X(i,l) += dX and block moves
+ *            X(i,.) += dX_i are accepted with p = W(X')/W(X).
+ *
+ * Conventions (all FP64):
+ *   B_l = exp(-dtau K) exp(-dtau V_l), K_ij = -t per nearest-neighbour displacement,
+ *   V_l = diag(g X(.,l) - mu).  G_l = (I + B_l..B_1 B_L..B_{l+1})^{-1}, G_ij = <c_i c_j^+>.
+ *   Site index i = x + nx*y.  Fields are laid out X[chain][l][i] (l = 0..L-1 is slice l+1).
+ *   A sweep = local moves at every (l, i) (l ascending, i ascending) with delayed rank-k
+ *   updates of G and a wrap G <- B_l G B_l^{-1} after each slice, restabilisation every
+ *   n_wrap slices (column-pivoted QR, UDV), then one block move per site (i ascending),
+ *   each accepted on the full stabilised determinant ratio.
+ *   Proposals come from Philox4x32-10 (Salmon et al., SC'11): key = seed, counter =
+ *   (event, sweep, chain, tag), event = l*N + i (tag 0, local) or i (tag 1, block);
+ *   u = ((w0>>5)*2^26 + (w1>>6)) 2^-53, dX = dx*(2 u1 - 1); accept iff u2 < p.
+ *
+ * Memory: the caller owns every host buffer; the API copies in and out.  The engine
+ * never allocates device memory: the caller passes one device arena of at least
+ * hq_arena_bytes() bytes (256-byte aligned), which holds all device state, and keeps it
+ * alive until hq_destroy().  Work is issued on the caller's CUDA stream (borrowed); calls
+ * that return data to the host synchronise that stream, other calls do not.
+ *
+ * Errors: functions return HQ_OK (0) or a negative HQ_E* code; hq_last_error() gives a
+ * message.  Nothing is thrown across the ABI.
+ */
+#ifndef HOLSTEIN_DQMC_H
+#define HOLSTEIN_DQMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HQ_OK 0
+#define HQ_EINVAL (-1)     /* bad argument or parameter set */
+#define HQ_ENOMEM (-2)     /* arena too small / misaligned */
+#define HQ_ECUDA (-3)      /* a CUDA runtime call failed */
+#define HQ_EUNSTABLE (-4)  /* wrap error above tolerance (reported, chain kept) */
+#define HQ_ENAN (-5)       /* non-finite G, ratio or log-determinant */
+
+/* hq_sweep flags */
+#define HQ_LOCAL 1u
+#define HQ_GLOBAL 2u
+#define HQ_MEASURE 4u
+
+/* observable ids for hq_get_series */
+#define HQ_OBS_DENSITY 0    /* <n> = (2/N) sum_i (1 - G_ii), averaged over restabilised slices */
+#define HQ_OBS_DOUBLE_OCC 1 /* (1/N) sum_i (1 - G_ii)^2 */
+#define HQ_OBS_SCDW 2       /* S_CDW(pi,pi) = (1/N) sum_ij (-1)^(i+j) <n_i n_j> (Wick) */
+#define HQ_OBS_X_MEAN 3     /* (1/NL) sum X at the end of the sweep */
+#define HQ_OBS_X2 4         /* (1/NL) sum X^2 at the end of the sweep */
+#define HQ_OBS_WRAP_ERR 5   /* max |G_wrapped - G_fresh| over the sweep's restabilisations */
+#define HQ_N_OBS 6
+
+typedef struct hq_params {
+  int nx, ny;       /* lattice sides: even, 2..16 each (N = nx*ny <= 256) */
+  double t;         /* nearest-neighbour hopping */
+  double mu;        /* chemical potential (half filling: -g^2/(M Omega^2)) */
+  double omega;     /* phonon frequency Omega > 0 */
+  double mass;      /* ion mass M > 0 */
+  double g;         /* electron-phonon coupling */
+  double beta;      /* inverse temperature; beta/dtau must be an integer L >= 2 */
+  double dtau;      /* Trotter step > 0 */
+  int n_wrap;       /* restabilise every n_wrap slices, >= 1 */
+  int delay_k;      /* delayed-update rank, 1..32 */
+  double dx_local;  /* local proposal dX ~ U[-dx_local, dx_local) */
+  double dx_global; /* block proposal dX ~ U[-dx_global, dx_global) */
+  uint64_t seed;    /* Philox key */
+} hq_params;
+
+typedef struct hq_obs {   /* per chain, accumulated since hq_create / hq_restore */
+  int64_t sweeps;          /* sweeps run */
+  int64_t measured;        /* sweeps with electronic measurements */
+  int64_t local_proposed, local_accepted;
+  int64_t global_proposed, global_accepted;
+  double density, double_occ, s_cdw;  /* means over measured sweeps */
+  double x_mean, x2;                  /* means over sweeps */
+  double max_wrap_error;              /* max over all restabilisations */
+  double logdet;                      /* log|det M| of the current fields */
+  int32_t status;                     /* 0, or HQ_ENAN if a non-finite value was seen */
+  int32_t pad;
+} hq_obs;
+
+typedef struct hq_engine hq_engine;
+
+/* Bytes of device arena needed for n_chains chains keeping up to max_series per-sweep
+ * records of each observable.  Returns 0 if the parameters are invalid. */
+size_t hq_arena_bytes(const hq_params* p, int n_chains, int max_series);
+
+/* Create an engine for n_chains independent chains (Philox chain ids first_chain ..
+ * first_chain+n_chains-1).  device_arena: device pointer, 256-byte aligned, >= arena_bytes
+ * from hq_arena_bytes(); owned by the caller.  stream: a cudaStream_t (NULL = legacy
+ * default stream), borrowed.  Fields start at zero; call hq_set_fields(). */
+int hq_create(const hq_params* p, int n_chains, int first_chain, int max_series,
+              void* device_arena, size_t arena_bytes, void* stream, hq_engine** out);
+
+/* Copy fields in from the host, X_host[chain][l][i] (n_chains*L*N doubles); G, the UDV
+ * stack and log|det M| are recomputed before the next use.  Resets no counters. */
+int hq_set_fields(hq_engine* e, const double* X_host);
+/* Same from a device buffer of the same layout (copied on the engine's stream). */
+int hq_set_fields_device(hq_engine* e, const double* X_device);
+/* Copy the current fields out to the host (synchronises the stream). */
+int hq_get_fields(hq_engine* e, double* X_host);
+
+/* Run n_sweeps sweeps of every chain.  flags: HQ_LOCAL | HQ_GLOBAL | HQ_MEASURE.
+ * Asynchronous on the engine's stream; returns HQ_EINVAL for bad flags, HQ_ENOMEM if
+ * more than max_series measured sweeps would be recorded. */
+int hq_sweep(hq_engine* e, int n_sweeps, unsigned flags);
+
+/* log W = 2 log|det M| - dtau S_ph and log|det M| of the current fields, one per chain
+ * (host arrays of n_chains doubles; either may be NULL).  Synchronises. */
+int hq_log_weight(hq_engine* e, double* logw_host, double* logdet_host);
+
+/* G_0 = G_L of one chain for the current fields, row-major G[i*N+j] = G_ij = <c_i c_j^+>
+ * (host, N*N doubles); *slice = 0.  Synchronises. */
+int hq_get_green(hq_engine* e, int chain, double* G_host, int* slice);
+
+/* Per-chain accumulated observables (host array of n_chains hq_obs).  Synchronises. */
+int hq_get_observables(hq_engine* e, hq_obs* out);
+
+/* Per-sweep series of one observable: out[chain][s] for s < *n_out (host, n_chains *
+ * max_series doubles).  NaN where the sweep had no electronic measurement. */
+int hq_get_series(hq_engine* e, int obs_id, double* out, int* n_out);
+
+/* Serialise the chain state (fields, sweep counter, counters, accumulators, series).
+ * With buf == NULL only *len is set.  Synchronises. */
+int hq_checkpoint(hq_engine* e, void* buf, size_t* len);
+/* Restore a state written by hq_checkpoint for the same parameters and chain count. */
+int hq_restore(hq_engine* e, const void* buf, size_t len);
+
+/* Number of chains, sites N, slices L and sweeps run. */
+int hq_shape(const hq_engine* e, int* n_chains, int* n_sites, int* n_slices, int64_t* sweeps);
+
+const char* hq_last_error(const hq_engine* e);
+void hq_destroy(hq_engine* e);
+
+/* Proposal stream check: the Philox uniforms (u1, u2) the sampler draws for the given
+ * events of (chain, sweep, tag), computed on the device.  u1_host, u2_host: n doubles.
+ * Synchronises the given stream. */
+int hq_proposal_uniforms(uint64_t seed, uint32_t chain, uint32_t sweep, uint32_t tag,
+                         const uint32_t* events_host, int n, double* u1_host,
+                         double* u2_host, void* stream);
+
+/* Integrated autocorrelation time of a series (host code): tau = 1/2 + sum_{t=1}^{W}
+ * rho(t) with the smallest window W >= c*tau (Madras-Sokal; c = 6 is usual).  Returns
+ * tau, stores W in *window if non-NULL.  n < 2 gives 0.5. */
+double hq_tau_int(const double* series, int n, double c, int* window);
+
+/* FP64 pipe probe: runs a DFMA throughput kernel on the stream for about reps*10 ms and
+ * returns achieved TFLOP/s (<= 0 on error).  Used to state the FP64 roofline. */
+double hq_fp64_peak_tflops(int reps, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HOLSTEIN_DQMC_H */

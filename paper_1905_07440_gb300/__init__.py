@@ -1,0 +1,251 @@
+"""Python binding of the GB300 Holstein DQMC engine (C ABI in include/holstein_dqmc.h).
+
+Argument marshalling only: every step of a sweep runs in the CUDA library
+libholstein_dqmc.so built in this directory (see build.py).  PyTorch provides the
+device arena and the stream; there is no CPU fallback -- importing the binding fails
+loudly when the library has not been built.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libholstein_dqmc.so")
+
+HQ_OK = 0
+HQ_EINVAL = -1
+HQ_ENOMEM = -2
+HQ_ECUDA = -3
+HQ_EUNSTABLE = -4
+HQ_ENAN = -5
+
+HQ_LOCAL = 1
+HQ_GLOBAL = 2
+HQ_MEASURE = 4
+
+HQ_OBS_DENSITY = 0
+HQ_OBS_DOUBLE_OCC = 1
+HQ_OBS_SCDW = 2
+HQ_OBS_X_MEAN = 3
+HQ_OBS_X2 = 4
+HQ_OBS_WRAP_ERR = 5
+HQ_N_OBS = 6
+OBS_NAMES = ("density", "double_occ", "s_cdw", "x_mean", "x2", "wrap_error")
+
+
+class hq_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("t", ctypes.c_double), ("mu", ctypes.c_double),
+                ("omega", ctypes.c_double), ("mass", ctypes.c_double), ("g", ctypes.c_double),
+                ("beta", ctypes.c_double), ("dtau", ctypes.c_double), ("n_wrap", ctypes.c_int),
+                ("delay_k", ctypes.c_int), ("dx_local", ctypes.c_double), ("dx_global", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+class hq_obs(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int64), ("measured", ctypes.c_int64),
+                ("local_proposed", ctypes.c_int64), ("local_accepted", ctypes.c_int64),
+                ("global_proposed", ctypes.c_int64), ("global_accepted", ctypes.c_int64),
+                ("density", ctypes.c_double), ("double_occ", ctypes.c_double), ("s_cdw", ctypes.c_double),
+                ("x_mean", ctypes.c_double), ("x2", ctypes.c_double), ("max_wrap_error", ctypes.c_double),
+                ("logdet", ctypes.c_double), ("status", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+_P = ctypes.POINTER
+_dp = _P(ctypes.c_double)
+_vp = ctypes.c_void_p
+_SIGNATURES = {
+    "hq_arena_bytes": (ctypes.c_size_t, [_P(hq_params), ctypes.c_int, ctypes.c_int]),
+    "hq_create": (ctypes.c_int, [_P(hq_params), ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t,
+                                 _vp, _P(_vp)]),
+    "hq_set_fields": (ctypes.c_int, [_vp, _dp]),
+    "hq_set_fields_device": (ctypes.c_int, [_vp, _vp]),
+    "hq_get_fields": (ctypes.c_int, [_vp, _dp]),
+    "hq_sweep": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_uint]),
+    "hq_log_weight": (ctypes.c_int, [_vp, _dp, _dp]),
+    "hq_get_green": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _P(ctypes.c_int)]),
+    "hq_get_observables": (ctypes.c_int, [_vp, _P(hq_obs)]),
+    "hq_get_series": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _P(ctypes.c_int)]),
+    "hq_checkpoint": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_size_t)]),
+    "hq_restore": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+    "hq_shape": (ctypes.c_int, [_vp, _P(ctypes.c_int), _P(ctypes.c_int), _P(ctypes.c_int), _P(ctypes.c_int64)]),
+    "hq_last_error": (ctypes.c_char_p, [_vp]),
+    "hq_destroy": (None, [_vp]),
+    "hq_proposal_uniforms": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                            _P(ctypes.c_uint32), ctypes.c_int, _dp, _dp, _vp]),
+    "hq_tau_int": (ctypes.c_double, [_dp, ctypes.c_int, ctypes.c_double, _P(ctypes.c_int)]),
+    "hq_fp64_peak_tflops": (ctypes.c_double, [ctypes.c_int, _vp]),
+}
+EXPORTED = tuple(_SIGNATURES)
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libholstein_dqmc.so and declare every exported symbol.  Raises if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_1905_07440_gb300.build.build() "
+                          "(the engine has no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+class HQError(RuntimeError):
+    pass
+
+
+def make_params(p):
+    """hq_params from any object with the workloads.HolsteinParams attributes."""
+    return hq_params(p.nx, p.ny, p.t, p.mu, p.omega, p.mass, p.g, p.beta, p.dtau, p.n_wrap, p.delay_k,
+                     p.dx_local, p.dx_global, p.seed)
+
+
+def arena_bytes(params, n_chains, max_series=0):
+    lib = load_library()
+    return int(lib.hq_arena_bytes(ctypes.byref(make_params(params)), n_chains, max_series))
+
+
+class Engine:
+    """n_chains independent Holstein DQMC chains on one GPU (thin wrapper of hq_*)."""
+
+    def __init__(self, params, n_chains, first_chain=0, max_series=0, device=None, stream=None):
+        import torch
+        self.lib = load_library()
+        self.params = params
+        self.n_chains = int(n_chains)
+        self.max_series = int(max_series)
+        self._p = make_params(params)
+        nbytes = self.lib.hq_arena_bytes(ctypes.byref(self._p), self.n_chains, self.max_series)
+        if nbytes == 0:
+            raise HQError("invalid parameters")
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.arena = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        base = self.arena.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        self._h = ctypes.c_void_p()
+        rc = self.lib.hq_create(ctypes.byref(self._p), self.n_chains, int(first_chain), self.max_series,
+                                ctypes.c_void_p(aligned), nbytes, ctypes.c_void_p(self.stream.cuda_stream),
+                                ctypes.byref(self._h))
+        if rc != HQ_OK:
+            raise HQError(f"hq_create failed ({rc})")
+        n_c, n_s, n_l = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self.lib.hq_shape(self._h, ctypes.byref(n_c), ctypes.byref(n_s), ctypes.byref(n_l), None)
+        self.n_sites, self.n_slices = n_s.value, n_l.value
+
+    def _check(self, rc, what):
+        if rc != HQ_OK:
+            msg = self.lib.hq_last_error(self._h)
+            raise HQError(f"{what} failed ({rc}): {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self.lib.hq_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def field_shape(self):
+        return (self.n_chains, self.n_slices, self.n_sites)
+
+    def set_fields(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        if X.shape != self.field_shape:
+            raise ValueError(f"fields must have shape {self.field_shape}")
+        self._check(self.lib.hq_set_fields(self._h, _dptr(X)), "hq_set_fields")
+
+    def set_fields_device(self, X):
+        """X: contiguous float64 CUDA tensor of field_shape."""
+        assert X.is_cuda and X.dtype.is_floating_point and X.element_size() == 8 and X.is_contiguous()
+        assert tuple(X.shape) == self.field_shape
+        self._check(self.lib.hq_set_fields_device(self._h, ctypes.c_void_p(X.data_ptr())), "hq_set_fields_device")
+
+    def get_fields(self, out=None):
+        out = np.empty(self.field_shape) if out is None else out
+        self._check(self.lib.hq_get_fields(self._h, _dptr(out)), "hq_get_fields")
+        return out
+
+    def sweep(self, n=1, local=True, global_=True, measure=True):
+        flags = (HQ_LOCAL if local else 0) | (HQ_GLOBAL if global_ else 0) | (HQ_MEASURE if measure else 0)
+        self._check(self.lib.hq_sweep(self._h, int(n), flags), "hq_sweep")
+
+    def log_weight(self):
+        lw = np.empty(self.n_chains)
+        ld = np.empty(self.n_chains)
+        self._check(self.lib.hq_log_weight(self._h, _dptr(lw), _dptr(ld)), "hq_log_weight")
+        return lw, ld
+
+    def green(self, chain):
+        G = np.empty((self.n_sites, self.n_sites))
+        sl = ctypes.c_int()
+        self._check(self.lib.hq_get_green(self._h, int(chain), _dptr(G), ctypes.byref(sl)), "hq_get_green")
+        return G
+
+    def observables(self):
+        arr = (hq_obs * self.n_chains)()
+        self._check(self.lib.hq_get_observables(self._h, arr), "hq_get_observables")
+        return [{f: getattr(o, f) for f, _ in hq_obs._fields_ if f != "pad"} for o in arr]
+
+    def series(self, obs_id):
+        out = np.full((self.n_chains, max(self.max_series, 1)), np.nan)
+        n = ctypes.c_int()
+        self._check(self.lib.hq_get_series(self._h, int(obs_id), _dptr(out), ctypes.byref(n)), "hq_get_series")
+        return out[:, :n.value]
+
+    def checkpoint(self):
+        n = ctypes.c_size_t()
+        self._check(self.lib.hq_checkpoint(self._h, None, ctypes.byref(n)), "hq_checkpoint")
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(self.lib.hq_checkpoint(self._h, buf, ctypes.byref(n)), "hq_checkpoint")
+        return buf.raw[: n.value]
+
+    def restore(self, blob):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        self._check(self.lib.hq_restore(self._h, buf, len(blob)), "hq_restore")
+
+    @property
+    def sweeps_done(self):
+        s = ctypes.c_int64()
+        self.lib.hq_shape(self._h, None, None, None, ctypes.byref(s))
+        return s.value
+
+
+def proposal_uniforms(seed, chain, sweep, events, tag, stream=None):
+    lib = load_library()
+    ev = np.ascontiguousarray(events, dtype=np.uint32)
+    u1 = np.empty(ev.size)
+    u2 = np.empty(ev.size)
+    rc = lib.hq_proposal_uniforms(int(seed), int(chain), int(sweep), int(tag), ev.ctypes.data_as(_P(ctypes.c_uint32)),
+                                  ev.size, _dptr(u1), _dptr(u2), ctypes.c_void_p(stream or 0))
+    if rc != HQ_OK:
+        raise HQError(f"hq_proposal_uniforms failed ({rc})")
+    return u1, u2
+
+
+def tau_int(series, c=6.0):
+    lib = load_library()
+    x = np.ascontiguousarray(series, dtype=np.float64)
+    w = ctypes.c_int()
+    t = lib.hq_tau_int(_dptr(x), x.size, float(c), ctypes.byref(w))
+    return float(t), w.value
+
+
+def fp64_peak_tflops(reps=20, stream=None):
+    return float(load_library().hq_fp64_peak_tflops(int(reps), ctypes.c_void_p(stream or 0)))

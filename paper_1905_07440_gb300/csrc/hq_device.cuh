@@ -1,0 +1,493 @@
+// Device building blocks of the Holstein DQMC engine (FP64, one CTA per Markov chain).
+//
+// Every routine is called by all HQ_THREADS threads of a CTA and works on column-major
+// n x n matrices (element (r, c) at c*ld + r) that live in global memory (L1/L2 cached).
+// The FP64 pipe is the bound on GB300 (about 1/74 of the FP32 rate), so the routines
+// aim at keeping DFMAs in flight and at cutting FP64 work (separable kinetic propagator),
+// not at staging: operand traffic per DFMA is far below L1 bandwidth.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define HQ_THREADS 256
+#define HQ_WARPS (HQ_THREADS / 32)
+#define HQ_FULL 0xffffffffu
+
+namespace hq {
+
+struct Lattice {
+  int nx, ny, n;
+  const double* ex;   // exp(-dtau K_x), nx x nx row-major (shared memory)
+  const double* exi;  // exp(+dtau K_x)
+  const double* ey;   // exp(-dtau K_y), ny x ny
+  const double* eyi;  // exp(+dtau K_y)
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(HQ_FULL, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(HQ_FULL, v, o));
+  return v;
+}
+
+// Sum over the CTA in a fixed order (deterministic); every thread gets the result.
+// red: HQ_WARPS doubles of shared memory.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int w = 0; w < HQ_WARPS; ++w) s += red[w];
+  return s;
+}
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+  v = warp_max(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = red[0];
+#pragma unroll
+  for (int w = 1; w < HQ_WARPS; ++w) s = fmax(s, red[w]);
+  return s;
+}
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw (SC'11): ten rounds of two 32x32->64 multiplies with the
+// round constants, key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ void philox4x32_10(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
+                                              uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+}
+
+// 53-bit uniform in [0,1) from the 27 high bits of a and the 26 high bits of b.
+__device__ __forceinline__ double uniform53(uint32_t a, uint32_t b) {
+  return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+__device__ __forceinline__ void proposal_uniforms(uint32_t key0, uint32_t key1, uint32_t event,
+                                                  uint32_t sweep, uint32_t chain, uint32_t tag,
+                                                  double& u1, double& u2) {
+  uint32_t c0 = event, c1 = sweep, c2 = chain, c3 = tag;
+  philox4x32_10(c0, c1, c2, c3, key0, key1);
+  u1 = uniform53(c0, c1);
+  u2 = uniform53(c2, c3);
+}
+
+// ------------------------------------------------------- separable kinetic propagator
+// exp(-dtau K) = E_x (x) E_y exactly, because K = K_x (x) 1 + 1 (x) K_y and the two terms
+// commute on the periodic lattice.  Applying it to an n x n matrix costs 2 n^2 (nx + ny)
+// flops instead of 2 n^3 for the dense product.
+
+// P <- (E_x (x) E_y) P  (acts on the row = site index of every column).
+template <int LMAX>
+__device__ void kin_rows(double* P, int ld, int ncols, const double* ex, const double* ey, int nx, int ny) {
+  for (int line = threadIdx.x; line < ny * ncols; line += HQ_THREADS) {
+    const int y = line % ny, j = line / ny;
+    double* base = P + (size_t)j * ld + nx * y;
+    double v[LMAX];
+#pragma unroll
+    for (int b = 0; b < LMAX; ++b) v[b] = (b < nx) ? base[b] : 0.0;
+#pragma unroll
+    for (int a = 0; a < LMAX; ++a) {
+      if (a < nx) {
+        double acc = 0.0;
+#pragma unroll
+        for (int b = 0; b < LMAX; ++b)
+          if (b < nx) acc = fma(ex[a * nx + b], v[b], acc);
+        base[a] = acc;
+      }
+    }
+  }
+  __syncthreads();
+  for (int line = threadIdx.x; line < nx * ncols; line += HQ_THREADS) {
+    const int x = line % nx, j = line / nx;
+    double* base = P + (size_t)j * ld + x;
+    double v[LMAX];
+#pragma unroll
+    for (int b = 0; b < LMAX; ++b) v[b] = (b < ny) ? base[b * nx] : 0.0;
+#pragma unroll
+    for (int a = 0; a < LMAX; ++a) {
+      if (a < ny) {
+        double acc = 0.0;
+#pragma unroll
+        for (int b = 0; b < LMAX; ++b)
+          if (b < ny) acc = fma(ey[a * ny + b], v[b], acc);
+        base[a * nx] = acc;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// P <- P (F_x (x) F_y)  (acts on the column index of every row); F given row-major.
+template <int LMAX>
+__device__ void kin_cols(double* P, int ld, int nrows, const double* fx, const double* fy, int nx, int ny) {
+  for (int line = threadIdx.x; line < nrows * ny; line += HQ_THREADS) {
+    const int r = line % nrows, y = line / nrows;
+    double* base = P + (size_t)(nx * y) * ld + r;
+    double v[LMAX];
+#pragma unroll
+    for (int b = 0; b < LMAX; ++b) v[b] = (b < nx) ? base[(size_t)b * ld] : 0.0;
+#pragma unroll
+    for (int a = 0; a < LMAX; ++a) {
+      if (a < nx) {
+        double acc = 0.0;
+#pragma unroll
+        for (int b = 0; b < LMAX; ++b)
+          if (b < nx) acc = fma(v[b], fx[b * nx + a], acc);
+        base[(size_t)a * ld] = acc;
+      }
+    }
+  }
+  __syncthreads();
+  for (int line = threadIdx.x; line < nrows * nx; line += HQ_THREADS) {
+    const int r = line % nrows, x = line / nrows;
+    double* base = P + (size_t)x * ld + r;
+    const size_t step = (size_t)nx * ld;
+    double v[LMAX];
+#pragma unroll
+    for (int b = 0; b < LMAX; ++b) v[b] = (b < ny) ? base[b * step] : 0.0;
+#pragma unroll
+    for (int a = 0; a < LMAX; ++a) {
+      if (a < ny) {
+        double acc = 0.0;
+#pragma unroll
+        for (int b = 0; b < LMAX; ++b)
+          if (b < ny) acc = fma(v[b], fy[b * ny + a], acc);
+        base[a * step] = acc;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// ----------------------------------------------------------------- small helpers
+
+__device__ __forceinline__ void set_identity(double* A, int ld, int n) {
+  for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+    const int r = idx % n, c = idx / n;
+    A[(size_t)c * ld + r] = (r == c) ? 1.0 : 0.0;
+  }
+}
+
+// A <- diag(d) A  (row scaling)
+__device__ __forceinline__ void scale_rows(double* A, int ld, int n, const double* d) {
+  for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+    const int r = idx % n, c = idx / n;
+    A[(size_t)c * ld + r] *= d[r];
+  }
+}
+
+// B <- A diag(d)  (column scaling into another buffer)
+__device__ __forceinline__ void copy_scale_cols(double* B, const double* A, int ld, int n, const double* d) {
+  for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+    const int r = idx % n, c = idx / n;
+    B[(size_t)c * ld + r] = A[(size_t)c * ld + r] * d[c];
+  }
+}
+
+__device__ __forceinline__ void copy_mat(double* B, const double* A, int ld, int n) {
+  for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+    const int r = idx % n, c = idx / n;
+    B[(size_t)c * ld + r] = A[(size_t)c * ld + r];
+  }
+}
+
+// ----------------------------------------------------- column-pivoted Householder QR
+// Scratch (shared memory): tau[n], vn1[n], vn2[n], vs[n], perm[n] (int), sint[>=1] (int).
+struct QrScratch {
+  double* tau;
+  double* vn1;
+  double* vn2;
+  double* vs;
+  int* perm;
+  int* sint;
+};
+
+// In place: on exit R is in the upper triangle of P, the Householder vectors (unit
+// leading entry implied) below it, tau[j] the reflector scalars and perm[j] the original
+// index of the column moved to position j.  Column norms are downdated after every step
+// and recomputed when cancellation makes the downdate unreliable (as in LAPACK xLAQP2).
+__device__ void qr_pivoted(double* P, int ld, int n, const QrScratch& s) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double tol3z = 1.4901161193847656e-08;  // sqrt(DBL_EPSILON)
+  for (int c = tid; c < n; c += HQ_THREADS) s.perm[c] = c;
+  for (int c = warp; c < n; c += HQ_WARPS) {
+    const double* col = P + (size_t)c * ld;
+    double a = 0.0;
+    for (int r = lane; r < n; r += 32) a = fma(col[r], col[r], a);
+    a = warp_sum(a);
+    if (lane == 0) {
+      s.vn1[c] = sqrt(a);
+      s.vn2[c] = s.vn1[c];
+    }
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (warp == 0) {
+      double best = -1.0;
+      int bi = j;
+      for (int c = j + lane; c < n; c += 32) {
+        const double v = s.vn1[c];
+        if (v > best) { best = v; bi = c; }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const double ob = __shfl_xor_sync(HQ_FULL, best, o);
+        const int oi = __shfl_xor_sync(HQ_FULL, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) s.sint[0] = bi;
+    }
+    __syncthreads();
+    const int p = s.sint[0];
+    if (p != j) {
+      double* cj = P + (size_t)j * ld;
+      double* cp = P + (size_t)p * ld;
+      for (int r = tid; r < n; r += HQ_THREADS) {
+        const double a = cj[r];
+        cj[r] = cp[r];
+        cp[r] = a;
+      }
+      if (tid == 0) {
+        double a = s.vn1[j]; s.vn1[j] = s.vn1[p]; s.vn1[p] = a;
+        a = s.vn2[j]; s.vn2[j] = s.vn2[p]; s.vn2[p] = a;
+        const int q = s.perm[j]; s.perm[j] = s.perm[p]; s.perm[p] = q;
+      }
+      __syncthreads();
+    }
+    double* cj = P + (size_t)j * ld;
+    if (warp == 0) {
+      double a = 0.0;
+      for (int r = j + 1 + lane; r < n; r += 32) a = fma(cj[r], cj[r], a);
+      a = warp_sum(a);
+      const double alpha = cj[j];
+      double tj = 0.0, beta = alpha, scal = 0.0;
+      if (a != 0.0) {
+        const double nrm = sqrt(fma(alpha, alpha, a));
+        beta = (alpha >= 0.0) ? -nrm : nrm;
+        tj = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+      }
+      for (int r = j + 1 + lane; r < n; r += 32) {
+        const double v = cj[r] * scal;
+        cj[r] = v;
+        s.vs[r] = v;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        cj[j] = beta;
+        s.vs[j] = 1.0;
+        s.tau[j] = tj;
+      }
+    }
+    __syncthreads();
+    const double tj = s.tau[j];
+    for (int c = j + 1 + warp; c < n; c += HQ_WARPS) {
+      double* cc = P + (size_t)c * ld;
+      if (tj != 0.0) {
+        double w = 0.0;
+        for (int r = j + lane; r < n; r += 32) w = fma(s.vs[r], cc[r], w);
+        w = warp_sum(w) * tj;
+        for (int r = j + lane; r < n; r += 32) cc[r] = fma(-w, s.vs[r], cc[r]);
+        __syncwarp();
+      }
+      const double nj = s.vn1[c];
+      const double n2 = s.vn2[c];
+      const double rj = cc[j];
+      __syncwarp();
+      if (nj != 0.0) {
+        const double q = fabs(rj) / nj;
+        const double temp = fmax(0.0, (1.0 - q) * (1.0 + q));
+        const double ratio = nj / n2;
+        const double temp2 = temp * ratio * ratio;
+        if (temp2 <= tol3z) {
+          double a = 0.0;
+          for (int r = j + 1 + lane; r < n; r += 32) a = fma(cc[r], cc[r], a);
+          a = warp_sum(a);
+          if (lane == 0) {
+            s.vn1[c] = sqrt(a);
+            s.vn2[c] = s.vn1[c];
+          }
+        } else if (lane == 0) {
+          s.vn1[c] = nj * sqrt(temp);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// U <- Q = H_0 H_1 ... H_{n-1} (explicit), from the reflectors stored in P and tau.
+__device__ void form_q(const double* P, int ld, int n, double* U, const QrScratch& s) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  set_identity(U, ld, n);
+  __syncthreads();
+  for (int j = n - 1; j >= 0; --j) {
+    const double tj = s.tau[j];
+    if (tj == 0.0) continue;  // uniform across the CTA
+    for (int r = j + tid; r < n; r += HQ_THREADS) s.vs[r] = (r == j) ? 1.0 : P[(size_t)j * ld + r];
+    __syncthreads();
+    for (int c = j + warp; c < n; c += HQ_WARPS) {
+      double* uc = U + (size_t)c * ld;
+      double w = 0.0;
+      for (int r = j + lane; r < n; r += 32) w = fma(s.vs[r], uc[r], w);
+      w = warp_sum(w) * tj;
+      for (int r = j + lane; r < n; r += 32) uc[r] = fma(-w, s.vs[r], uc[r]);
+    }
+    __syncthreads();
+  }
+}
+
+// D[j] = |R_jj| and Tout = T' Tprev with T'(j, perm[c]) = R(j, c) / D[j] for c >= j
+// (T' = D^-1 R Pi^T).  With Tprev == nullptr, Tout = T'.
+__device__ void t_update(const double* P, int ld, int n, const QrScratch& s, double* D,
+                         const double* Tprev, double* Tout) {
+  for (int j = threadIdx.x; j < n; j += HQ_THREADS) D[j] = fabs(P[(size_t)j * ld + j]);
+  __syncthreads();
+  if (Tprev == nullptr) {
+    for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+      const int j = idx % n, c = idx / n;
+      Tout[(size_t)s.perm[c] * ld + j] = (c >= j) ? P[(size_t)c * ld + j] / D[j] : 0.0;
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+      const int j = idx % n, col = idx / n;
+      const double* tc = Tprev + (size_t)col * ld;
+      double acc = 0.0;
+      for (int c = j; c < n; ++c) acc = fma(P[(size_t)c * ld + j], tc[s.perm[c]], acc);
+      Tout[(size_t)col * ld + j] = acc / D[j];
+    }
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------- LU and triangular solves
+// In-place LU with partial (row) pivoting.  piv[j] = row swapped with j at step j.
+// Returns sum_j log|U_jj| (same value in every thread).
+__device__ double lu_logdet(double* A, int ld, int n, int* piv, int* sint, double* red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int j = 0; j < n; ++j) {
+    double* aj = A + (size_t)j * ld;
+    if (warp == 0) {
+      double best = -1.0;
+      int bi = j;
+      for (int r = j + lane; r < n; r += 32) {
+        const double v = fabs(aj[r]);
+        if (v > best) { best = v; bi = r; }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const double ob = __shfl_xor_sync(HQ_FULL, best, o);
+        const int oi = __shfl_xor_sync(HQ_FULL, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) {
+        sint[0] = bi;
+        piv[j] = bi;
+      }
+    }
+    __syncthreads();
+    const int p = sint[0];
+    if (p != j) {
+      for (int c = tid; c < n; c += HQ_THREADS) {
+        double* ac = A + (size_t)c * ld;
+        const double a = ac[j];
+        ac[j] = ac[p];
+        ac[p] = a;
+      }
+      __syncthreads();
+    }
+    const double pv = aj[j];
+    for (int r = j + 1 + tid; r < n; r += HQ_THREADS) aj[r] = aj[r] / pv;
+    __syncthreads();
+    const int m = n - j - 1;
+    for (int idx = tid; idx < m * m; idx += HQ_THREADS) {
+      const int r = j + 1 + idx % m, c = j + 1 + idx / m;
+      A[(size_t)c * ld + r] = fma(-aj[r], A[(size_t)c * ld + j], A[(size_t)c * ld + r]);
+    }
+    __syncthreads();
+  }
+  double a = 0.0;
+  for (int j = tid; j < n; j += HQ_THREADS) a += log(fabs(A[(size_t)j * ld + j]));
+  return block_sum(a, red);
+}
+
+// Y <- A^-1 Y for the LU factors from lu_logdet (n right-hand sides, one warp per column).
+__device__ void lu_solve(const double* A, int ld, int n, const int* piv, double* Y) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = warp; c < n; c += HQ_WARPS) {
+    double* y = Y + (size_t)c * ld;
+    if (lane == 0) {
+      for (int j = 0; j < n; ++j) {
+        const int p = piv[j];
+        if (p != j) { const double a = y[j]; y[j] = y[p]; y[p] = a; }
+      }
+    }
+    __syncwarp();
+    for (int j = 0; j < n; ++j) {
+      const double yj = y[j];
+      const double* lj = A + (size_t)j * ld;
+      for (int r = j + 1 + lane; r < n; r += 32) y[r] = fma(-lj[r], yj, y[r]);
+      __syncwarp();
+    }
+    for (int j = n - 1; j >= 0; --j) {
+      const double* uj = A + (size_t)j * ld;
+      const double yj = y[j] / uj[j];
+      __syncwarp();
+      if (lane == 0) y[j] = yj;
+      for (int r = lane; r < j; r += 32) y[r] = fma(-uj[r], yj, y[r]);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------- CTA GEMM
+// C = op(A) op(B) for n x n column-major operands (n a multiple of 4: n = nx*ny with
+// even sides); each thread accumulates 4x4 tiles.
+template <bool TA, bool TB>
+__device__ void gemm_nn(int n, const double* A, const double* B, double* C, int ld) {
+  const int tiles = n >> 2;
+  for (int t = threadIdx.x; t < tiles * tiles; t += HQ_THREADS) {
+    const int r0 = (t % tiles) * 4, c0 = (t / tiles) * 4;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int k = 0; k < n; ++k) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = TA ? A[(size_t)(r0 + a) * ld + k] : A[(size_t)k * ld + r0 + a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = TB ? B[(size_t)k * ld + c0 + b] : B[(size_t)(c0 + b) * ld + k];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) C[(size_t)(c0 + b) * ld + r0 + a] = acc[a][b];
+  }
+  __syncthreads();
+}
+
+}  // namespace hq

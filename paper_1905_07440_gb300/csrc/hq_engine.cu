@@ -1,0 +1,512 @@
+// Host side of the C ABI (include/holstein_dqmc.h): parameter validation, arena layout,
+// kinetic propagators, the sweep schedule, copies in and out, checkpoints, tau_int.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hq_internal.h"
+#include "../../include/holstein_dqmc.h"
+
+struct hq_engine {
+  hq_params p;
+  hq::Dev d;
+  cudaStream_t stream;
+  char* arena;
+  size_t arena_bytes;
+  double* tmp;          // [C] device scratch inside the arena
+  int series_len;       // per-sweep records kept so far (<= max_series)
+  long long sweeps;     // sweeps run (Philox sweep counter)
+  bool stack_valid;     // left stack, G_0 and log|det M| match the fields
+  bool logdet_valid;    // log|det M| matches the fields
+  bool green_valid;     // G holds G_0 of the fields
+  std::string err;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+struct Layout {
+  size_t kin, X, G, logdet, UR, TR, DR, work, stU, stT, stD, Adl, Bdl, acc, tot, series, counters, status, tmp;
+  size_t total;
+};
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+int n_slices(const hq_params& p) { return (int)std::llround(p.beta / p.dtau); }
+
+const char* validate(const hq_params* p, int n_chains, int max_series) {
+  if (!p) return "params is NULL";
+  if (p->nx < 2 || p->ny < 2 || p->nx > hq::kMaxSide || p->ny > hq::kMaxSide) return "nx, ny must be in 2..16";
+  if ((p->nx & 1) || (p->ny & 1)) return "nx and ny must be even (bipartite lattice)";
+  if (!(p->dtau > 0.0) || !(p->beta > 0.0)) return "beta and dtau must be positive";
+  const double Lf = p->beta / p->dtau;
+  const long long L = std::llround(Lf);
+  if (std::fabs(Lf - (double)L) > 1e-9 * std::fmax(1.0, Lf)) return "beta/dtau must be an integer";
+  if (L < 2 || L > 100000) return "L = beta/dtau must be in 2..100000";
+  if (p->n_wrap < 1) return "n_wrap must be >= 1";
+  if (p->delay_k < 1 || p->delay_k > hq::kMaxK) return "delay_k must be in 1..32";
+  if (!(p->mass > 0.0) || !(p->omega > 0.0)) return "mass and omega must be positive";
+  if (!std::isfinite(p->t) || !std::isfinite(p->mu) || !std::isfinite(p->g)) return "t, mu, g must be finite";
+  if (!(p->dx_local >= 0.0) || !(p->dx_global >= 0.0)) return "proposal widths must be >= 0";
+  if (n_chains < 1) return "n_chains must be >= 1";
+  if (max_series < 0) return "max_series must be >= 0";
+  return nullptr;
+}
+
+Layout layout(const hq_params& p, int C, int max_series) {
+  Layout l{};
+  const size_t n = (size_t)p.nx * p.ny, L = (size_t)n_slices(p), nn = n * n;
+  const size_t nb = (L - 1) / (size_t)p.n_wrap;
+  const size_t k = (size_t)p.delay_k;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes); return o; };
+  l.kin = take(sizeof(double) * (2 * p.nx * p.nx + 2 * p.ny * p.ny));
+  l.X = take(sizeof(double) * C * L * n);
+  l.G = take(sizeof(double) * C * nn);
+  l.logdet = take(sizeof(double) * C);
+  l.UR = take(sizeof(double) * C * nn);
+  l.TR = take(sizeof(double) * C * nn);
+  l.DR = take(sizeof(double) * C * n);
+  l.work = take(sizeof(double) * C * hq::kWorkMats * nn);
+  l.stU = take(sizeof(double) * C * nb * nn);
+  l.stT = take(sizeof(double) * C * nb * nn);
+  l.stD = take(sizeof(double) * C * nb * n);
+  l.Adl = take(sizeof(double) * C * k * n);
+  l.Bdl = take(sizeof(double) * C * k * n);
+  l.acc = take(sizeof(double) * C * hq::kAccSlots);
+  l.tot = take(sizeof(double) * C * hq::kTotSlots);
+  l.series = take(sizeof(double) * C * HQ_N_OBS * (size_t)(max_series > 0 ? max_series : 1));
+  l.counters = take(sizeof(long long) * C * hq::kCounters);
+  l.status = take(sizeof(int) * C);
+  l.tmp = take(sizeof(double) * C);
+  l.total = off;
+  return l;
+}
+
+// exp(-sgn dtau K_ring) for a ring of m sites with K_ab = -t per displacement +-1:
+// eigenvalues -2t cos(2 pi q/m) on plane waves, so
+// E_ab = (1/m) sum_q cos(2 pi q (a-b)/m) exp(sgn 2 t dtau cos(2 pi q/m)).
+void ring_propagator(int m, double t, double dtau, double sgn, double* E) {
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < m; ++b) {
+      double s = 0.0;
+      for (int q = 0; q < m; ++q)
+        s += std::cos(two_pi * q * (a - b) / m) * std::exp(sgn * 2.0 * t * dtau * std::cos(two_pi * q / m));
+      E[a * m + b] = s / m;
+    }
+}
+
+int set_err(hq_engine* e, int code, const std::string& msg) {
+  if (e) e->err = msg;
+  return code;
+}
+
+int cuda_check(hq_engine* e, cudaError_t st, const char* what) {
+  if (st == cudaSuccess) return HQ_OK;
+  return set_err(e, HQ_ECUDA, std::string(what) + ": " + cudaGetErrorString(st));
+}
+
+int ensure_state(hq_engine* e) {
+  if (e->stack_valid) return HQ_OK;
+  int rc = cuda_check(e, hq::launch_stack_build(e->d, e->stream), "stack_build launch");
+  if (rc) return rc;
+  e->stack_valid = e->logdet_valid = e->green_valid = true;
+  return HQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t hq_arena_bytes(const hq_params* p, int n_chains, int max_series) {
+  if (validate(p, n_chains, max_series)) return 0;
+  return layout(*p, n_chains, max_series).total;
+}
+
+int hq_create(const hq_params* p, int n_chains, int first_chain, int max_series, void* device_arena,
+              size_t arena_bytes, void* stream, hq_engine** out) {
+  if (!out) return HQ_EINVAL;
+  *out = nullptr;
+  if (const char* why = validate(p, n_chains, max_series)) {
+    std::fprintf(stderr, "hq_create: %s\n", why);
+    return HQ_EINVAL;
+  }
+  if (first_chain < 0) return HQ_EINVAL;
+  const Layout l = layout(*p, n_chains, max_series);
+  if (!device_arena || arena_bytes < l.total || ((uintptr_t)device_arena % kAlign) != 0) return HQ_ENOMEM;
+  hq_engine* e = new (std::nothrow) hq_engine();
+  if (!e) return HQ_ENOMEM;
+  e->p = *p;
+  e->stream = (cudaStream_t)stream;
+  e->arena = (char*)device_arena;
+  e->arena_bytes = arena_bytes;
+  hq::Dev& d = e->d;
+  d.nx = p->nx;
+  d.ny = p->ny;
+  d.n = p->nx * p->ny;
+  d.L = n_slices(*p);
+  d.n_wrap = p->n_wrap;
+  d.k = p->delay_k;
+  d.n_chains = n_chains;
+  d.first_chain = first_chain;
+  d.n_bound = (d.L - 1) / d.n_wrap;
+  d.max_series = max_series;
+  d.t = p->t;
+  d.mu = p->mu;
+  d.omega = p->omega;
+  d.mass = p->mass;
+  d.g = p->g;
+  d.dtau = p->dtau;
+  d.dx_local = p->dx_local;
+  d.dx_global = p->dx_global;
+  d.key0 = (uint32_t)(p->seed & 0xffffffffu);
+  d.key1 = (uint32_t)(p->seed >> 32);
+  char* a = e->arena;
+  d.kin = (const double*)(a + l.kin);
+  d.X = (double*)(a + l.X);
+  d.G = (double*)(a + l.G);
+  d.logdet = (double*)(a + l.logdet);
+  d.UR = (double*)(a + l.UR);
+  d.TR = (double*)(a + l.TR);
+  d.DR = (double*)(a + l.DR);
+  d.work = (double*)(a + l.work);
+  d.stU = (double*)(a + l.stU);
+  d.stT = (double*)(a + l.stT);
+  d.stD = (double*)(a + l.stD);
+  d.Adl = (double*)(a + l.Adl);
+  d.Bdl = (double*)(a + l.Bdl);
+  d.acc = (double*)(a + l.acc);
+  d.tot = (double*)(a + l.tot);
+  d.series = (double*)(a + l.series);
+  d.counters = (long long*)(a + l.counters);
+  d.status = (int*)(a + l.status);
+  e->tmp = (double*)(a + l.tmp);
+
+  // kinetic propagators: exp(-dtau K) = E_x (x) E_y with ring factors
+  std::vector<double> kin(2 * d.nx * d.nx + 2 * d.ny * d.ny);
+  double* kx = kin.data();
+  ring_propagator(d.nx, p->t, p->dtau, +1.0, kx);                              // exp(-dtau K_x)
+  ring_propagator(d.nx, p->t, p->dtau, -1.0, kx + d.nx * d.nx);                // exp(+dtau K_x)
+  ring_propagator(d.ny, p->t, p->dtau, +1.0, kx + 2 * d.nx * d.nx);            // exp(-dtau K_y)
+  ring_propagator(d.ny, p->t, p->dtau, -1.0, kx + 2 * d.nx * d.nx + d.ny * d.ny);
+  int rc = HQ_OK;
+  rc = rc ? rc : cuda_check(e, cudaMemsetAsync(a, 0, l.total, e->stream), "arena clear");
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync((void*)d.kin, kin.data(), kin.size() * sizeof(double),
+                                               cudaMemcpyHostToDevice, e->stream), "kinetic upload");
+  rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "create sync");
+  if (rc) {
+    std::fprintf(stderr, "hq_create: %s\n", e->err.c_str());
+    delete e;
+    return rc;
+  }
+  e->series_len = 0;
+  e->sweeps = 0;
+  e->stack_valid = e->logdet_valid = e->green_valid = false;
+  *out = e;
+  return HQ_OK;
+}
+
+void hq_destroy(hq_engine* e) { delete e; }
+
+const char* hq_last_error(const hq_engine* e) { return e ? e->err.c_str() : "engine is NULL"; }
+
+int hq_shape(const hq_engine* e, int* n_chains, int* n_sites, int* n_slices_out, int64_t* sweeps) {
+  if (!e) return HQ_EINVAL;
+  if (n_chains) *n_chains = e->d.n_chains;
+  if (n_sites) *n_sites = e->d.n;
+  if (n_slices_out) *n_slices_out = e->d.L;
+  if (sweeps) *sweeps = e->sweeps;
+  return HQ_OK;
+}
+
+static size_t field_bytes(const hq_engine* e) { return sizeof(double) * (size_t)e->d.n_chains * e->d.L * e->d.n; }
+
+int hq_set_fields(hq_engine* e, const double* X_host) {
+  if (!e || !X_host) return HQ_EINVAL;
+  int rc = cuda_check(e, cudaMemcpyAsync(e->d.X, X_host, field_bytes(e), cudaMemcpyHostToDevice, e->stream),
+                      "set_fields copy");
+  e->stack_valid = e->logdet_valid = e->green_valid = false;
+  return rc;
+}
+
+int hq_set_fields_device(hq_engine* e, const double* X_device) {
+  if (!e || !X_device) return HQ_EINVAL;
+  int rc = cuda_check(e, cudaMemcpyAsync(e->d.X, X_device, field_bytes(e), cudaMemcpyDeviceToDevice, e->stream),
+                      "set_fields_device copy");
+  e->stack_valid = e->logdet_valid = e->green_valid = false;
+  return rc;
+}
+
+int hq_get_fields(hq_engine* e, double* X_host) {
+  if (!e || !X_host) return HQ_EINVAL;
+  int rc = cuda_check(e, cudaMemcpyAsync(X_host, e->d.X, field_bytes(e), cudaMemcpyDeviceToHost, e->stream),
+                      "get_fields copy");
+  return rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "get_fields sync");
+}
+
+int hq_sweep(hq_engine* e, int n_sweeps, unsigned flags) {
+  if (!e || n_sweeps < 0 || (flags & ~(HQ_LOCAL | HQ_GLOBAL | HQ_MEASURE))) return HQ_EINVAL;
+  const bool do_local = flags & HQ_LOCAL, do_global = flags & HQ_GLOBAL, meas = flags & HQ_MEASURE;
+  const hq::Dev& d = e->d;
+  for (int it = 0; it < n_sweeps; ++it) {
+    const uint32_t sw = (uint32_t)e->sweeps;
+    int rc = HQ_OK;
+    if (do_local || !e->logdet_valid) rc = ensure_state(e);
+    if (rc) return rc;
+    if (do_local) {
+      for (int s0 = 0; s0 < d.L; s0 += d.n_wrap) {
+        const int s1 = s0 + d.n_wrap < d.L ? s0 + d.n_wrap : d.L;
+        rc = cuda_check(e, hq::launch_local_chunk(d, s0, s1, sw, meas ? 1 : 0, e->stream), "local_chunk launch");
+        if (rc) return rc;
+      }
+      e->stack_valid = false;  // fields changed; G_0 and log|det M| are fresh (restabilised at l = L)
+      e->logdet_valid = e->green_valid = true;
+    }
+    if (do_global) {
+      for (int i = 0; i < d.n; ++i) {
+        rc = cuda_check(e, hq::launch_global_move(d, i, sw, e->stream), "global_move launch");
+        if (rc) return rc;
+      }
+      e->stack_valid = false;
+      e->green_valid = false;  // log|det M| is kept current by the accepted moves
+    }
+    const int slot = e->series_len < d.max_series ? e->series_len : -1;
+    rc = cuda_check(e, hq::launch_sweep_end(d, slot, (meas && do_local) ? 1 : 0, e->stream), "sweep_end launch");
+    if (rc) return rc;
+    if (slot >= 0) e->series_len++;
+    e->sweeps++;
+  }
+  return HQ_OK;
+}
+
+int hq_log_weight(hq_engine* e, double* logw_host, double* logdet_host) {
+  if (!e) return HQ_EINVAL;
+  int rc = e->logdet_valid ? HQ_OK : ensure_state(e);
+  if (rc) return rc;
+  const size_t C = (size_t)e->d.n_chains;
+  rc = cuda_check(e, hq::launch_log_weight(e->d, e->tmp, e->stream), "log_weight launch");
+  if (!rc && logw_host)
+    rc = cuda_check(e, cudaMemcpyAsync(logw_host, e->tmp, C * sizeof(double), cudaMemcpyDeviceToHost, e->stream),
+                    "log_weight copy");
+  if (!rc && logdet_host)
+    rc = cuda_check(e, cudaMemcpyAsync(logdet_host, e->d.logdet, C * sizeof(double), cudaMemcpyDeviceToHost,
+                                       e->stream), "logdet copy");
+  return rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "log_weight sync");
+}
+
+int hq_get_green(hq_engine* e, int chain, double* G_host, int* slice) {
+  if (!e || !G_host || chain < 0 || chain >= e->d.n_chains) return HQ_EINVAL;
+  int rc = HQ_OK;
+  if (!e->green_valid) {
+    e->stack_valid = false;
+    rc = ensure_state(e);
+    if (rc) return rc;
+  }
+  const size_t n = (size_t)e->d.n;
+  std::vector<double> cm(n * n);
+  rc = cuda_check(e, cudaMemcpyAsync(cm.data(), e->d.G + (size_t)chain * n * n, n * n * sizeof(double),
+                                     cudaMemcpyDeviceToHost, e->stream), "get_green copy");
+  rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "get_green sync");
+  if (rc) return rc;
+  for (size_t i = 0; i < n; ++i)
+    for (size_t j = 0; j < n; ++j) G_host[i * n + j] = cm[j * n + i];
+  if (slice) *slice = 0;
+  return HQ_OK;
+}
+
+int hq_get_observables(hq_engine* e, hq_obs* out) {
+  if (!e || !out) return HQ_EINVAL;
+  const size_t C = (size_t)e->d.n_chains;
+  std::vector<double> tot(C * hq::kTotSlots), ld(C);
+  std::vector<long long> cnt(C * hq::kCounters);
+  std::vector<int> st(C);
+  int rc = e->logdet_valid ? HQ_OK : ensure_state(e);
+  if (rc) return rc;
+  rc = cuda_check(e, cudaMemcpyAsync(tot.data(), e->d.tot, tot.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                     e->stream), "obs copy");
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(cnt.data(), e->d.counters, cnt.size() * sizeof(long long),
+                                               cudaMemcpyDeviceToHost, e->stream), "counter copy");
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(st.data(), e->d.status, st.size() * sizeof(int),
+                                               cudaMemcpyDeviceToHost, e->stream), "status copy");
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(ld.data(), e->d.logdet, ld.size() * sizeof(double),
+                                               cudaMemcpyDeviceToHost, e->stream), "logdet copy");
+  rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "obs sync");
+  if (rc) return rc;
+  for (size_t c = 0; c < C; ++c) {
+    const double* t = tot.data() + c * hq::kTotSlots;
+    const long long* k = cnt.data() + c * hq::kCounters;
+    hq_obs o{};
+    o.sweeps = (int64_t)t[hq::TOT_SWEEPS];
+    o.measured = (int64_t)t[hq::TOT_MEASURED];
+    o.local_proposed = k[0];
+    o.local_accepted = k[1];
+    o.global_proposed = k[2];
+    o.global_accepted = k[3];
+    const double nm = t[hq::TOT_MEASURED], ns = t[hq::TOT_SWEEPS];
+    o.density = nm > 0 ? t[hq::TOT_DENSITY] / nm : NAN;
+    o.double_occ = nm > 0 ? t[hq::TOT_DOCC] / nm : NAN;
+    o.s_cdw = nm > 0 ? t[hq::TOT_SCDW] / nm : NAN;
+    o.x_mean = ns > 0 ? t[hq::TOT_XMEAN] / ns : NAN;
+    o.x2 = ns > 0 ? t[hq::TOT_X2] / ns : NAN;
+    o.max_wrap_error = t[hq::TOT_WRAP];
+    o.logdet = ld[c];
+    o.status = st[c];
+    out[c] = o;
+  }
+  return HQ_OK;
+}
+
+int hq_get_series(hq_engine* e, int obs_id, double* out, int* n_out) {
+  if (!e || !out || obs_id < 0 || obs_id >= HQ_N_OBS) return HQ_EINVAL;
+  const size_t C = (size_t)e->d.n_chains, M = (size_t)e->d.max_series;
+  if (n_out) *n_out = e->series_len;
+  if (M == 0) return HQ_OK;
+  std::vector<double> all(C * HQ_N_OBS * M);
+  int rc = cuda_check(e, cudaMemcpyAsync(all.data(), e->d.series, all.size() * sizeof(double),
+                                         cudaMemcpyDeviceToHost, e->stream), "series copy");
+  rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "series sync");
+  if (rc) return rc;
+  for (size_t c = 0; c < C; ++c)
+    for (int s = 0; s < e->series_len; ++s) out[c * M + s] = all[(c * HQ_N_OBS + obs_id) * M + s];
+  return HQ_OK;
+}
+
+// checkpoint: header, then X, counters, totals, series (host byte order).
+struct CkHeader {
+  char magic[8];
+  int32_t version, n_chains, first_chain, max_series, series_len, pad;
+  long long sweeps;
+  hq_params params;
+};
+
+static size_t ck_len(const hq_engine* e) {
+  const size_t C = (size_t)e->d.n_chains;
+  return sizeof(CkHeader) + field_bytes(e) + C * hq::kCounters * sizeof(long long) +
+         C * hq::kTotSlots * sizeof(double) + C * HQ_N_OBS * (size_t)e->d.max_series * sizeof(double);
+}
+
+int hq_checkpoint(hq_engine* e, void* buf, size_t* len) {
+  if (!e || !len) return HQ_EINVAL;
+  const size_t need = ck_len(e);
+  if (!buf) {
+    *len = need;
+    return HQ_OK;
+  }
+  if (*len < need) return set_err(e, HQ_EINVAL, "checkpoint buffer too small");
+  *len = need;
+  const size_t C = (size_t)e->d.n_chains;
+  CkHeader h{};
+  std::memcpy(h.magic, "HQCKPT1", 8);
+  h.version = 1;
+  h.n_chains = e->d.n_chains;
+  h.first_chain = e->d.first_chain;
+  h.max_series = e->d.max_series;
+  h.series_len = e->series_len;
+  h.sweeps = e->sweeps;
+  h.params = e->p;
+  char* o = (char*)buf;
+  std::memcpy(o, &h, sizeof h);
+  o += sizeof h;
+  int rc = cuda_check(e, cudaMemcpyAsync(o, e->d.X, field_bytes(e), cudaMemcpyDeviceToHost, e->stream), "ck X");
+  o += field_bytes(e);
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(o, e->d.counters, C * hq::kCounters * sizeof(long long),
+                                               cudaMemcpyDeviceToHost, e->stream), "ck counters");
+  o += C * hq::kCounters * sizeof(long long);
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(o, e->d.tot, C * hq::kTotSlots * sizeof(double),
+                                               cudaMemcpyDeviceToHost, e->stream), "ck totals");
+  o += C * hq::kTotSlots * sizeof(double);
+  if (e->d.max_series > 0)
+    rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(o, e->d.series, C * HQ_N_OBS * (size_t)e->d.max_series * sizeof(double),
+                                                 cudaMemcpyDeviceToHost, e->stream), "ck series");
+  return rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "checkpoint sync");
+}
+
+int hq_restore(hq_engine* e, const void* buf, size_t len) {
+  if (!e || !buf || len < sizeof(CkHeader)) return HQ_EINVAL;
+  CkHeader h;
+  std::memcpy(&h, buf, sizeof h);
+  if (std::memcmp(h.magic, "HQCKPT1", 8) != 0 || h.version != 1) return set_err(e, HQ_EINVAL, "not a checkpoint");
+  if (h.n_chains != e->d.n_chains || h.max_series != e->d.max_series ||
+      std::memcmp(&h.params, &e->p, sizeof(hq_params)) != 0)
+    return set_err(e, HQ_EINVAL, "checkpoint is for another parameter set or chain count");
+  if (len < ck_len(e)) return set_err(e, HQ_EINVAL, "checkpoint truncated");
+  const size_t C = (size_t)e->d.n_chains;
+  const char* o = (const char*)buf + sizeof h;
+  int rc = cuda_check(e, cudaMemcpyAsync(e->d.X, o, field_bytes(e), cudaMemcpyHostToDevice, e->stream), "rs X");
+  o += field_bytes(e);
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(e->d.counters, o, C * hq::kCounters * sizeof(long long),
+                                               cudaMemcpyHostToDevice, e->stream), "rs counters");
+  o += C * hq::kCounters * sizeof(long long);
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(e->d.tot, o, C * hq::kTotSlots * sizeof(double),
+                                               cudaMemcpyHostToDevice, e->stream), "rs totals");
+  o += C * hq::kTotSlots * sizeof(double);
+  if (e->d.max_series > 0)
+    rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(e->d.series, o, C * HQ_N_OBS * (size_t)e->d.max_series * sizeof(double),
+                                                 cudaMemcpyHostToDevice, e->stream), "rs series");
+  rc = rc ? rc : cuda_check(e, hq::launch_reset_acc(e->d, e->stream), "rs acc");
+  rc = rc ? rc : cuda_check(e, cudaMemsetAsync(e->d.status, 0, C * sizeof(int), e->stream), "rs status");
+  rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "restore sync");
+  if (rc) return rc;
+  e->sweeps = h.sweeps;
+  e->series_len = h.series_len;
+  e->stack_valid = e->logdet_valid = e->green_valid = false;
+  return HQ_OK;
+}
+
+int hq_proposal_uniforms(uint64_t seed, uint32_t chain, uint32_t sweep, uint32_t tag, const uint32_t* events_host,
+                         int n, double* u1_host, double* u2_host, void* stream) {
+  if (n < 0 || (n > 0 && (!events_host || !u1_host || !u2_host))) return HQ_EINVAL;
+  if (n == 0) return HQ_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* buf = nullptr;
+  const size_t bytes = align_up(n * sizeof(uint32_t)) + 2 * align_up(n * sizeof(double));
+  if (cudaMallocAsync((void**)&buf, bytes, s) != cudaSuccess) return HQ_ECUDA;
+  uint32_t* ev = (uint32_t*)buf;
+  double* u1 = (double*)(buf + align_up(n * sizeof(uint32_t)));
+  double* u2 = u1 + align_up(n * sizeof(double)) / sizeof(double);
+  cudaError_t st = cudaMemcpyAsync(ev, events_host, n * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+  if (st == cudaSuccess)
+    st = hq::launch_proposals((uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), chain, sweep, tag, ev, n, u1,
+                              u2, s);
+  if (st == cudaSuccess) st = cudaMemcpyAsync(u1_host, u1, n * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (st == cudaSuccess) st = cudaMemcpyAsync(u2_host, u2, n * sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(buf, s);
+  if (st == cudaSuccess) st = cudaStreamSynchronize(s);
+  return st == cudaSuccess ? HQ_OK : HQ_ECUDA;
+}
+
+double hq_tau_int(const double* x, int n, double c, int* window) {
+  if (window) *window = 0;
+  if (!x || n < 2) return 0.5;
+  double mean = 0.0;
+  for (int i = 0; i < n; ++i) mean += x[i];
+  mean /= n;
+  double c0 = 0.0;
+  for (int i = 0; i < n; ++i) c0 += (x[i] - mean) * (x[i] - mean);
+  c0 /= n;
+  if (c0 == 0.0) return 0.5;
+  double tau = 0.5;
+  for (int W = 1; W < n; ++W) {
+    double cw = 0.0;
+    for (int i = 0; i + W < n; ++i) cw += (x[i] - mean) * (x[i + W] - mean);
+    tau += cw / n / c0;
+    if (W >= c * tau) {
+      if (window) *window = W;
+      return tau;
+    }
+  }
+  if (window) *window = n - 1;
+  return tau;
+}
+
+double hq_fp64_peak_tflops(int reps, void* stream) {
+  if (reps < 1) reps = 1;
+  return hq::fp64_probe_tflops(reps, (cudaStream_t)stream);
+}
+
+}  // extern "C"

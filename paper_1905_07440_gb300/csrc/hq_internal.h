@@ -1,0 +1,64 @@
+// Internal interface between the C-ABI host code and the kernels (not exported).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hq {
+
+constexpr int kMaxSide = 16;
+constexpr int kMaxN = 256;
+constexpr int kMaxK = 32;
+constexpr int kWorkMats = 7;   // per-chain N x N work matrices
+constexpr int kAccSlots = 8;   // per-chain per-sweep accumulators
+constexpr int kTotSlots = 16;  // per-chain running totals
+constexpr int kCounters = 4;   // local proposed / accepted, global proposed / accepted
+
+// accumulator slots (per sweep)
+enum { ACC_DENSITY = 0, ACC_DOCC = 1, ACC_SCDW = 2, ACC_COUNT = 3, ACC_WRAP = 4 };
+// running-total slots
+enum { TOT_DENSITY = 0, TOT_DOCC = 1, TOT_SCDW = 2, TOT_MEASURED = 3, TOT_XMEAN = 4, TOT_X2 = 5,
+       TOT_SWEEPS = 6, TOT_WRAP = 7 };
+// work matrix slots
+enum { WK_P = 0, WK_U = 1, WK_T = 2, WK_T2 = 3, WK_M1 = 4, WK_M2 = 5, WK_M3 = 6 };
+
+struct Dev {
+  // model and run shape
+  int nx, ny, n, L, n_wrap, k, n_chains, first_chain, n_bound, max_series;
+  double t, mu, omega, mass, g, dtau, dx_local, dx_global;
+  uint32_t key0, key1;
+  // device buffers (bases over all chains)
+  const double* kin;  // ex[nx*nx], exi[nx*nx], ey[ny*ny], eyi[ny*ny]
+  double* X;          // [C][L][N]
+  double* G;          // [C][N*N] column-major
+  double* logdet;     // [C]
+  double* UR;         // [C][N*N] right UDV (product B_l..B_1)
+  double* TR;         // [C][N*N]
+  double* DR;         // [C][N]
+  double* work;       // [C][kWorkMats][N*N]
+  double* stU;        // [C][n_bound][N*N] left stack (transposed product B_L..B_{b+1})
+  double* stT;        // [C][n_bound][N*N]
+  double* stD;        // [C][n_bound][N]
+  double* Adl;        // [C][k][N] delayed-update columns
+  double* Bdl;        // [C][k][N] delayed-update rows
+  double* acc;        // [C][kAccSlots]
+  double* tot;        // [C][kTotSlots]
+  double* series;     // [C][HQ_N_OBS][max_series]
+  long long* counters;  // [C][kCounters]
+  int* status;        // [C]
+};
+
+size_t smem_bytes(const Dev& d);
+
+// Launchers (asynchronous on the stream).  Return cudaGetLastError().
+cudaError_t launch_stack_build(const Dev& d, cudaStream_t s);
+cudaError_t launch_local_chunk(const Dev& d, int s0, int s1, uint32_t sweep, int measure, cudaStream_t s);
+cudaError_t launch_global_move(const Dev& d, int site, uint32_t sweep, cudaStream_t s);
+cudaError_t launch_sweep_end(const Dev& d, int series_slot, int measured, cudaStream_t s);
+cudaError_t launch_reset_acc(const Dev& d, cudaStream_t s);
+cudaError_t launch_log_weight(const Dev& d, double* out_logw, cudaStream_t s);
+cudaError_t launch_proposals(uint32_t key0, uint32_t key1, uint32_t chain, uint32_t sweep, uint32_t tag,
+                             const uint32_t* events, int n, double* u1, double* u2, cudaStream_t s);
+double fp64_probe_tflops(int reps, cudaStream_t s);
+
+}  // namespace hq

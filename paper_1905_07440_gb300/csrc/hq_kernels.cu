@@ -1,0 +1,634 @@
+// Kernels of the Holstein DQMC engine: one CTA per Markov chain, FP64 throughout.
+//
+//   stack_build   fields -> left UDV stack of B_L..B_{b+1} at every restabilisation
+//                 boundary b, fresh G_0 and log|det M|           (DQMC section: M = I + B_L..B_1)
+//   local_chunk   n_wrap slices of local Metropolis moves with delayed rank-k updates of
+//                 G and the wrap G <- B_l G B_l^-1, then the right UDV update and a fresh
+//                 G_l from the right factors and the left stack  (local updates at each
+//                 spacetime point, fast update of the paper's ref. WhitePRB1989)
+//   global_move   one block move X(i, .) += dX per chain with the full stabilised
+//                 determinant ratio                              (block updates)
+//   sweep_end     per-sweep observable records
+#include <cstdio>
+#include "hq_device.cuh"
+#include "hq_internal.h"
+#include "../../include/holstein_dqmc.h"
+
+namespace hq {
+
+struct Smem {
+  double *ex, *exi, *ey, *eyi;
+  double *dl, *u2, *xn, *dlt, *es, *dcorr, *tau, *vn1, *vn2, *vs, *dv;
+  double *red, *scal;
+  int *perm, *piv, *sint;
+};
+
+static constexpr int kSmemVecs = 11;
+
+__host__ __device__ inline size_t smem_layout_bytes(int nx, int ny, int n) {
+  return (size_t)(2 * nx * nx + 2 * ny * ny + kSmemVecs * n + 32 + 16) * sizeof(double) +
+         (size_t)(2 * n + 8) * sizeof(int);
+}
+
+size_t smem_bytes(const Dev& d) { return smem_layout_bytes(d.nx, d.ny, d.n); }
+
+__device__ inline Smem carve(const Dev& d, double* base) {
+  Smem s;
+  double* p = base;
+  const int n = d.n;
+  s.ex = p; p += d.nx * d.nx;
+  s.exi = p; p += d.nx * d.nx;
+  s.ey = p; p += d.ny * d.ny;
+  s.eyi = p; p += d.ny * d.ny;
+  s.dl = p; p += n;
+  s.u2 = p; p += n;
+  s.xn = p; p += n;
+  s.dlt = p; p += n;
+  s.es = p; p += n;
+  s.dcorr = p; p += n;
+  s.tau = p; p += n;
+  s.vn1 = p; p += n;
+  s.vn2 = p; p += n;
+  s.vs = p; p += n;
+  s.dv = p; p += n;
+  s.red = p; p += 32;
+  s.scal = p; p += 16;
+  int* q = reinterpret_cast<int*>(p);
+  s.perm = q; q += n;
+  s.piv = q; q += n;
+  s.sint = q;
+  return s;
+}
+
+__device__ inline void load_kinetic(const Dev& d, const Smem& s) {
+  const int a = d.nx * d.nx, b = d.ny * d.ny;
+  for (int i = threadIdx.x; i < 2 * a + 2 * b; i += HQ_THREADS) s.ex[i] = d.kin[i];  // contiguous
+  __syncthreads();
+}
+
+__device__ inline double* chain_work(const Dev& d, int c, int slot) {
+  return d.work + ((size_t)c * kWorkMats + slot) * (size_t)d.n * d.n;
+}
+
+__device__ inline void flag_nonfinite(const Dev& d, int c, double v) {
+  if (!isfinite(v)) d.status[c] = HQ_ENAN;
+}
+
+// UDV factors of the transposed top-down product (B_L .. B_1)^T = B_1^T .. B_L^T, built
+// by left-multiplying B_s^T = exp(-dtau V_s) exp(-dtau K) for s = L-1 .. 0 and refactoring
+// by pivoted QR after every chunk that ends on a restabilisation boundary.  The field at
+// `site` (if >= 0) is shifted by dx in every slice (block-move proposal).  With `store`
+// the factors at each boundary b > 0 go to the left stack.  Returns log|det M|; with
+// G0 != nullptr also writes G_0 = (I + B_L..B_1)^-1.
+template <int LMAX>
+__device__ double udv_top_down(const Dev& d, int c, const Smem& sm, const double* X, int site, double dx,
+                               bool store, double* G0) {
+  const int n = d.n, L = d.L, nw = d.n_wrap;
+  double* P = chain_work(d, c, WK_P);
+  double* U = chain_work(d, c, WK_U);
+  double* Tc = chain_work(d, c, WK_T);
+  double* Tn = chain_work(d, c, WK_T2);
+  const QrScratch qs{sm.tau, sm.vn1, sm.vn2, sm.vs, sm.perm, sm.sint};
+  int hi = L, lo = ((L - 1) / nw) * nw;
+  bool first = true;
+  while (true) {
+    if (first) set_identity(P, n, n);
+    else copy_scale_cols(P, U, n, n, sm.dv);
+    __syncthreads();
+    for (int s = hi - 1; s >= lo; --s) {
+      for (int r = threadIdx.x; r < n; r += HQ_THREADS) {
+        double x = X[(size_t)s * n + r];
+        if (r == site) x = x + dx;
+        sm.dl[r] = exp(-d.dtau * (d.g * x - d.mu));
+      }
+      kin_rows<LMAX>(P, n, n, sm.ex, sm.ey, d.nx, d.ny);
+      scale_rows(P, n, n, sm.dl);
+      __syncthreads();
+    }
+    qr_pivoted(P, n, n, qs);
+    form_q(P, n, n, U, qs);
+    t_update(P, n, n, qs, sm.dv, first ? nullptr : Tc, Tn);
+    double* t = Tc; Tc = Tn; Tn = t;
+    if (store && lo > 0) {
+      const size_t b = (size_t)c * d.n_bound + (lo / nw - 1);
+      copy_mat(d.stU + b * n * n, U, n, n);
+      copy_mat(d.stT + b * n * n, Tc, n, n);
+      for (int r = threadIdx.x; r < n; r += HQ_THREADS) d.stD[b * n + r] = sm.dv[r];
+      __syncthreads();
+    }
+    first = false;
+    if (lo == 0) break;
+    hi = lo;
+    lo -= nw;
+  }
+  // I + U D T = U Db (Db^-1 U^T + Ds T):  log|det| = sum log Db + log|det A|
+  double* A = chain_work(d, c, WK_M1);
+  double* Y = chain_work(d, c, WK_M2);
+  for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+    const int i = idx % n, col = idx / n;
+    const double D = sm.dv[i];
+    const double db = fmax(D, 1.0), ds = fmin(D, 1.0);
+    const double ut = U[(size_t)i * n + col] / db;
+    A[(size_t)col * n + i] = ut + ds * Tc[(size_t)col * n + i];
+    if (G0) Y[(size_t)col * n + i] = ut;
+  }
+  double lsum = 0.0;
+  for (int i = threadIdx.x; i < n; i += HQ_THREADS) lsum += log(fmax(sm.dv[i], 1.0));
+  const double lb = block_sum(lsum, sm.red);
+  const double la = lu_logdet(A, n, n, sm.piv, sm.sint, sm.red);
+  if (G0) {
+    lu_solve(A, n, n, sm.piv, Y);
+    // Y = (I + (B_L..B_1)^T)^-1, so G_0 = Y^T
+    for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+      const int r = idx % n, col = idx / n;
+      G0[(size_t)col * n + r] = Y[(size_t)r * n + col];
+    }
+    __syncthreads();
+  }
+  return lb + la;
+}
+
+template <int LMAX>
+__global__ void __launch_bounds__(HQ_THREADS) stack_build_kernel(Dev d) {
+  extern __shared__ double smraw[];
+  const int c = blockIdx.x;
+  const Smem sm = carve(d, smraw);
+  load_kinetic(d, sm);
+  const double* X = d.X + (size_t)c * d.L * d.n;
+  double* G = d.G + (size_t)c * d.n * d.n;
+  const double ld = udv_top_down<LMAX>(d, c, sm, X, -1, 0.0, true, G);
+  if (threadIdx.x == 0) {
+    d.logdet[c] = ld;
+    flag_nonfinite(d, c, ld);
+  }
+}
+
+// Fresh G_l at boundary l from the right factors (B_l..B_1 = UR DR TR) and, if l < L,
+// the left stack ((B_L..B_{l+1})^T = UL DL TL):
+//   G_l = UL DLb^-1 [DRb^-1 UR^T UL DLb^-1 + DRs TR TL^T DLs]^-1 DRb^-1 UR^T.
+// Returns log|det M|; G_l goes to Gf.
+__device__ double green_two_sided(const Dev& d, int c, const Smem& sm, int l, double* Gf) {
+  const int n = d.n;
+  const double* UR = d.UR + (size_t)c * n * n;
+  const double* TR = d.TR + (size_t)c * n * n;
+  const double* DR = d.DR + (size_t)c * n;
+  double* M1 = chain_work(d, c, WK_M1);
+  double* M2 = chain_work(d, c, WK_M2);
+  double* M3 = chain_work(d, c, WK_M3);
+  double lsum = 0.0;
+  double la;
+  if (l < d.L) {
+    const size_t b = (size_t)c * d.n_bound + (l / d.n_wrap - 1);
+    const double* UL = d.stU + b * n * n;
+    const double* TL = d.stT + b * n * n;
+    const double* DL = d.stD + b * n;
+    gemm_nn<true, false>(n, UR, UL, M1, n);   // UR^T UL
+    gemm_nn<false, true>(n, TR, TL, M2, n);   // TR TL^T
+    for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+      const int i = idx % n, j = idx / n;
+      const double drb = fmax(DR[i], 1.0), drs = fmin(DR[i], 1.0);
+      const double dlb = fmax(DL[j], 1.0), dls = fmin(DL[j], 1.0);
+      const size_t o = (size_t)j * n + i;
+      M2[o] = M1[o] / (drb * dlb) + drs * M2[o] * dls;
+      M3[o] = UR[(size_t)i * n + j] / drb;
+    }
+    for (int i = threadIdx.x; i < n; i += HQ_THREADS) lsum += log(fmax(DR[i], 1.0)) + log(fmax(DL[i], 1.0));
+    __syncthreads();
+    la = lu_logdet(M2, n, n, sm.piv, sm.sint, sm.red);
+    lu_solve(M2, n, n, sm.piv, M3);
+    // M1 <- UL DLb^-1, Gf = M1 M3
+    for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+      const int j = idx / n;
+      M1[idx] = UL[idx] / fmax(DL[j], 1.0);
+    }
+    __syncthreads();
+    gemm_nn<false, false>(n, M1, M3, Gf, n);
+  } else {
+    for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+      const int i = idx % n, j = idx / n;
+      const double drb = fmax(DR[i], 1.0), drs = fmin(DR[i], 1.0);
+      const double ut = UR[(size_t)i * n + j] / drb;
+      M2[(size_t)j * n + i] = ut + drs * TR[(size_t)j * n + i];
+      Gf[(size_t)j * n + i] = ut;
+    }
+    for (int i = threadIdx.x; i < n; i += HQ_THREADS) lsum += log(fmax(DR[i], 1.0));
+    __syncthreads();
+    la = lu_logdet(M2, n, n, sm.piv, sm.sint, sm.red);
+    lu_solve(M2, n, n, sm.piv, Gf);
+  }
+  return block_sum(lsum, sm.red) + la;
+}
+
+// Electronic observables from a fresh G (Wick; both spins share G), added to the chain's
+// per-sweep accumulators.
+__device__ void measure_green(const Dev& d, int c, const Smem& sm, const double* G) {
+  const int n = d.n;
+  double sm_m = 0.0, sm_m2 = 0.0, sm_sm = 0.0, sm_g = 0.0, conn = 0.0;
+  for (int r = threadIdx.x; r < n; r += HQ_THREADS) {
+    const double g = G[(size_t)r * n + r];
+    const double m = 1.0 - g;
+    const double sg = (((r % d.nx) + (r / d.nx)) & 1) ? -1.0 : 1.0;
+    sm_m += m;
+    sm_m2 += m * m;
+    sm_sm += sg * m;
+    sm_g += g;
+  }
+  for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+    const int r = idx % n, col = idx / n;
+    const double sr = (((r % d.nx) + (r / d.nx)) & 1) ? -1.0 : 1.0;
+    const double sc = (((col % d.nx) + (col / d.nx)) & 1) ? -1.0 : 1.0;
+    conn += sr * sc * G[(size_t)col * n + r] * G[(size_t)r * n + col];
+  }
+  sm_m = block_sum(sm_m, sm.red);
+  sm_m2 = block_sum(sm_m2, sm.red);
+  sm_sm = block_sum(sm_sm, sm.red);
+  sm_g = block_sum(sm_g, sm.red);
+  conn = block_sum(conn, sm.red);
+  if (threadIdx.x == 0) {
+    double* acc = d.acc + (size_t)c * kAccSlots;
+    acc[ACC_DENSITY] += 2.0 * sm_m / n;
+    acc[ACC_DOCC] += sm_m2 / n;
+    acc[ACC_SCDW] += (4.0 * sm_sm * sm_sm + 2.0 * sm_g - 2.0 * conn) / n;
+    acc[ACC_COUNT] += 1.0;
+  }
+}
+
+template <int LMAX>
+__global__ void __launch_bounds__(HQ_THREADS)
+local_chunk_kernel(Dev d, int s0, int s1, uint32_t sweep, int measure) {
+  extern __shared__ double smraw[];
+  const int c = blockIdx.x;
+  const int n = d.n, L = d.L, k = d.k;
+  const Smem sm = carve(d, smraw);
+  load_kinetic(d, sm);
+  double* X = d.X + (size_t)c * L * n;
+  double* G = d.G + (size_t)c * n * n;
+  double* A = d.Adl + (size_t)c * k * n;
+  double* B = d.Bdl + (size_t)c * k * n;
+  const uint32_t chain = (uint32_t)(d.first_chain + c);
+  long long n_acc = 0;
+
+  for (int s = s0; s < s1; ++s) {
+    // Every proposal of this slice depends only on its own site's field and on the
+    // neighbouring slices, so the random numbers, dX, delta = exp(-dtau g dX) - 1 and
+    // exp(-dtau dS_ph) are prepared in parallel; only the ratio needs the running G.
+    for (int i = threadIdx.x; i < n; i += HQ_THREADS) {
+      double u1, u2;
+      proposal_uniforms(d.key0, d.key1, (uint32_t)(s * n + i), sweep, chain, 0u, u1, u2);
+      const double dx = d.dx_local * (2.0 * u1 - 1.0);
+      const double xo = X[(size_t)s * n + i];
+      const double xnew = xo + dx;
+      const double xp = X[(size_t)((s + 1) % L) * n + i];
+      const double xm = X[(size_t)((s - 1 + L) % L) * n + i];
+      const double kin = (xp - xnew) * (xp - xnew) + (xnew - xm) * (xnew - xm) - (xp - xo) * (xp - xo) -
+                         (xo - xm) * (xo - xm);
+      const double pot = xnew * xnew - xo * xo;
+      const double dS = d.mass / (2.0 * d.dtau) * kin + 0.5 * d.dtau * d.mass * (d.omega * d.omega) * pot;
+      sm.u2[i] = u2;
+      sm.xn[i] = xnew;
+      sm.dlt[i] = exp(-d.dtau * d.g * dx) - 1.0;
+      sm.es[i] = exp(-dS);
+      sm.dcorr[i] = 0.0;
+    }
+    __syncthreads();
+    int kk = 0;
+    for (int i = 0; i < n; ++i) {
+      const int slot = i & 1;
+      if (threadIdx.x == 0) {
+        // ratio of one spin: R1 = 1 + delta (1 - G_ii), G_ii including pending updates
+        const double gii = G[(size_t)i * n + i] + sm.dcorr[i];
+        const double delta = sm.dlt[i];
+        const double R1 = 1.0 + delta * (1.0 - gii);
+        const double prob = R1 * R1 * sm.es[i];
+        const int accept = sm.u2[i] < prob;
+        sm.sint[2 + slot] = accept;
+        sm.scal[slot] = delta / R1;
+        if (accept) {
+          X[(size_t)s * n + i] = sm.xn[i];
+          ++n_acc;
+        }
+        if (!isfinite(R1)) d.status[c] = HQ_ENAN;
+      }
+      __syncthreads();
+      if (sm.sint[2 + slot]) {
+        // G' = Gc + a b^T with a = (delta/R1)(Gc[:, i] - e_i), b = Gc[i, :],
+        // Gc = G + sum_m A[:, m] B[:, m]^T (updates not yet flushed).
+        const double f = sm.scal[slot];
+        for (int idx = threadIdx.x; idx < 2 * n; idx += HQ_THREADS) {
+          if (idx < n) {
+            const int r = idx;
+            double v = G[(size_t)i * n + r];
+            for (int m = 0; m < kk; ++m) v = fma(A[m * n + r], B[m * n + i], v);
+            if (r == i) v -= 1.0;
+            A[kk * n + r] = f * v;
+          } else {
+            const int col = idx - n;
+            double v = G[(size_t)col * n + i];
+            for (int m = 0; m < kk; ++m) v = fma(A[m * n + i], B[m * n + col], v);
+            B[kk * n + col] = v;
+          }
+        }
+        __syncthreads();
+        for (int r = threadIdx.x; r < n; r += HQ_THREADS) sm.dcorr[r] = fma(A[kk * n + r], B[kk * n + r], sm.dcorr[r]);
+        ++kk;
+        if (kk == k) {
+          // flush: G += A B^T, an n x n x k FP64 contraction
+          for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+            const int r = idx % n, col = idx / n;
+            double v = G[(size_t)col * n + r];
+            for (int m = 0; m < kk; ++m) v = fma(A[m * n + r], B[m * n + col], v);
+            G[(size_t)col * n + r] = v;
+          }
+          __syncthreads();
+          for (int r = threadIdx.x; r < n; r += HQ_THREADS) sm.dcorr[r] = 0.0;
+          kk = 0;
+        }
+        __syncthreads();
+      }
+    }
+    if (kk > 0) {
+      for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+        const int r = idx % n, col = idx / n;
+        double v = G[(size_t)col * n + r];
+        for (int m = 0; m < kk; ++m) v = fma(A[m * n + r], B[m * n + col], v);
+        G[(size_t)col * n + r] = v;
+      }
+    }
+    // wrap: G_l = exp(-dtau K) D_l G_{l-1} D_l^-1 exp(dtau K), D_l = exp(-dtau V_l)
+    for (int r = threadIdx.x; r < n; r += HQ_THREADS) sm.dl[r] = exp(-d.dtau * (d.g * X[(size_t)s * n + r] - d.mu));
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+      const int r = idx % n, col = idx / n;
+      G[(size_t)col * n + r] = (sm.dl[r] * G[(size_t)col * n + r]) / sm.dl[col];
+    }
+    __syncthreads();
+    kin_rows<LMAX>(G, n, n, sm.ex, sm.ey, d.nx, d.ny);
+    kin_cols<LMAX>(G, n, n, sm.exi, sm.eyi, d.nx, d.ny);
+  }
+  if (threadIdx.x == 0) {
+    long long* cnt = d.counters + (size_t)c * kCounters;
+    cnt[0] += (long long)(s1 - s0) * n;
+    cnt[1] += n_acc;
+  }
+
+  // ---- restabilisation at l = s1: right factors B_{s1}..B_1 = UR DR TR
+  double* UR = d.UR + (size_t)c * n * n;
+  double* TR = d.TR + (size_t)c * n * n;
+  double* DR = d.DR + (size_t)c * n;
+  double* P = chain_work(d, c, WK_P);
+  double* T2 = chain_work(d, c, WK_T2);
+  double* Gf = chain_work(d, c, WK_U);
+  const bool first = (s0 == 0);
+  if (first) set_identity(P, n, n);
+  else copy_scale_cols(P, UR, n, n, DR);
+  __syncthreads();
+  for (int s = s0; s < s1; ++s) {
+    for (int r = threadIdx.x; r < n; r += HQ_THREADS) sm.dl[r] = exp(-d.dtau * (d.g * X[(size_t)s * n + r] - d.mu));
+    __syncthreads();
+    scale_rows(P, n, n, sm.dl);
+    __syncthreads();
+    kin_rows<LMAX>(P, n, n, sm.ex, sm.ey, d.nx, d.ny);
+  }
+  const QrScratch qs{sm.tau, sm.vn1, sm.vn2, sm.vs, sm.perm, sm.sint};
+  qr_pivoted(P, n, n, qs);
+  form_q(P, n, n, UR, qs);
+  t_update(P, n, n, qs, DR, first ? nullptr : TR, T2);
+  copy_mat(TR, T2, n, n);
+  __syncthreads();
+  const double ld = green_two_sided(d, c, sm, s1, Gf);
+  double err = 0.0, bad = 0.0;
+  for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+    const double gf = Gf[idx];
+    if (!isfinite(gf)) bad = 1.0;
+    err = fmax(err, fabs(G[idx] - gf));
+  }
+  err = block_max(err, sm.red);
+  bad = block_max(bad, sm.red);
+  copy_mat(G, Gf, n, n);
+  if (threadIdx.x == 0) {
+    double* acc = d.acc + (size_t)c * kAccSlots;
+    acc[ACC_WRAP] = fmax(acc[ACC_WRAP], err);
+    if (s1 == L) d.logdet[c] = ld;
+    flag_nonfinite(d, c, ld);
+    if (bad != 0.0) d.status[c] = HQ_ENAN;
+  }
+  __syncthreads();
+  if (measure) measure_green(d, c, sm, G);
+}
+
+template <int LMAX>
+__global__ void __launch_bounds__(HQ_THREADS) global_move_kernel(Dev d, int site, uint32_t sweep) {
+  extern __shared__ double smraw[];
+  const int c = blockIdx.x;
+  const int n = d.n, L = d.L;
+  const Smem sm = carve(d, smraw);
+  load_kinetic(d, sm);
+  double* X = d.X + (size_t)c * L * n;
+  if (threadIdx.x == 0) {
+    double u1, u2;
+    proposal_uniforms(d.key0, d.key1, (uint32_t)site, sweep, (uint32_t)(d.first_chain + c), 1u, u1, u2);
+    sm.scal[0] = d.dx_global * (2.0 * u1 - 1.0);
+    sm.scal[1] = u2;
+  }
+  __syncthreads();
+  const double dx = sm.scal[0];
+  double a = 0.0;
+  for (int s = threadIdx.x; s < L; s += HQ_THREADS) {
+    const double x = X[(size_t)s * n + site];
+    a += (x + dx) * (x + dx) - x * x;
+  }
+  a = block_sum(a, sm.red);
+  const double dS = 0.5 * d.dtau * d.mass * (d.omega * d.omega) * a;
+  const double ld_new = udv_top_down<LMAX>(d, c, sm, X, site, dx, false, nullptr);
+  if (threadIdx.x == 0) {
+    const double arg = 2.0 * (ld_new - d.logdet[c]) - dS;
+    const double prob = exp(fmin(arg, 709.0));
+    const int accept = sm.scal[1] < prob;
+    long long* cnt = d.counters + (size_t)c * kCounters;
+    cnt[2] += 1;
+    if (accept) {
+      cnt[3] += 1;
+      d.logdet[c] = ld_new;
+    }
+    flag_nonfinite(d, c, ld_new);
+    sm.sint[4] = accept;
+  }
+  __syncthreads();
+  if (sm.sint[4]) {
+    for (int s = threadIdx.x; s < L; s += HQ_THREADS) X[(size_t)s * n + site] = X[(size_t)s * n + site] + dx;
+  }
+}
+
+__global__ void __launch_bounds__(HQ_THREADS) sweep_end_kernel(Dev d, int slot, int measured) {
+  __shared__ double red[HQ_WARPS];
+  const int c = blockIdx.x;
+  const int n = d.n, L = d.L;
+  const double* X = d.X + (size_t)c * L * n;
+  double s1 = 0.0, s2 = 0.0;
+  for (int idx = threadIdx.x; idx < L * n; idx += HQ_THREADS) {
+    const double x = X[idx];
+    s1 += x;
+    s2 += x * x;
+  }
+  s1 = block_sum(s1, red);
+  s2 = block_sum(s2, red);
+  if (threadIdx.x == 0) {
+    double* acc = d.acc + (size_t)c * kAccSlots;
+    double* tot = d.tot + (size_t)c * kTotSlots;
+    const double xm = s1 / ((double)L * n), x2 = s2 / ((double)L * n);
+    double vals[HQ_N_OBS];
+    const bool has = measured && acc[ACC_COUNT] > 0.0;
+    const double nanv = __longlong_as_double(0x7ff8000000000000LL);
+    vals[HQ_OBS_DENSITY] = has ? acc[ACC_DENSITY] / acc[ACC_COUNT] : nanv;
+    vals[HQ_OBS_DOUBLE_OCC] = has ? acc[ACC_DOCC] / acc[ACC_COUNT] : nanv;
+    vals[HQ_OBS_SCDW] = has ? acc[ACC_SCDW] / acc[ACC_COUNT] : nanv;
+    vals[HQ_OBS_X_MEAN] = xm;
+    vals[HQ_OBS_X2] = x2;
+    vals[HQ_OBS_WRAP_ERR] = acc[ACC_WRAP];
+    if (slot >= 0 && slot < d.max_series)
+      for (int o = 0; o < HQ_N_OBS; ++o) d.series[((size_t)c * HQ_N_OBS + o) * d.max_series + slot] = vals[o];
+    if (has) {
+      tot[TOT_DENSITY] += vals[HQ_OBS_DENSITY];
+      tot[TOT_DOCC] += vals[HQ_OBS_DOUBLE_OCC];
+      tot[TOT_SCDW] += vals[HQ_OBS_SCDW];
+      tot[TOT_MEASURED] += 1.0;
+    }
+    tot[TOT_XMEAN] += xm;
+    tot[TOT_X2] += x2;
+    tot[TOT_SWEEPS] += 1.0;
+    tot[TOT_WRAP] = fmax(tot[TOT_WRAP], acc[ACC_WRAP]);
+    for (int o = 0; o < kAccSlots; ++o) acc[o] = 0.0;
+  }
+}
+
+__global__ void reset_acc_kernel(Dev d) {
+  const int c = blockIdx.x;
+  for (int o = threadIdx.x; o < kAccSlots; o += blockDim.x) d.acc[(size_t)c * kAccSlots + o] = 0.0;
+}
+
+// log W = 2 log|det M| - dtau S_ph per chain.
+__global__ void __launch_bounds__(HQ_THREADS) log_weight_kernel(Dev d, double* out) {
+  __shared__ double red[HQ_WARPS];
+  const int c = blockIdx.x;
+  const int n = d.n, L = d.L;
+  const double* X = d.X + (size_t)c * L * n;
+  double kin = 0.0, pot = 0.0;
+  for (int idx = threadIdx.x; idx < L * n; idx += HQ_THREADS) {
+    const int s = idx / n, i = idx % n;
+    const double x = X[idx];
+    const double xp = X[(size_t)((s + 1) % L) * n + i];
+    kin += (xp - x) * (xp - x);
+    pot += x * x;
+  }
+  kin = block_sum(kin, red);
+  pot = block_sum(pot, red);
+  if (threadIdx.x == 0) {
+    const double act = d.mass / (2.0 * d.dtau) * kin + 0.5 * d.dtau * d.mass * (d.omega * d.omega) * pot;
+    out[c] = 2.0 * d.logdet[c] - act;
+  }
+}
+
+__global__ void proposals_kernel(uint32_t key0, uint32_t key1, uint32_t chain, uint32_t sweep, uint32_t tag,
+                                 const uint32_t* events, int n, double* u1, double* u2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    double a, b;
+    proposal_uniforms(key0, key1, events[i], sweep, chain, tag, a, b);
+    u1[i] = a;
+    u2[i] = b;
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+
+static inline int lmax_of(int nx, int ny) {
+  const int m = nx > ny ? nx : ny;
+  return m <= 2 ? 2 : m <= 4 ? 4 : m <= 8 ? 8 : 16;
+}
+
+#define HQ_DISPATCH(KERNEL, d, stream, ...)                                                  \
+  do {                                                                                      \
+    const size_t sb = smem_bytes(d);                                                        \
+    switch (lmax_of((d).nx, (d).ny)) {                                                      \
+      case 2: KERNEL<2><<<(d).n_chains, HQ_THREADS, sb, stream>>>(__VA_ARGS__); break;      \
+      case 4: KERNEL<4><<<(d).n_chains, HQ_THREADS, sb, stream>>>(__VA_ARGS__); break;      \
+      case 8: KERNEL<8><<<(d).n_chains, HQ_THREADS, sb, stream>>>(__VA_ARGS__); break;      \
+      default: KERNEL<16><<<(d).n_chains, HQ_THREADS, sb, stream>>>(__VA_ARGS__); break;    \
+    }                                                                                       \
+  } while (0)
+
+cudaError_t launch_stack_build(const Dev& d, cudaStream_t s) {
+  HQ_DISPATCH(stack_build_kernel, d, s, d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_local_chunk(const Dev& d, int s0, int s1, uint32_t sweep, int measure, cudaStream_t s) {
+  HQ_DISPATCH(local_chunk_kernel, d, s, d, s0, s1, sweep, measure);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_global_move(const Dev& d, int site, uint32_t sweep, cudaStream_t s) {
+  HQ_DISPATCH(global_move_kernel, d, s, d, site, sweep);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_end(const Dev& d, int slot, int measured, cudaStream_t s) {
+  sweep_end_kernel<<<d.n_chains, HQ_THREADS, 0, s>>>(d, slot, measured);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reset_acc(const Dev& d, cudaStream_t s) {
+  reset_acc_kernel<<<d.n_chains, 32, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_log_weight(const Dev& d, double* out, cudaStream_t s) {
+  log_weight_kernel<<<d.n_chains, HQ_THREADS, 0, s>>>(d, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_proposals(uint32_t key0, uint32_t key1, uint32_t chain, uint32_t sweep, uint32_t tag,
+                             const uint32_t* events, int n, double* u1, double* u2, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  proposals_kernel<<<(n + 255) / 256, 256, 0, s>>>(key0, key1, chain, sweep, tag, events, n, u1, u2);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ FP64 pipe probe
+#define HQ_PROBE_ITERS 4096
+__global__ void fp64_probe_kernel(double* out, double b, double c) {
+  double a0 = threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
+  for (int it = 0; it < HQ_PROBE_ITERS; ++it) {
+    a0 = fma(a0, b, c); a1 = fma(a1, b, c); a2 = fma(a2, b, c); a3 = fma(a3, b, c);
+    a4 = fma(a4, b, c); a5 = fma(a5, b, c); a6 = fma(a6, b, c); a7 = fma(a7, b, c);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+}
+
+double fp64_probe_tflops(int reps, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1.0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1.0;
+  const int grid = sms * 4, block = 256;
+  double* out = nullptr;
+  if (cudaMallocAsync(&out, sizeof(double) * grid * block, s) != cudaSuccess) return -1.0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  fp64_probe_kernel<<<grid, block, 0, s>>>(out, 0.999, 1e-3);
+  cudaEventRecord(e0, s);
+  for (int r = 0; r < reps; ++r) fp64_probe_kernel<<<grid, block, 0, s>>>(out, 0.999, 1e-3);
+  cudaEventRecord(e1, s);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(out, s);
+  cudaStreamSynchronize(s);
+  if (cudaGetLastError() != cudaSuccess || ms <= 0.f) return -1.0;
+  const double flops = (double)reps * grid * block * HQ_PROBE_ITERS * 8 * 2;
+  return flops / (ms * 1e-3) / 1e12;
+}
+
+}  // namespace hq

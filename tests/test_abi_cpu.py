@@ -1,0 +1,79 @@
+"""C-ABI checks that need no GPU: the library loads, exports every declared symbol,
+validates parameters on the host and computes tau_int like the oracle."""
+import ctypes
+import math
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "holstein_dqmc.h")
+
+
+def _lib():
+    import paper_1905_07440_gb300 as hq
+    if not os.path.exists(hq.LIB_PATH):
+        from paper_1905_07440_gb300 import build
+        build.build()
+    return hq, hq.load_library()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hq_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declarations_match_binding():
+    hq, _ = _lib()
+    assert declared_functions() == sorted(hq.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol():
+    hq, lib = _lib()
+    out = subprocess.run(["nm", "-D", "--defined-only", hq.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (hq_[a-z0-9_]+)\b", out))
+    for name in declared_functions():
+        assert name in exported, name
+        assert getattr(lib, name) is not None
+
+
+def test_arena_bytes_validates_parameters():
+    hq, _ = _lib()
+    from workloads import SMALL, BATCHED
+    assert hq.arena_bytes(SMALL, 1) > 0
+    assert hq.arena_bytes(BATCHED, 256, 1000) > hq.arena_bytes(BATCHED, 128, 1000)
+    bad = [SMALL.with_(nx=3, ny=3), SMALL.with_(nx=18, ny=18), SMALL.with_(beta=4.05), SMALL.with_(dtau=0.0),
+           SMALL.with_(delay_k=0), SMALL.with_(delay_k=33), SMALL.with_(n_wrap=0), SMALL.with_(mass=0.0),
+           SMALL.with_(beta=0.1)]
+    for p in bad:
+        assert hq.arena_bytes(p, 1) == 0, p
+    assert hq.arena_bytes(SMALL, 0) == 0
+
+
+def test_arena_holds_the_largest_lattice():
+    hq, _ = _lib()
+    from workloads import LARGEST
+    nb = hq.arena_bytes(LARGEST, 64, 2000)
+    # fields, G, UDV stack (15 boundaries x 2 N^2), 7 work matrices, right factors
+    n, L = 256, 160
+    assert nb >= 8 * 64 * (L * n + (15 * 2 + 10) * n * n)
+    assert nb < 4 * 2 ** 30
+
+
+def test_tau_int_matches_oracle():
+    hq, _ = _lib()
+    from oracle import autocorr
+    rng = np.random.default_rng(7)
+    x = np.empty(5000)
+    x[0] = 0.0
+    for k in range(1, x.size):
+        x[k] = 0.8 * x[k - 1] + rng.standard_normal()
+    t_c, w_c = hq.tau_int(x)
+    t_o, w_o = autocorr.tau_int(x)
+    assert w_c == w_o
+    assert abs(t_c - t_o) < 1e-10 * t_o
+    assert hq.tau_int(np.ones(10))[0] == 0.5
