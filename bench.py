@@ -1,0 +1,336 @@
+"""Benchmark of the GB300 Holstein DQMC engine (plain DQMC, batched chains).
+
+Workload (default): 8x8 periodic lattice (N = 64), t = M = Omega = 1, g = sqrt(2),
+mu = -2 (half filling), beta = 8, dtau = 0.1 (L = 80), 256 independent chains, delayed
+rank k = 16, n_wrap = 10; one step = one sweep of every chain: local moves at every
+(l, i) with dX ~ U[-0.5, 0.5), then one block move per site with dX ~ U[-1, 1) accepted
+on the full stabilised determinant ratio.  FP64 throughout.  Fields start i.i.d.
+N(0, 1/(M Omega^2)) from seed 20190517 + chain id (synthetic; the paper has no dataset).
+
+Metric: chain-sweeps per second over all ranks (every rank runs its own chains: weak
+scaling, no collective on the data path).  Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "indep. samples/s (τ_int-corrected) learned vs plain DQMC; sweeps/s; p50/p99"
+UNIT = "chain-sweeps/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+# ------------------------------------------------------------------ flop model
+def flops_block_move(p):
+    """FP64 flops of one block-move launch for one chain (global_move_kernel).
+
+    Per slice: separable exp(-dtau K) on an N x N matrix, 2 N^2 (nx + ny), and the
+    exp(-dtau V) row scaling, N^2.  Per chunk of n_wrap slices: pivoted Householder QR
+    4/3 N^3, explicit Q 4/3 N^3, T update N^3 (not for the first chunk).  Final LU 2/3 N^3.
+    """
+    n, L = p.n_sites, p.n_slices
+    chunks = math.ceil(L / p.n_wrap)
+    per_slice = 2.0 * n * n * (p.nx + p.ny) + n * n
+    return L * per_slice + chunks * (8.0 / 3.0) * n ** 3 + (chunks - 1) * n ** 3 + (2.0 / 3.0) * n ** 3
+
+
+# -------------------------------------------------------------- CPU baseline
+def _oracle_worker(args):
+    params, chain, n_sweeps = args
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    import numpy as np  # noqa: F401
+    from oracle import dqmc
+    X0 = workloads.initial_fields(params, 1, seed=workloads.DEFAULT_SEED + chain)[0]
+    ch = dqmc.OracleChain(params, X0, chain=chain)
+    t0 = time.perf_counter()
+    for _ in range(n_sweeps):
+        ch.sweep()
+    return n_sweeps, time.perf_counter() - t0
+
+
+def oracle_throughput(params, workers, sweeps_per_worker=1, first_chain=0):
+    """Oracle chain-sweeps/s with one chain per process (BLAS pinned to one thread)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        res = pool.map(_oracle_worker, [(params, first_chain + w, sweeps_per_worker) for w in range(workers)])
+    rate = sum(n / t for n, t in res)
+    cpu_s = sum(t for _, t in res)
+    return rate, cpu_s
+
+
+def cpu_count():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -------------------------------------------------------------------- arms
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def workload_params(name):
+    if name == "batched":
+        return workloads.BATCHED, workloads.BATCHED_RUN["n_chains"], "batched plain DQMC 8x8 beta=8 L=80"
+    if name == "small":
+        return workloads.SMALL, 1, "plain DQMC 4x4 beta=4 L=40"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    params, chains, wname = workload_params(args.workload)
+    cores = cpu_count()
+    workers = min(cores, chains)
+    for _ in range(args.warmup):
+        oracle_throughput(params, workers, 1)
+    rates, cpu_s = [], 0.0
+    for k in range(args.steps):
+        r, c = oracle_throughput(params, workers, 1, first_chain=k * workers % chains)
+        rates.append(r)
+        cpu_s += c
+    value = statistics.mean(rates)
+    sample = f"{workers} chains x 1 sweep per step, one chain per process, BLAS 1 thread, {cpu_s:.1f} s CPU total"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wname, "chains_per_rank": chains},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    rank, world, local_rank = dist_env()
+    params, chains, wname = workload_params(args.workload)
+    if args.chains:
+        chains = args.chains
+    if args.dx_global is not None:
+        params = params.with_(dx_global=args.dx_global)
+
+    # CPU baseline first (spawned before any CUDA call), rank 0 at N = 1 only.
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        workers = min(cpu_count(), 16)
+        rate, cpu_s = oracle_throughput(params, workers, 1)
+        cpu = {"value": rate, "unit": UNIT, "cores": workers, "kind": "oracle",
+               "sample": f"{workers} chains x 1 sweep of the same workload, one chain per process "
+                         f"(BLAS 1 thread), {cpu_s:.1f} s CPU"}
+
+    import numpy as np
+    import torch
+    import paper_1905_07440_gb300 as hq
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", device_id=dev)
+    stream = torch.cuda.Stream(device=dev)
+    first = rank * chains
+    X0 = workloads.initial_fields(params, chains, seed=workloads.DEFAULT_SEED + first)
+
+    with torch.cuda.stream(stream):
+        peak = hq.fp64_peak_tflops(20, stream.cuda_stream)
+        eng = hq.Engine(params, chains, first_chain=first, max_series=args.warmup + 2 * args.steps + 4,
+                        device=dev, stream=stream)
+        eng.set_fields(X0)
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+        for _ in range(args.warmup):
+            eng.sweep(1)
+        torch.cuda.synchronize(dev)
+
+        def barrier():
+            if world > 1:
+                torch.distributed.barrier()
+
+        # ---- device-resident timing: one event pair per sweep, L2 flushed between sweeps
+        eng.set_timing(True)
+        eng.timing()
+        uuid = None
+        try:
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+        except Exception:
+            pass
+        clocks = ClockSampler(uuid)
+        clocks.start()
+        barrier()
+        torch.cuda.synchronize(dev)
+        evs = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            eng.sweep(1)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize(dev)
+        barrier()
+        clk = clocks.stop()
+        phases = eng.timing()
+        eng.set_timing(False)
+        t_dev = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+        if world > 1:
+            t = torch.tensor([t_dev], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            t_dev = float(t.item())
+        value = chains * world * args.steps / t_dev
+
+        # ---- end to end through the C ABI with host buffers (pinned), copies timed
+        Xh = torch.empty(eng.field_shape, dtype=torch.float64, pin_memory=True).numpy()
+        Xh[:] = eng.get_fields()
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        obs = None
+        for _ in range(args.steps):
+            eng.set_fields(Xh)
+            eng.sweep(1)
+            eng.get_fields(Xh)
+            obs = eng.observables()
+        t_e2e = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = chains * world * args.steps / t_e2e
+        status_ok = all(o["status"] == 0 for o in obs)
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel (largest share of the timed region)
+    dom = max(phases, key=lambda k: phases[k][0])
+    ms, launches = phases[dom]
+    per_launch_s = ms / 1e3 / max(launches, 1)
+    if dom == "global_move":
+        fl = flops_block_move(params) * chains
+    else:
+        fl = None
+    achieved = fl / per_launch_s / 1e12 if fl else None
+    gpu_launches = sum(n for _, n in phases.values())
+    total_ms = sum(m for m, _ in phases.values())
+    xbytes = 8 * chains * params.n_slices * params.n_sites
+    obs_bytes = 104 * chains
+    acc_l = sum(o["local_accepted"] for o in obs) / max(1, sum(o["local_proposed"] for o in obs))
+    acc_g = sum(o["global_accepted"] for o in obs) / max(1, sum(o["global_proposed"] for o in obs))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_dev * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wname, "lattice": f"{params.nx}x{params.ny}", "beta": params.beta,
+                   "dtau": params.dtau, "L": params.n_slices, "chains_per_rank": chains, "delay_k": params.delay_k,
+                   "n_wrap": params.n_wrap, "block_moves_per_sweep": params.n_sites,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "flushed (512 MB write) before every timed sweep; flush outside the events"},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": xbytes, "d2h_bytes_per_step": xbytes + obs_bytes},
+        "gpu_launches": gpu_launches,
+        "roofline": {"bound": "alu", "kernel": dom + "_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "peak_source": "FP64 DFMA probe measured in this run (hq_fp64_peak_tflops)",
+                     "flops_per_launch": fl, "ms_per_launch": per_launch_s * 1e3,
+                     "share": ms / total_ms if total_ms else None},
+        "phases_ms": {k: v[0] for k, v in phases.items()},
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "acceptance": {"local": acc_l, "block": acc_g},
+        "status_ok": status_ok,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default="batched")
+    ap.add_argument("--chains", type=int, default=0, help="override chains per rank (profiling runs)")
+    ap.add_argument("--dx-global", type=float, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up sweeps", file=sys.stderr)
+    sys.exit(run_reference(args) if args.impl == "reference" else run_ours(args))
+
+
+if __name__ == "__main__":
+    main()

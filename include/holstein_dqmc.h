@@ -156,6 +156,15 @@ int hq_proposal_uniforms(uint64_t seed, uint32_t chain, uint32_t sweep, uint32_t
  * tau, stores W in *window if non-NULL.  n < 2 gives 0.5. */
 double hq_tau_int(const double* series, int n, double c, int* window);
 
+/* Kernel timing of hq_sweep: when enabled, CUDA events on the engine's stream bracket
+ * every launch group -- phase 0: stack build (1 launch), 1: local chunks (one launch per
+ * n_wrap slices), 2: block moves (N launches, one per site), 3: sweep end (1 launch).
+ * hq_get_timing synchronises, returns the milliseconds and launches per phase
+ * accumulated since the last call (ms[4], launches[4]) and clears them. */
+#define HQ_N_PHASES 4
+int hq_set_timing(hq_engine* e, int enable);
+int hq_get_timing(hq_engine* e, double* ms, int64_t* launches);
+
 /* FP64 pipe probe: runs a DFMA throughput kernel on the stream for about reps*10 ms and
  * returns achieved TFLOP/s (<= 0 on error).  Used to state the FP64 roofline. */
 double hq_fp64_peak_tflops(int reps, void* stream);

@@ -75,7 +75,11 @@ _SIGNATURES = {
                                             _P(ctypes.c_uint32), ctypes.c_int, _dp, _dp, _vp]),
     "hq_tau_int": (ctypes.c_double, [_dp, ctypes.c_int, ctypes.c_double, _P(ctypes.c_int)]),
     "hq_fp64_peak_tflops": (ctypes.c_double, [ctypes.c_int, _vp]),
+    "hq_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "hq_get_timing": (ctypes.c_int, [_vp, _dp, _P(ctypes.c_int64)]),
 }
+HQ_N_PHASES = 4
+PHASES = ("stack_build", "local_chunk", "global_move", "sweep_end")
 EXPORTED = tuple(_SIGNATURES)
 
 _lib = None
@@ -219,6 +223,16 @@ class Engine:
     def restore(self, blob):
         buf = ctypes.create_string_buffer(blob, len(blob))
         self._check(self.lib.hq_restore(self._h, buf, len(blob)), "hq_restore")
+
+    def set_timing(self, enable=True):
+        self._check(self.lib.hq_set_timing(self._h, 1 if enable else 0), "hq_set_timing")
+
+    def timing(self):
+        """{phase: (milliseconds, launches)} accumulated since the last call."""
+        ms = np.zeros(HQ_N_PHASES)
+        n = (ctypes.c_int64 * HQ_N_PHASES)()
+        self._check(self.lib.hq_get_timing(self._h, _dptr(ms), n), "hq_get_timing")
+        return {PHASES[i]: (float(ms[i]), int(n[i])) for i in range(HQ_N_PHASES)}
 
     @property
     def sweeps_done(self):

@@ -23,6 +23,17 @@ struct hq_engine {
   bool logdet_valid;    // log|det M| matches the fields
   bool green_valid;     // G holds G_0 of the fields
   std::string err;
+  // optional per-phase timing
+  struct Span { cudaEvent_t a, b; int phase, launches; };
+  bool timing = false;
+  std::vector<Span> spans;
+  std::vector<cudaEvent_t> spare;
+  double phase_ms[HQ_N_PHASES] = {0, 0, 0, 0};
+  long long phase_launches[HQ_N_PHASES] = {0, 0, 0, 0};
+  ~hq_engine() {
+    for (auto& s : spans) { cudaEventDestroy(s.a); cudaEventDestroy(s.b); }
+    for (auto ev : spare) cudaEventDestroy(ev);
+  }
 };
 
 namespace {
@@ -111,8 +122,38 @@ int cuda_check(hq_engine* e, cudaError_t st, const char* what) {
   return set_err(e, HQ_ECUDA, std::string(what) + ": " + cudaGetErrorString(st));
 }
 
+cudaEvent_t take_event(hq_engine* e) {
+  if (!e->spare.empty()) {
+    cudaEvent_t ev = e->spare.back();
+    e->spare.pop_back();
+    return ev;
+  }
+  cudaEvent_t ev = nullptr;
+  if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+  return ev;
+}
+
+// Brackets a launch group with events when timing is enabled.
+struct PhaseTimer {
+  hq_engine* e;
+  hq_engine::Span span{};
+  bool on = false;
+  PhaseTimer(hq_engine* eng, int phase, int launches) : e(eng) {
+    if (!e->timing) return;
+    span.a = take_event(e);
+    span.b = take_event(e);
+    span.phase = phase;
+    span.launches = launches;
+    on = span.a && span.b && cudaEventRecord(span.a, e->stream) == cudaSuccess;
+  }
+  ~PhaseTimer() {
+    if (on && cudaEventRecord(span.b, e->stream) == cudaSuccess) e->spans.push_back(span);
+  }
+};
+
 int ensure_state(hq_engine* e) {
   if (e->stack_valid) return HQ_OK;
+  PhaseTimer pt(e, 0, 1);
   int rc = cuda_check(e, hq::launch_stack_build(e->d, e->stream), "stack_build launch");
   if (rc) return rc;
   e->stack_valid = e->logdet_valid = e->green_valid = true;
@@ -259,6 +300,7 @@ int hq_sweep(hq_engine* e, int n_sweeps, unsigned flags) {
     if (do_local || !e->logdet_valid) rc = ensure_state(e);
     if (rc) return rc;
     if (do_local) {
+      PhaseTimer pt(e, 1, (d.L + d.n_wrap - 1) / d.n_wrap);
       for (int s0 = 0; s0 < d.L; s0 += d.n_wrap) {
         const int s1 = s0 + d.n_wrap < d.L ? s0 + d.n_wrap : d.L;
         rc = cuda_check(e, hq::launch_local_chunk(d, s0, s1, sw, meas ? 1 : 0, e->stream), "local_chunk launch");
@@ -268,6 +310,7 @@ int hq_sweep(hq_engine* e, int n_sweeps, unsigned flags) {
       e->logdet_valid = e->green_valid = true;
     }
     if (do_global) {
+      PhaseTimer pt(e, 2, d.n);
       for (int i = 0; i < d.n; ++i) {
         rc = cuda_check(e, hq::launch_global_move(d, i, sw, e->stream), "global_move launch");
         if (rc) return rc;
@@ -276,7 +319,10 @@ int hq_sweep(hq_engine* e, int n_sweeps, unsigned flags) {
       e->green_valid = false;  // log|det M| is kept current by the accepted moves
     }
     const int slot = e->series_len < d.max_series ? e->series_len : -1;
-    rc = cuda_check(e, hq::launch_sweep_end(d, slot, (meas && do_local) ? 1 : 0, e->stream), "sweep_end launch");
+    {
+      PhaseTimer pt(e, 3, 1);
+      rc = cuda_check(e, hq::launch_sweep_end(d, slot, (meas && do_local) ? 1 : 0, e->stream), "sweep_end launch");
+    }
     if (rc) return rc;
     if (slot >= 0) e->series_len++;
     e->sweeps++;
@@ -502,6 +548,35 @@ double hq_tau_int(const double* x, int n, double c, int* window) {
   }
   if (window) *window = n - 1;
   return tau;
+}
+
+int hq_set_timing(hq_engine* e, int enable) {
+  if (!e) return HQ_EINVAL;
+  e->timing = enable != 0;
+  return HQ_OK;
+}
+
+int hq_get_timing(hq_engine* e, double* ms, int64_t* launches) {
+  if (!e) return HQ_EINVAL;
+  int rc = cuda_check(e, cudaStreamSynchronize(e->stream), "timing sync");
+  if (rc) return rc;
+  for (auto& sp : e->spans) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, sp.a, sp.b) == cudaSuccess) {
+      e->phase_ms[sp.phase] += t;
+      e->phase_launches[sp.phase] += sp.launches;
+    }
+    e->spare.push_back(sp.a);
+    e->spare.push_back(sp.b);
+  }
+  e->spans.clear();
+  for (int i = 0; i < HQ_N_PHASES; ++i) {
+    if (ms) ms[i] = e->phase_ms[i];
+    if (launches) launches[i] = e->phase_launches[i];
+    e->phase_ms[i] = 0.0;
+    e->phase_launches[i] = 0;
+  }
+  return HQ_OK;
 }
 
 double hq_fp64_peak_tflops(int reps, void* stream) {
