@@ -39,8 +39,9 @@ def flops_block_move(p):
     """FP64 flops of one block-move launch for one chain (global_move_kernel).
 
     Per slice: separable exp(-dtau K) on an N x N matrix, 2 N^2 (nx + ny), and the
-    exp(-dtau V) row scaling, N^2.  Per chunk of n_wrap slices: pivoted Householder QR
-    4/3 N^3, explicit Q 4/3 N^3, T update N^3 (not for the first chunk).  Final LU 2/3 N^3.
+    exp(-dtau V) row scaling, N^2.  Per chunk of n_wrap slices: Householder QR (after a
+    one-time column ordering) 4/3 N^3, explicit Q 4/3 N^3, T update N^3 (not for the first
+    chunk).  Final LU 2/3 N^3.
     """
     n, L = p.n_sites, p.n_slices
     chunks = math.ceil(L / p.n_wrap)
@@ -176,8 +177,6 @@ def run_ours(args):
     params, chains, wname = workload_params(args.workload)
     if args.chains:
         chains = args.chains
-    if args.dx_global is not None:
-        params = params.with_(dx_global=args.dx_global)
 
     # CPU baseline first (spawned before any CUDA call), rank 0 at N = 1 only.
     cpu = None
@@ -202,7 +201,7 @@ def run_ours(args):
     X0 = workloads.initial_fields(params, chains, seed=workloads.DEFAULT_SEED + first)
 
     with torch.cuda.stream(stream):
-        peak = hq.fp64_peak_tflops(20, stream.cuda_stream)
+        peak = hq.fp64_peak_tflops(20, stream.cuda_stream, kind=hq.HQ_PROBE_DFMA)
         eng = hq.Engine(params, chains, first_chain=first, max_series=args.warmup + 2 * args.steps + 4,
                         device=dev, stream=stream)
         eng.set_fields(X0)
@@ -277,8 +276,10 @@ def run_ours(args):
     dom = max(phases, key=lambda k: phases[k][0])
     ms, launches = phases[dom]
     per_launch_s = ms / 1e3 / max(launches, 1)
-    if dom == "global_move":
-        fl = flops_block_move(params) * chains
+    kernel_names = {"block_moves": "global_phase_kernel", "local_chunk": "local_chunk_kernel",
+                    "stack_build": "stack_build_kernel", "sweep_end": "sweep_end_kernel"}
+    if dom == "block_moves":
+        fl = flops_block_move(params) * chains * params.n_sites   # one launch = N moves per chain
     else:
         fl = None
     achieved = fl / per_launch_s / 1e12 if fl else None
@@ -299,7 +300,7 @@ def run_ours(args):
                    "l2": "flushed (512 MB write) before every timed sweep; flush outside the events"},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": xbytes, "d2h_bytes_per_step": xbytes + obs_bytes},
         "gpu_launches": gpu_launches,
-        "roofline": {"bound": "alu", "kernel": dom + "_kernel", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "alu", "kernel": kernel_names[dom], "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
                      "peak_source": "FP64 DFMA probe measured in this run (hq_fp64_peak_tflops)",
                      "flops_per_launch": fl, "ms_per_launch": per_launch_s * 1e3,
@@ -316,6 +317,37 @@ def run_ours(args):
     return 0
 
 
+def run_peaks():
+    """FP64 pipe evidence: DFMA and DMMA probes of the library, cuBLAS DGEMM/SGEMM via torch."""
+    import torch
+    import paper_1905_07440_gb300 as hq
+    out = {"dfma_tflops": hq.fp64_peak_tflops(20, kind=hq.HQ_PROBE_DFMA),
+           "dmma_tflops": hq.fp64_peak_tflops(20, kind=hq.HQ_PROBE_DMMA)}
+
+    def rate(fn, flops, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return flops * reps / (a.elapsed_time(b) / 1e3) / 1e12
+
+    n = 8192
+    x = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    out["cublas_dgemm_8192_tflops"] = rate(lambda: x @ x, 2 * n ** 3)
+    xb = torch.randn(256, 64, 64, dtype=torch.float64, device="cuda")
+    out["cublas_batched_dgemm_256x64_tflops"] = rate(lambda: torch.bmm(xb, xb), 2 * 256 * 64 ** 3, 50)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    xs = x.float()
+    out["cublas_sgemm_8192_tflops"] = rate(lambda: xs @ xs, 2 * n ** 3)
+    out["device"] = torch.cuda.get_device_name()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -324,9 +356,11 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default="batched")
     ap.add_argument("--chains", type=int, default=0, help="override chains per rank (profiling runs)")
-    ap.add_argument("--dx-global", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--peaks", action="store_true", help="print the FP64/FP32 pipe probes and exit")
     args = ap.parse_args()
+    if args.peaks:
+        sys.exit(run_peaks())
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up sweeps", file=sys.stderr)
     sys.exit(run_reference(args) if args.impl == "reference" else run_ours(args))

@@ -47,6 +47,7 @@ extern "C" {
 #define HQ_ECUDA (-3)      /* a CUDA runtime call failed */
 #define HQ_EUNSTABLE (-4)  /* wrap error above tolerance (reported, chain kept) */
 #define HQ_ENAN (-5)       /* non-finite G, ratio or log-determinant */
+#define HQ_ETIMEOUT (-6)   /* a bounded device wait expired (chain state incomplete) */
 
 /* hq_sweep flags */
 #define HQ_LOCAL 1u
@@ -87,7 +88,7 @@ typedef struct hq_obs {   /* per chain, accumulated since hq_create / hq_restore
   double x_mean, x2;                  /* means over sweeps */
   double max_wrap_error;              /* max over all restabilisations */
   double logdet;                      /* log|det M| of the current fields */
-  int32_t status;                     /* 0, or HQ_ENAN if a non-finite value was seen */
+  int32_t status;                     /* 0, or HQ_ENAN / HQ_ETIMEOUT */
   int32_t pad;
 } hq_obs;
 
@@ -158,16 +159,27 @@ double hq_tau_int(const double* series, int n, double c, int* window);
 
 /* Kernel timing of hq_sweep: when enabled, CUDA events on the engine's stream bracket
  * every launch group -- phase 0: stack build (1 launch), 1: local chunks (one launch per
- * n_wrap slices), 2: block moves (N launches, one per site), 3: sweep end (1 launch).
+ * n_wrap slices), 2: block moves (1 launch), 3: sweep end (1 launch).
  * hq_get_timing synchronises, returns the milliseconds and launches per phase
- * accumulated since the last call (ms[4], launches[4]) and clears them. */
+ * accumulated since the last call (ms[4], launches[4]) and clears them.  The block-move
+ * phase is one persistent launch per sweep (N x n_chains moves). */
 #define HQ_N_PHASES 4
 int hq_set_timing(hq_engine* e, int enable);
 int hq_get_timing(hq_engine* e, double* ms, int64_t* launches);
 
-/* FP64 pipe probe: runs a DFMA throughput kernel on the stream for about reps*10 ms and
- * returns achieved TFLOP/s (<= 0 on error).  Used to state the FP64 roofline. */
-double hq_fp64_peak_tflops(int reps, void* stream);
+/* Per-section device cycle counters (profiling builds compiled with -DHQ_SECTION_TIMING):
+ * copies up to n counters (sum over CTAs of thread 0's clock64 spans; ids in
+ * csrc/hq_device.cuh) to out and clears them.  Returns the number copied; 0 in normal
+ * builds. */
+int hq_get_section_cycles(uint64_t* out, int n);
+
+/* FP64 pipe probe: runs a throughput kernel on the stream (reps launches of about 10 ms)
+ * and returns achieved TFLOP/s, or <= 0 on error.  kind 0: DFMA (fma on doubles, the
+ * engine's arithmetic); kind 1: DMMA (mma.sync m8n8k4 f64, the FP64 tensor path).  Used to
+ * state the FP64 roofline; allocates and frees its own small buffer. */
+#define HQ_PROBE_DFMA 0
+#define HQ_PROBE_DMMA 1
+double hq_fp64_peak_tflops(int kind, int reps, void* stream);
 
 #ifdef __cplusplus
 }

@@ -19,6 +19,7 @@ HQ_ENOMEM = -2
 HQ_ECUDA = -3
 HQ_EUNSTABLE = -4
 HQ_ENAN = -5
+HQ_ETIMEOUT = -6
 
 HQ_LOCAL = 1
 HQ_GLOBAL = 2
@@ -74,12 +75,13 @@ _SIGNATURES = {
     "hq_proposal_uniforms": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                             _P(ctypes.c_uint32), ctypes.c_int, _dp, _dp, _vp]),
     "hq_tau_int": (ctypes.c_double, [_dp, ctypes.c_int, ctypes.c_double, _P(ctypes.c_int)]),
-    "hq_fp64_peak_tflops": (ctypes.c_double, [ctypes.c_int, _vp]),
+    "hq_fp64_peak_tflops": (ctypes.c_double, [ctypes.c_int, ctypes.c_int, _vp]),
     "hq_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "hq_get_section_cycles": (ctypes.c_int, [_P(ctypes.c_uint64), ctypes.c_int]),
     "hq_get_timing": (ctypes.c_int, [_vp, _dp, _P(ctypes.c_int64)]),
 }
 HQ_N_PHASES = 4
-PHASES = ("stack_build", "local_chunk", "global_move", "sweep_end")
+PHASES = ("stack_build", "local_chunk", "block_moves", "sweep_end")
 EXPORTED = tuple(_SIGNATURES)
 
 _lib = None
@@ -261,5 +263,20 @@ def tau_int(series, c=6.0):
     return float(t), w.value
 
 
-def fp64_peak_tflops(reps=20, stream=None):
-    return float(load_library().hq_fp64_peak_tflops(int(reps), ctypes.c_void_p(stream or 0)))
+SECTIONS = ("dl", "kin", "prepivot", "qr", "form_q", "t_update", "logdet", "move", "wait", "prop_prep",
+            "prop_seq", "wrap", "restab_prod", "restab_qr", "restab_green", "measure")
+
+
+def section_cycles():
+    """{section: cycles} from a -DHQ_SECTION_TIMING build (empty otherwise); clears them."""
+    out = (ctypes.c_uint64 * len(SECTIONS))()
+    n = load_library().hq_get_section_cycles(out, len(SECTIONS))
+    return {SECTIONS[i]: int(out[i]) for i in range(max(n, 0))}
+
+
+HQ_PROBE_DFMA = 0
+HQ_PROBE_DMMA = 1
+
+
+def fp64_peak_tflops(reps=20, stream=None, kind=HQ_PROBE_DFMA):
+    return float(load_library().hq_fp64_peak_tflops(int(kind), int(reps), ctypes.c_void_p(stream or 0)))

@@ -15,6 +15,26 @@
 
 namespace hq {
 
+// Optional per-section cycle counters (compile with -DHQ_SECTION_TIMING): thread 0 of each
+// CTA adds the clock64() span of a code section to a device array that
+// hq_get_section_cycles() returns.  Off by default; no effect on results.
+enum {
+  SEC_DL = 0, SEC_KIN, SEC_PREPIVOT, SEC_QR, SEC_FORMQ, SEC_TUPD, SEC_LOGDET, SEC_MOVE, SEC_WAIT,
+  SEC_PROP_PREP, SEC_PROP_SEQ, SEC_WRAP, SEC_RESTAB_PROD, SEC_RESTAB_QR, SEC_RESTAB_GREEN, SEC_MEASURE,
+  SEC_COUNT
+};
+#ifdef HQ_SECTION_TIMING
+__device__ unsigned long long g_section_cycles[SEC_COUNT];  // one translation unit includes this header
+#define HQ_TIC(name) const long long hq_tic_##name = clock64()
+#define HQ_TOC(name, slot)                                                              \
+  do {                                                                                \
+    if (threadIdx.x == 0) atomicAdd(&g_section_cycles[slot], (unsigned long long)(clock64() - hq_tic_##name)); \
+  } while (0)
+#else
+#define HQ_TIC(name) (void)0
+#define HQ_TOC(name, slot) (void)0
+#endif
+
 struct Lattice {
   int nx, ny, n;
   const double* ex;   // exp(-dtau K_x), nx x nx row-major (shared memory)
@@ -93,15 +113,23 @@ __device__ __forceinline__ void proposal_uniforms(uint32_t key0, uint32_t key1, 
 // commute on the periodic lattice.  Applying it to an n x n matrix costs 2 n^2 (nx + ny)
 // flops instead of 2 n^3 for the dense product.
 
-// P <- (E_x (x) E_y) P  (acts on the row = site index of every column).
-template <int LMAX>
-__device__ void kin_rows(double* P, int ld, int ncols, const double* ex, const double* ey, int nx, int ny) {
+enum { KIN_PLAIN = 0, KIN_SCALE_BEFORE = 1, KIN_SCALE_AFTER = 2 };
+
+// P <- (E_x (x) E_y) P (acts on the row = site index of every column).  With
+// KIN_SCALE_BEFORE the rows are first multiplied by d (P <- E diag(d) P, a slice matrix
+// B = exp(-dtau K) exp(-dtau V)); with KIN_SCALE_AFTER afterwards (P <- diag(d) E P = B^T P).
+template <int LMAX, int MODE>
+__device__ void kin_rows(double* P, int ld, int ncols, const double* ex, const double* ey, int nx, int ny,
+                         const double* d = nullptr) {
   for (int line = threadIdx.x; line < ny * ncols; line += HQ_THREADS) {
     const int y = line % ny, j = line / ny;
     double* base = P + (size_t)j * ld + nx * y;
     double v[LMAX];
 #pragma unroll
-    for (int b = 0; b < LMAX; ++b) v[b] = (b < nx) ? base[b] : 0.0;
+    for (int b = 0; b < LMAX; ++b) {
+      v[b] = (b < nx) ? base[b] : 0.0;
+      if (MODE == KIN_SCALE_BEFORE && b < nx) v[b] *= d[nx * y + b];
+    }
 #pragma unroll
     for (int a = 0; a < LMAX; ++a) {
       if (a < nx) {
@@ -127,6 +155,7 @@ __device__ void kin_rows(double* P, int ld, int ncols, const double* ex, const d
 #pragma unroll
         for (int b = 0; b < LMAX; ++b)
           if (b < ny) acc = fma(ey[a * ny + b], v[b], acc);
+        if (MODE == KIN_SCALE_AFTER) acc *= d[x + nx * a];
         base[a * nx] = acc;
       }
     }
@@ -208,125 +237,134 @@ __device__ __forceinline__ void copy_mat(double* B, const double* A, int ld, int
   }
 }
 
-// ----------------------------------------------------- column-pivoted Householder QR
-// Scratch (shared memory): tau[n], vn1[n], vn2[n], vs[n], perm[n] (int), sint[>=1] (int).
+// ------------------------------------------- Householder QR with column pre-pivoting
+// Column-pivoted QR in the form used for DQMC stabilisation by Bauer (SciPost Phys. Core 2,
+// 011 (2020)): the columns are ordered once by decreasing Euclidean norm, then factored by
+// unpivoted Householder QR.  The product being factored is column-graded (B..B U D), so the
+// one-time ordering gives the graded R that the UDV decomposition needs, without per-step
+// pivot searches and norm downdates.
+//
+// Column work is spread over groups of 8 lanes (32 groups per CTA): each group reduces a
+// column's dot product with 3 shuffles, and every warp runs the same number of passes so
+// the shuffles always see all 32 lanes.
 struct QrScratch {
-  double* tau;
-  double* vn1;
-  double* vn2;
-  double* vs;
-  int* perm;
-  int* sint;
+  double* tau;   // [n] reflector scalars
+  double* vs;    // [2n] Householder vectors (current and next)
+  double* rinv;  // [n] 1 / D
+  int* perm;     // [n] perm[j] = original column placed at position j
+  int* sint;     // >= 1
 };
 
-// In place: on exit R is in the upper triangle of P, the Householder vectors (unit
-// leading entry implied) below it, tau[j] the reflector scalars and perm[j] the original
-// index of the column moved to position j.  Column norms are downdated after every step
-// and recomputed when cancellation makes the downdate unreliable (as in LAPACK xLAQP2).
-__device__ void qr_pivoted(double* P, int ld, int n, const QrScratch& s) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const double tol3z = 1.4901161193847656e-08;  // sqrt(DBL_EPSILON)
-  for (int c = tid; c < n; c += HQ_THREADS) s.perm[c] = c;
-  for (int c = warp; c < n; c += HQ_WARPS) {
-    const double* col = P + (size_t)c * ld;
+constexpr int kGroup = 8;
+constexpr int kGroups = HQ_THREADS / kGroup;
+
+__device__ __forceinline__ double group_sum(double v) {
+  v += __shfl_xor_sync(HQ_FULL, v, 4);
+  v += __shfl_xor_sync(HQ_FULL, v, 2);
+  v += __shfl_xor_sync(HQ_FULL, v, 1);
+  return v;
+}
+
+// Q <- columns of P ordered by decreasing norm (stable: ties keep index order); perm
+// records the order.  Norms are compared through their IEEE bit patterns, which order
+// non-negative doubles exactly like their values.  `norm2` is n doubles of scratch.
+__device__ void prepivot(const double* P, double* Q, int ld, int n, const QrScratch& s, double* norm2) {
+  const int g = threadIdx.x / kGroup, sub = threadIdx.x % kGroup;
+  for (int base = 0; base < n; base += kGroups) {
+    const int c = base + g;
     double a = 0.0;
-    for (int r = lane; r < n; r += 32) a = fma(col[r], col[r], a);
-    a = warp_sum(a);
-    if (lane == 0) {
-      s.vn1[c] = sqrt(a);
-      s.vn2[c] = s.vn1[c];
+    if (c < n) {
+      const double* col = P + (size_t)c * ld;
+      for (int r = sub; r < n; r += kGroup) a = fma(col[r], col[r], a);
     }
+    a = group_sum(a);
+    if (c < n && sub == 0) norm2[c] = a;
   }
   __syncthreads();
+  for (int c = threadIdx.x; c < n; c += HQ_THREADS) {
+    const long long mine = __double_as_longlong(norm2[c]);
+    int rank = 0;
+    for (int o = 0; o < n; ++o) {
+      const long long other = __double_as_longlong(norm2[o]);
+      rank += (other > mine) || (other == mine && o < c);
+    }
+    s.perm[rank] = c;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+    const int r = idx % n, j = idx / n;
+    Q[(size_t)j * ld + r] = P[(size_t)s.perm[j] * ld + r];
+  }
+  __syncthreads();
+}
+
+// Householder vector for column j of P (warp 0 only): v has a unit leading entry, its
+// tail overwrites P(j+1:, j), P(j, j) <- beta, tau[j] set (LAPACK xLARFG convention).
+__device__ __forceinline__ void house_gen(double* P, int ld, int n, int j, double* vs, double* tau) {
+  const int lane = threadIdx.x & 31;
+  double* cj = P + (size_t)j * ld;
+  double a = 0.0;
+  for (int r = j + 1 + lane; r < n; r += 32) a = fma(cj[r], cj[r], a);
+  a = warp_sum(a);
+  const double alpha = cj[j];
+  double tj = 0.0, beta = alpha, scal = 0.0;
+  if (a != 0.0) {
+    const double nrm = sqrt(fma(alpha, alpha, a));
+    beta = (alpha >= 0.0) ? -nrm : nrm;
+    tj = (beta - alpha) / beta;
+    scal = 1.0 / (alpha - beta);
+  }
+  for (int r = j + 1 + lane; r < n; r += 32) {
+    const double v = cj[r] * scal;
+    cj[r] = v;
+    vs[r] = v;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    cj[j] = beta;
+    vs[j] = 1.0;
+    tau[j] = tj;
+  }
+  __syncwarp();
+}
+
+// In place unpivoted Householder QR: R in the upper triangle, reflector vectors (unit
+// leading entry implied) below it, tau[j] the reflector scalars (LAPACK xGEQR2 result).
+// One barrier per column with look-ahead: during step j, warp 0 applies reflector j to
+// column j+1 and builds reflector j+1 while warps 1.. apply reflector j to columns j+2..
+// (two vector buffers in `vs`, 2n doubles).
+__device__ void qr_householder(double* P, int ld, int n, const QrScratch& s) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = (tid - 32) / kGroup, sub = tid % kGroup;  // groups of warps 1..
+  constexpr int kTailGroups = (HQ_THREADS - 32) / kGroup;
+  if (warp == 0) house_gen(P, ld, n, 0, s.vs, s.tau);
+  __syncthreads();
   for (int j = 0; j < n; ++j) {
-    if (warp == 0) {
-      double best = -1.0;
-      int bi = j;
-      for (int c = j + lane; c < n; c += 32) {
-        const double v = s.vn1[c];
-        if (v > best) { best = v; bi = c; }
-      }
-#pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        const double ob = __shfl_xor_sync(HQ_FULL, best, o);
-        const int oi = __shfl_xor_sync(HQ_FULL, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (lane == 0) s.sint[0] = bi;
-    }
-    __syncthreads();
-    const int p = s.sint[0];
-    if (p != j) {
-      double* cj = P + (size_t)j * ld;
-      double* cp = P + (size_t)p * ld;
-      for (int r = tid; r < n; r += HQ_THREADS) {
-        const double a = cj[r];
-        cj[r] = cp[r];
-        cp[r] = a;
-      }
-      if (tid == 0) {
-        double a = s.vn1[j]; s.vn1[j] = s.vn1[p]; s.vn1[p] = a;
-        a = s.vn2[j]; s.vn2[j] = s.vn2[p]; s.vn2[p] = a;
-        const int q = s.perm[j]; s.perm[j] = s.perm[p]; s.perm[p] = q;
-      }
-      __syncthreads();
-    }
-    double* cj = P + (size_t)j * ld;
-    if (warp == 0) {
-      double a = 0.0;
-      for (int r = j + 1 + lane; r < n; r += 32) a = fma(cj[r], cj[r], a);
-      a = warp_sum(a);
-      const double alpha = cj[j];
-      double tj = 0.0, beta = alpha, scal = 0.0;
-      if (a != 0.0) {
-        const double nrm = sqrt(fma(alpha, alpha, a));
-        beta = (alpha >= 0.0) ? -nrm : nrm;
-        tj = (beta - alpha) / beta;
-        scal = 1.0 / (alpha - beta);
-      }
-      for (int r = j + 1 + lane; r < n; r += 32) {
-        const double v = cj[r] * scal;
-        cj[r] = v;
-        s.vs[r] = v;
-      }
-      __syncwarp();
-      if (lane == 0) {
-        cj[j] = beta;
-        s.vs[j] = 1.0;
-        s.tau[j] = tj;
-      }
-    }
-    __syncthreads();
+    const double* vc = s.vs + (j & 1) * n;
+    double* vn = s.vs + ((j + 1) & 1) * n;
     const double tj = s.tau[j];
-    for (int c = j + 1 + warp; c < n; c += HQ_WARPS) {
-      double* cc = P + (size_t)c * ld;
-      if (tj != 0.0) {
-        double w = 0.0;
-        for (int r = j + lane; r < n; r += 32) w = fma(s.vs[r], cc[r], w);
-        w = warp_sum(w) * tj;
-        for (int r = j + lane; r < n; r += 32) cc[r] = fma(-w, s.vs[r], cc[r]);
-        __syncwarp();
-      }
-      const double nj = s.vn1[c];
-      const double n2 = s.vn2[c];
-      const double rj = cc[j];
-      __syncwarp();
-      if (nj != 0.0) {
-        const double q = fabs(rj) / nj;
-        const double temp = fmax(0.0, (1.0 - q) * (1.0 + q));
-        const double ratio = nj / n2;
-        const double temp2 = temp * ratio * ratio;
-        if (temp2 <= tol3z) {
-          double a = 0.0;
-          for (int r = j + 1 + lane; r < n; r += 32) a = fma(cc[r], cc[r], a);
-          a = warp_sum(a);
-          if (lane == 0) {
-            s.vn1[c] = sqrt(a);
-            s.vn2[c] = s.vn1[c];
-          }
-        } else if (lane == 0) {
-          s.vn1[c] = nj * sqrt(temp);
+    if (warp == 0) {
+      if (j + 1 < n) {
+        double* cc = P + (size_t)(j + 1) * ld;
+        if (tj != 0.0) {
+          double w = 0.0;
+          for (int r = j + lane; r < n; r += 32) w = fma(vc[r], cc[r], w);
+          w = warp_sum(w) * tj;
+          for (int r = j + lane; r < n; r += 32) cc[r] = fma(-w, vc[r], cc[r]);
+          __syncwarp();
         }
+        house_gen(P, ld, n, j + 1, vn, s.tau);
+      }
+    } else if (tj != 0.0) {
+      for (int base = j + 2; base < n; base += kTailGroups) {
+        const int c = base + g;
+        double* cc = P + (size_t)c * ld;
+        double w = 0.0;
+        if (c < n)
+          for (int r = j + sub; r < n; r += kGroup) w = fma(vc[r], cc[r], w);
+        w = group_sum(w) * tj;
+        if (c < n)
+          for (int r = j + sub; r < n; r += kGroup) cc[r] = fma(-w, vc[r], cc[r]);
       }
     }
     __syncthreads();
@@ -334,44 +372,74 @@ __device__ void qr_pivoted(double* P, int ld, int n, const QrScratch& s) {
 }
 
 // U <- Q = H_0 H_1 ... H_{n-1} (explicit), from the reflectors stored in P and tau.
+// One barrier per reflector: the next reflector's vector is staged into the other half of
+// `vs` while the current one is applied.
 __device__ void form_q(const double* P, int ld, int n, double* U, const QrScratch& s) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = threadIdx.x / kGroup, sub = threadIdx.x % kGroup;
   set_identity(U, ld, n);
+  const int jl = n - 1;
+  for (int r = jl + threadIdx.x; r < n; r += HQ_THREADS) s.vs[(jl & 1) * n + r] = 1.0;
   __syncthreads();
   for (int j = n - 1; j >= 0; --j) {
+    const double* vc = s.vs + (j & 1) * n;
+    if (j > 0) {
+      double* vn = s.vs + ((j - 1) & 1) * n;
+      for (int r = j - 1 + threadIdx.x; r < n; r += HQ_THREADS) vn[r] = (r == j - 1) ? 1.0 : P[(size_t)(j - 1) * ld + r];
+    }
     const double tj = s.tau[j];
-    if (tj == 0.0) continue;  // uniform across the CTA
-    for (int r = j + tid; r < n; r += HQ_THREADS) s.vs[r] = (r == j) ? 1.0 : P[(size_t)j * ld + r];
-    __syncthreads();
-    for (int c = j + warp; c < n; c += HQ_WARPS) {
-      double* uc = U + (size_t)c * ld;
-      double w = 0.0;
-      for (int r = j + lane; r < n; r += 32) w = fma(s.vs[r], uc[r], w);
-      w = warp_sum(w) * tj;
-      for (int r = j + lane; r < n; r += 32) uc[r] = fma(-w, s.vs[r], uc[r]);
+    if (tj != 0.0) {
+      for (int base = j; base < n; base += kGroups) {
+        const int c = base + g;
+        double* uc = U + (size_t)c * ld;
+        double w = 0.0;
+        if (c < n)
+          for (int r = j + sub; r < n; r += kGroup) w = fma(vc[r], uc[r], w);
+        w = group_sum(w) * tj;
+        if (c < n)
+          for (int r = j + sub; r < n; r += kGroup) uc[r] = fma(-w, vc[r], uc[r]);
+      }
     }
     __syncthreads();
   }
 }
 
 // D[j] = |R_jj| and Tout = T' Tprev with T'(j, perm[c]) = R(j, c) / D[j] for c >= j
-// (T' = D^-1 R Pi^T).  With Tprev == nullptr, Tout = T'.
+// (T' = D^-1 R Pi^T).  With Tprev == nullptr, Tout = T'.  Each thread produces four
+// outputs of one row j (four independent FMA chains); lanes of a warp share j or j+1, so
+// trip counts stay nearly uniform.
 __device__ void t_update(const double* P, int ld, int n, const QrScratch& s, double* D,
                          const double* Tprev, double* Tout) {
-  for (int j = threadIdx.x; j < n; j += HQ_THREADS) D[j] = fabs(P[(size_t)j * ld + j]);
+  for (int j = threadIdx.x; j < n; j += HQ_THREADS) {
+    const double dj = fabs(P[(size_t)j * ld + j]);
+    D[j] = dj;
+    s.rinv[j] = 1.0 / dj;
+  }
   __syncthreads();
   if (Tprev == nullptr) {
     for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
       const int j = idx % n, c = idx / n;
-      Tout[(size_t)s.perm[c] * ld + j] = (c >= j) ? P[(size_t)c * ld + j] / D[j] : 0.0;
+      Tout[(size_t)s.perm[c] * ld + j] = (c >= j) ? P[(size_t)c * ld + j] * s.rinv[j] : 0.0;
     }
   } else {
-    for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
-      const int j = idx % n, col = idx / n;
-      const double* tc = Tprev + (size_t)col * ld;
-      double acc = 0.0;
-      for (int c = j; c < n; ++c) acc = fma(P[(size_t)c * ld + j], tc[s.perm[c]], acc);
-      Tout[(size_t)col * ld + j] = acc / D[j];
+    const int nq = n >> 2;  // n is a multiple of 4
+    for (int idx = threadIdx.x; idx < n * nq; idx += HQ_THREADS) {
+      const int q = idx % nq, j = idx / nq;
+      const double* t0 = Tprev + (size_t)(4 * q) * ld;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      for (int c = j; c < n; ++c) {
+        const double r = P[(size_t)c * ld + j];
+        const int pc = s.perm[c];
+        a0 = fma(r, t0[pc], a0);
+        a1 = fma(r, t0[ld + pc], a1);
+        a2 = fma(r, t0[2 * (size_t)ld + pc], a2);
+        a3 = fma(r, t0[3 * (size_t)ld + pc], a3);
+      }
+      const double ri = s.rinv[j];
+      double* o = Tout + (size_t)(4 * q) * ld + j;
+      o[0] = a0 * ri;
+      o[ld] = a1 * ri;
+      o[2 * (size_t)ld] = a2 * ri;
+      o[3 * (size_t)ld] = a3 * ri;
     }
   }
   __syncthreads();
@@ -413,8 +481,8 @@ __device__ double lu_logdet(double* A, int ld, int n, int* piv, int* sint, doubl
       }
       __syncthreads();
     }
-    const double pv = aj[j];
-    for (int r = j + 1 + tid; r < n; r += HQ_THREADS) aj[r] = aj[r] / pv;
+    const double rp = 1.0 / aj[j];
+    for (int r = j + 1 + tid; r < n; r += HQ_THREADS) aj[r] *= rp;
     __syncthreads();
     const int m = n - j - 1;
     for (int idx = tid; idx < m * m; idx += HQ_THREADS) {

@@ -41,7 +41,7 @@ namespace {
 constexpr size_t kAlign = 256;
 
 struct Layout {
-  size_t kin, X, G, logdet, UR, TR, DR, work, stU, stT, stD, Adl, Bdl, acc, tot, series, counters, status, tmp;
+  size_t kin, X, G, logdet, UR, TR, DR, work, stU, stT, stD, Adl, Bdl, acc, tot, series, counters, status, sched, tmp;
   size_t total;
 };
 
@@ -93,6 +93,7 @@ Layout layout(const hq_params& p, int C, int max_series) {
   l.series = take(sizeof(double) * C * HQ_N_OBS * (size_t)(max_series > 0 ? max_series : 1));
   l.counters = take(sizeof(long long) * C * hq::kCounters);
   l.status = take(sizeof(int) * C);
+  l.sched = take(sizeof(int) * (hq::kSchedHeader + C));
   l.tmp = take(sizeof(double) * C);
   l.total = off;
   return l;
@@ -226,6 +227,7 @@ int hq_create(const hq_params* p, int n_chains, int first_chain, int max_series,
   d.series = (double*)(a + l.series);
   d.counters = (long long*)(a + l.counters);
   d.status = (int*)(a + l.status);
+  d.sched = (int*)(a + l.sched);
   e->tmp = (double*)(a + l.tmp);
 
   // kinetic propagators: exp(-dtau K) = E_x (x) E_y with ring factors
@@ -310,11 +312,9 @@ int hq_sweep(hq_engine* e, int n_sweeps, unsigned flags) {
       e->logdet_valid = e->green_valid = true;
     }
     if (do_global) {
-      PhaseTimer pt(e, 2, d.n);
-      for (int i = 0; i < d.n; ++i) {
-        rc = cuda_check(e, hq::launch_global_move(d, i, sw, e->stream), "global_move launch");
-        if (rc) return rc;
-      }
+      PhaseTimer pt(e, 2, 1);
+      rc = cuda_check(e, hq::launch_global_phase(d, sw, e->stream), "global_phase launch");
+      if (rc) return rc;
       e->stack_valid = false;
       e->green_valid = false;  // log|det M| is kept current by the accepted moves
     }
@@ -371,6 +371,7 @@ int hq_get_observables(hq_engine* e, hq_obs* out) {
   std::vector<double> tot(C * hq::kTotSlots), ld(C);
   std::vector<long long> cnt(C * hq::kCounters);
   std::vector<int> st(C);
+  int aborted = 0;
   int rc = e->logdet_valid ? HQ_OK : ensure_state(e);
   if (rc) return rc;
   rc = cuda_check(e, cudaMemcpyAsync(tot.data(), e->d.tot, tot.size() * sizeof(double), cudaMemcpyDeviceToHost,
@@ -381,6 +382,8 @@ int hq_get_observables(hq_engine* e, hq_obs* out) {
                                                cudaMemcpyDeviceToHost, e->stream), "status copy");
   rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(ld.data(), e->d.logdet, ld.size() * sizeof(double),
                                                cudaMemcpyDeviceToHost, e->stream), "logdet copy");
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(&aborted, e->d.sched + 1, sizeof(int), cudaMemcpyDeviceToHost,
+                                               e->stream), "abort flag copy");
   rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "obs sync");
   if (rc) return rc;
   for (size_t c = 0; c < C; ++c) {
@@ -401,7 +404,7 @@ int hq_get_observables(hq_engine* e, hq_obs* out) {
     o.x2 = ns > 0 ? t[hq::TOT_X2] / ns : NAN;
     o.max_wrap_error = t[hq::TOT_WRAP];
     o.logdet = ld[c];
-    o.status = st[c];
+    o.status = aborted ? HQ_ETIMEOUT : st[c];
     out[c] = o;
   }
   return HQ_OK;
@@ -579,9 +582,15 @@ int hq_get_timing(hq_engine* e, double* ms, int64_t* launches) {
   return HQ_OK;
 }
 
-double hq_fp64_peak_tflops(int reps, void* stream) {
+int hq_get_section_cycles(uint64_t* out, int n) {
+  if (!out || n < 0) return HQ_EINVAL;
+  return hq::section_cycles((unsigned long long*)out, n);
+}
+
+double hq_fp64_peak_tflops(int kind, int reps, void* stream) {
   if (reps < 1) reps = 1;
-  return hq::fp64_probe_tflops(reps, (cudaStream_t)stream);
+  if (kind != HQ_PROBE_DFMA && kind != HQ_PROBE_DMMA) return -1.0;
+  return hq::fp64_probe_tflops(kind, reps, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -13,6 +13,9 @@ constexpr int kWorkMats = 7;   // per-chain N x N work matrices
 constexpr int kAccSlots = 8;   // per-chain per-sweep accumulators
 constexpr int kTotSlots = 16;  // per-chain running totals
 constexpr int kCounters = 4;   // local proposed / accepted, global proposed / accepted
+constexpr int kSchedHeader = 32;  // block-move task queue: counter, abort flag, then progress[C]
+constexpr int kWorkersPerSm = 2;
+constexpr unsigned long long kWaitLimitNs = 30ull * 1000000000ull;  // bounded wait of a task
 
 // accumulator slots (per sweep)
 enum { ACC_DENSITY = 0, ACC_DOCC = 1, ACC_SCDW = 2, ACC_COUNT = 3, ACC_WRAP = 4 };
@@ -46,6 +49,7 @@ struct Dev {
   double* series;     // [C][HQ_N_OBS][max_series]
   long long* counters;  // [C][kCounters]
   int* status;        // [C]
+  int* sched;         // [kSchedHeader + C] block-move task queue
 };
 
 size_t smem_bytes(const Dev& d);
@@ -53,12 +57,13 @@ size_t smem_bytes(const Dev& d);
 // Launchers (asynchronous on the stream).  Return cudaGetLastError().
 cudaError_t launch_stack_build(const Dev& d, cudaStream_t s);
 cudaError_t launch_local_chunk(const Dev& d, int s0, int s1, uint32_t sweep, int measure, cudaStream_t s);
-cudaError_t launch_global_move(const Dev& d, int site, uint32_t sweep, cudaStream_t s);
+cudaError_t launch_global_phase(const Dev& d, uint32_t sweep, cudaStream_t s);
 cudaError_t launch_sweep_end(const Dev& d, int series_slot, int measured, cudaStream_t s);
 cudaError_t launch_reset_acc(const Dev& d, cudaStream_t s);
 cudaError_t launch_log_weight(const Dev& d, double* out_logw, cudaStream_t s);
 cudaError_t launch_proposals(uint32_t key0, uint32_t key1, uint32_t chain, uint32_t sweep, uint32_t tag,
                              const uint32_t* events, int n, double* u1, double* u2, cudaStream_t s);
-double fp64_probe_tflops(int reps, cudaStream_t s);
+double fp64_probe_tflops(int kind, int reps, cudaStream_t s);
+int section_cycles(unsigned long long* out, int n);
 
 }  // namespace hq

@@ -16,14 +16,28 @@
 
 namespace hq {
 
+int section_cycles(unsigned long long* out, int n) {
+#ifdef HQ_SECTION_TIMING
+  if (n > SEC_COUNT) n = SEC_COUNT;
+  if (cudaMemcpyFromSymbol(out, g_section_cycles, sizeof(unsigned long long) * n) != cudaSuccess) return -1;
+  unsigned long long zero[SEC_COUNT] = {0};
+  cudaMemcpyToSymbol(g_section_cycles, zero, sizeof(zero));
+  return n;
+#else
+  (void)out;
+  (void)n;
+  return 0;
+#endif
+}
+
 struct Smem {
   double *ex, *exi, *ey, *eyi;
-  double *dl, *u2, *xn, *dlt, *es, *dcorr, *tau, *vn1, *vn2, *vs, *dv;
+  double *dl, *u2, *xn, *dlt, *es, *dcorr, *tau, *norm2, *rinv, *vs, *dv;
   double *red, *scal;
   int *perm, *piv, *sint;
 };
 
-static constexpr int kSmemVecs = 11;
+static constexpr int kSmemVecs = 12;  // vs takes two
 
 __host__ __device__ inline size_t smem_layout_bytes(int nx, int ny, int n) {
   return (size_t)(2 * nx * nx + 2 * ny * ny + kSmemVecs * n + 32 + 16) * sizeof(double) +
@@ -47,9 +61,9 @@ __device__ inline Smem carve(const Dev& d, double* base) {
   s.es = p; p += n;
   s.dcorr = p; p += n;
   s.tau = p; p += n;
-  s.vn1 = p; p += n;
-  s.vn2 = p; p += n;
-  s.vs = p; p += n;
+  s.norm2 = p; p += n;
+  s.rinv = p; p += n;
+  s.vs = p; p += 2 * n;
   s.dv = p; p += n;
   s.red = p; p += 32;
   s.scal = p; p += 16;
@@ -88,7 +102,8 @@ __device__ double udv_top_down(const Dev& d, int c, const Smem& sm, const double
   double* U = chain_work(d, c, WK_U);
   double* Tc = chain_work(d, c, WK_T);
   double* Tn = chain_work(d, c, WK_T2);
-  const QrScratch qs{sm.tau, sm.vn1, sm.vn2, sm.vs, sm.perm, sm.sint};
+  double* Q = chain_work(d, c, WK_M1);
+  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint};
   int hi = L, lo = ((L - 1) / nw) * nw;
   bool first = true;
   while (true) {
@@ -96,18 +111,30 @@ __device__ double udv_top_down(const Dev& d, int c, const Smem& sm, const double
     else copy_scale_cols(P, U, n, n, sm.dv);
     __syncthreads();
     for (int s = hi - 1; s >= lo; --s) {
+      HQ_TIC(dl);
       for (int r = threadIdx.x; r < n; r += HQ_THREADS) {
         double x = X[(size_t)s * n + r];
         if (r == site) x = x + dx;
         sm.dl[r] = exp(-d.dtau * (d.g * x - d.mu));
       }
-      kin_rows<LMAX>(P, n, n, sm.ex, sm.ey, d.nx, d.ny);
-      scale_rows(P, n, n, sm.dl);
-      __syncthreads();
+      HQ_TOC(dl, SEC_DL);
+      HQ_TIC(kin);
+      // B_s^T P = exp(-dtau V_s) exp(-dtau K) P (the scaling reads dl after kin_rows' barrier)
+      kin_rows<LMAX, KIN_SCALE_AFTER>(P, n, n, sm.ex, sm.ey, d.nx, d.ny, sm.dl);
+      HQ_TOC(kin, SEC_KIN);
     }
-    qr_pivoted(P, n, n, qs);
-    form_q(P, n, n, U, qs);
-    t_update(P, n, n, qs, sm.dv, first ? nullptr : Tc, Tn);
+    HQ_TIC(pp);
+    prepivot(P, Q, n, n, qs, sm.norm2);
+    HQ_TOC(pp, SEC_PREPIVOT);
+    HQ_TIC(qr);
+    qr_householder(Q, n, n, qs);
+    HQ_TOC(qr, SEC_QR);
+    HQ_TIC(fq);
+    form_q(Q, n, n, U, qs);
+    HQ_TOC(fq, SEC_FORMQ);
+    HQ_TIC(tu);
+    t_update(Q, n, n, qs, sm.dv, first ? nullptr : Tc, Tn);
+    HQ_TOC(tu, SEC_TUPD);
     double* t = Tc; Tc = Tn; Tn = t;
     if (store && lo > 0) {
       const size_t b = (size_t)c * d.n_bound + (lo / nw - 1);
@@ -122,6 +149,7 @@ __device__ double udv_top_down(const Dev& d, int c, const Smem& sm, const double
     lo -= nw;
   }
   // I + U D T = U Db (Db^-1 U^T + Ds T):  log|det| = sum log Db + log|det A|
+  HQ_TIC(ld);
   double* A = chain_work(d, c, WK_M1);
   double* Y = chain_work(d, c, WK_M2);
   for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
@@ -145,6 +173,7 @@ __device__ double udv_top_down(const Dev& d, int c, const Smem& sm, const double
     }
     __syncthreads();
   }
+  HQ_TOC(ld, SEC_LOGDET);
   return lb + la;
 }
 
@@ -269,6 +298,7 @@ local_chunk_kernel(Dev d, int s0, int s1, uint32_t sweep, int measure) {
   long long n_acc = 0;
 
   for (int s = s0; s < s1; ++s) {
+    HQ_TIC(pp);
     // Every proposal of this slice depends only on its own site's field and on the
     // neighbouring slices, so the random numbers, dX, delta = exp(-dtau g dX) - 1 and
     // exp(-dtau dS_ph) are prepared in parallel; only the ratio needs the running G.
@@ -291,6 +321,8 @@ local_chunk_kernel(Dev d, int s0, int s1, uint32_t sweep, int measure) {
       sm.dcorr[i] = 0.0;
     }
     __syncthreads();
+    HQ_TOC(pp, SEC_PROP_PREP);
+    HQ_TIC(seq);
     int kk = 0;
     for (int i = 0; i < n; ++i) {
       const int slot = i & 1;
@@ -354,6 +386,8 @@ local_chunk_kernel(Dev d, int s0, int s1, uint32_t sweep, int measure) {
         G[(size_t)col * n + r] = v;
       }
     }
+    HQ_TOC(seq, SEC_PROP_SEQ);
+    HQ_TIC(wr);
     // wrap: G_l = exp(-dtau K) D_l G_{l-1} D_l^-1 exp(dtau K), D_l = exp(-dtau V_l)
     for (int r = threadIdx.x; r < n; r += HQ_THREADS) sm.dl[r] = exp(-d.dtau * (d.g * X[(size_t)s * n + r] - d.mu));
     __syncthreads();
@@ -362,8 +396,9 @@ local_chunk_kernel(Dev d, int s0, int s1, uint32_t sweep, int measure) {
       G[(size_t)col * n + r] = (sm.dl[r] * G[(size_t)col * n + r]) / sm.dl[col];
     }
     __syncthreads();
-    kin_rows<LMAX>(G, n, n, sm.ex, sm.ey, d.nx, d.ny);
+    kin_rows<LMAX, KIN_PLAIN>(G, n, n, sm.ex, sm.ey, d.nx, d.ny);
     kin_cols<LMAX>(G, n, n, sm.exi, sm.eyi, d.nx, d.ny);
+    HQ_TOC(wr, SEC_WRAP);
   }
   if (threadIdx.x == 0) {
     long long* cnt = d.counters + (size_t)c * kCounters;
@@ -378,6 +413,7 @@ local_chunk_kernel(Dev d, int s0, int s1, uint32_t sweep, int measure) {
   double* P = chain_work(d, c, WK_P);
   double* T2 = chain_work(d, c, WK_T2);
   double* Gf = chain_work(d, c, WK_U);
+  HQ_TIC(rp);
   const bool first = (s0 == 0);
   if (first) set_identity(P, n, n);
   else copy_scale_cols(P, UR, n, n, DR);
@@ -385,16 +421,21 @@ local_chunk_kernel(Dev d, int s0, int s1, uint32_t sweep, int measure) {
   for (int s = s0; s < s1; ++s) {
     for (int r = threadIdx.x; r < n; r += HQ_THREADS) sm.dl[r] = exp(-d.dtau * (d.g * X[(size_t)s * n + r] - d.mu));
     __syncthreads();
-    scale_rows(P, n, n, sm.dl);
-    __syncthreads();
-    kin_rows<LMAX>(P, n, n, sm.ex, sm.ey, d.nx, d.ny);
+    // B_s P = exp(-dtau K) exp(-dtau V_s) P
+    kin_rows<LMAX, KIN_SCALE_BEFORE>(P, n, n, sm.ex, sm.ey, d.nx, d.ny, sm.dl);
   }
-  const QrScratch qs{sm.tau, sm.vn1, sm.vn2, sm.vs, sm.perm, sm.sint};
-  qr_pivoted(P, n, n, qs);
-  form_q(P, n, n, UR, qs);
-  t_update(P, n, n, qs, DR, first ? nullptr : TR, T2);
+  HQ_TOC(rp, SEC_RESTAB_PROD);
+  HQ_TIC(rq);
+  double* Q = chain_work(d, c, WK_M1);
+  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint};
+  prepivot(P, Q, n, n, qs, sm.norm2);
+  qr_householder(Q, n, n, qs);
+  form_q(Q, n, n, UR, qs);
+  t_update(Q, n, n, qs, DR, first ? nullptr : TR, T2);
   copy_mat(TR, T2, n, n);
   __syncthreads();
+  HQ_TOC(rq, SEC_RESTAB_QR);
+  HQ_TIC(rg);
   const double ld = green_two_sided(d, c, sm, s1, Gf);
   double err = 0.0, bad = 0.0;
   for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
@@ -413,17 +454,19 @@ local_chunk_kernel(Dev d, int s0, int s1, uint32_t sweep, int measure) {
     if (bad != 0.0) d.status[c] = HQ_ENAN;
   }
   __syncthreads();
+  HQ_TOC(rg, SEC_RESTAB_GREEN);
+  HQ_TIC(ms);
   if (measure) measure_green(d, c, sm, G);
+  HQ_TOC(ms, SEC_MEASURE);
 }
 
+// One block move X(site, .) += dX of chain c: Philox draw, dtau dS_ph, the full stabilised
+// log|det M(X')| and the Metropolis decision (all threads of the CTA).
 template <int LMAX>
-__global__ void __launch_bounds__(HQ_THREADS) global_move_kernel(Dev d, int site, uint32_t sweep) {
-  extern __shared__ double smraw[];
-  const int c = blockIdx.x;
+__device__ void block_move(const Dev& d, const Smem& sm, int c, int site, uint32_t sweep) {
   const int n = d.n, L = d.L;
-  const Smem sm = carve(d, smraw);
-  load_kinetic(d, sm);
   double* X = d.X + (size_t)c * L * n;
+  HQ_TIC(mv);
   if (threadIdx.x == 0) {
     double u1, u2;
     proposal_uniforms(d.key0, d.key1, (uint32_t)site, sweep, (uint32_t)(d.first_chain + c), 1u, u1, u2);
@@ -439,6 +482,7 @@ __global__ void __launch_bounds__(HQ_THREADS) global_move_kernel(Dev d, int site
   }
   a = block_sum(a, sm.red);
   const double dS = 0.5 * d.dtau * d.mass * (d.omega * d.omega) * a;
+  HQ_TOC(mv, SEC_MOVE);
   const double ld_new = udv_top_down<LMAX>(d, c, sm, X, site, dx, false, nullptr);
   if (threadIdx.x == 0) {
     const double arg = 2.0 * (ld_new - d.logdet[c]) - dS;
@@ -456,6 +500,71 @@ __global__ void __launch_bounds__(HQ_THREADS) global_move_kernel(Dev d, int site
   __syncthreads();
   if (sm.sint[4]) {
     for (int s = threadIdx.x; s < L; s += HQ_THREADS) X[(size_t)s * n + site] = X[(size_t)s * n + site] + dx;
+  }
+}
+
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// The block-move phase of a sweep as one persistent launch.  Task t = site * C + chain
+// (every chain's N moves in site order).  Workers take tasks from an atomic counter; a task
+// waits until its chain has finished the previous site (progress flag written with a
+// release fence after the move, read before the move with an acquire fence).  Faster SMs
+// take more tasks, so the load balances across SMs whatever C is.  The wait is bounded:
+// after kWaitLimitNs the worker raises the abort flag, marks the chain HQ_ETIMEOUT and
+// every worker stops taking tasks.  sched = [counter, abort, ..., progress[C] at
+// kSchedHeader], zeroed before the launch.
+template <int LMAX>
+__global__ void __launch_bounds__(HQ_THREADS) global_phase_kernel(Dev d, uint32_t sweep) {
+  extern __shared__ double smraw[];
+  __shared__ int s_task;
+  const Smem sm = carve(d, smraw);
+  load_kinetic(d, sm);
+  const int C = d.n_chains, ntask = d.n * C;
+  int* counter = d.sched;
+  volatile int* abort_flag = d.sched + 1;
+  volatile int* progress = d.sched + kSchedHeader;
+  for (;;) {
+    HQ_TIC(wait);
+    if (threadIdx.x == 0) {
+      int t = -1;
+      if (*abort_flag == 0) {
+        t = atomicAdd(counter, 1);
+        if (t < ntask) {
+          const int site = t / C, c = t % C;
+          if (progress[c] < site) {
+            const unsigned long long t0 = global_timer_ns();
+            unsigned ns = 32;
+            while (progress[c] < site) {
+              if (*abort_flag != 0 || global_timer_ns() - t0 > kWaitLimitNs) {
+                // the phase did not complete: every chain's state is suspect
+                if (atomicExch((int*)abort_flag, 1) == 0)
+                  for (int q = 0; q < C; ++q) d.status[q] = HQ_ETIMEOUT;
+                t = -1;
+                break;
+              }
+              __nanosleep(ns);
+              if (ns < 2048) ns *= 2;
+            }
+          }
+        }
+      }
+      s_task = t;
+    }
+    __syncthreads();
+    HQ_TOC(wait, SEC_WAIT);
+    const int t = s_task;
+    if (t < 0 || t >= ntask) break;
+    __threadfence();  // acquire: the previous move of this chain (possibly on another SM)
+    block_move<LMAX>(d, sm, t % C, t / C, sweep);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();  // release the move before publishing it
+      atomicExch((int*)&progress[t % C], t / C + 1);
+    }
   }
 }
 
@@ -567,9 +676,34 @@ cudaError_t launch_local_chunk(const Dev& d, int s0, int s1, uint32_t sweep, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_global_move(const Dev& d, int site, uint32_t sweep, cudaStream_t s) {
-  HQ_DISPATCH(global_move_kernel, d, s, d, site, sweep);
+template <int LMAX>
+static cudaError_t launch_phase(const Dev& d, uint32_t sweep, cudaStream_t s) {
+  const size_t sb = smem_bytes(d);
+  int dev = 0, sms = 0, occ = 0;
+  cudaError_t st = cudaGetDevice(&dev);
+  if (st == cudaSuccess) st = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (st == cudaSuccess)
+    st = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, global_phase_kernel<LMAX>, HQ_THREADS, sb);
+  if (st != cudaSuccess) return st;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  // every worker must be resident (a waiting worker relies on the owner of the previous
+  // task running), so the grid never exceeds one wave
+  const int ntask = d.n * d.n_chains;
+  int workers = sms * (occ < kWorkersPerSm ? occ : kWorkersPerSm);
+  if (workers > ntask) workers = ntask;
+  st = cudaMemsetAsync(d.sched, 0, sizeof(int) * (kSchedHeader + d.n_chains), s);
+  if (st != cudaSuccess) return st;
+  global_phase_kernel<LMAX><<<workers, HQ_THREADS, sb, s>>>(d, sweep);
   return cudaGetLastError();
+}
+
+cudaError_t launch_global_phase(const Dev& d, uint32_t sweep, cudaStream_t s) {
+  switch (lmax_of(d.nx, d.ny)) {
+    case 2: return launch_phase<2>(d, sweep, s);
+    case 4: return launch_phase<4>(d, sweep, s);
+    case 8: return launch_phase<8>(d, sweep, s);
+    default: return launch_phase<16>(d, sweep, s);
+  }
 }
 
 cudaError_t launch_sweep_end(const Dev& d, int slot, int measured, cudaStream_t s) {
@@ -605,7 +739,26 @@ __global__ void fp64_probe_kernel(double* out, double b, double c) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
 }
 
-double fp64_probe_tflops(int reps, cudaStream_t s) {
+__global__ void dmma_probe_kernel(double* out, double av, double bv) {
+  double c[4][2];
+  for (int j = 0; j < 4; ++j) {
+    c[j][0] = threadIdx.x;
+    c[j][1] = j;
+  }
+  const double a = av + threadIdx.x * 1e-3, b = bv;
+  for (int it = 0; it < HQ_PROBE_ITERS / 2; ++it) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                   : "+d"(c[j][0]), "+d"(c[j][1])
+                   : "d"(a), "d"(b));
+  }
+  double s = 0.0;
+  for (int j = 0; j < 4; ++j) s += c[j][0] + c[j][1];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+double fp64_probe_tflops(int kind, int reps, cudaStream_t s) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1.0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1.0;
@@ -615,9 +768,13 @@ double fp64_probe_tflops(int reps, cudaStream_t s) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  fp64_probe_kernel<<<grid, block, 0, s>>>(out, 0.999, 1e-3);
+  auto launch = [&]() {
+    if (kind == 1) dmma_probe_kernel<<<grid, block, 0, s>>>(out, 0.5, 0.25);
+    else fp64_probe_kernel<<<grid, block, 0, s>>>(out, 0.999, 1e-3);
+  };
+  launch();
   cudaEventRecord(e0, s);
-  for (int r = 0; r < reps; ++r) fp64_probe_kernel<<<grid, block, 0, s>>>(out, 0.999, 1e-3);
+  for (int r = 0; r < reps; ++r) launch();
   cudaEventRecord(e1, s);
   cudaEventSynchronize(e1);
   float ms = 0.f;
@@ -627,7 +784,10 @@ double fp64_probe_tflops(int reps, cudaStream_t s) {
   cudaFreeAsync(out, s);
   cudaStreamSynchronize(s);
   if (cudaGetLastError() != cudaSuccess || ms <= 0.f) return -1.0;
-  const double flops = (double)reps * grid * block * HQ_PROBE_ITERS * 8 * 2;
+  // DFMA: 8 FMAs per thread per iteration; DMMA: 4 m8n8k4 MMAs (512 flops) per warp per
+  // iteration over HQ_PROBE_ITERS / 2 iterations.
+  const double flops = kind == 1 ? (double)reps * grid * (block / 32) * (HQ_PROBE_ITERS / 2) * 4 * 512.0
+                                 : (double)reps * grid * block * HQ_PROBE_ITERS * 8 * 2;
   return flops / (ms * 1e-3) / 1e12;
 }
 
