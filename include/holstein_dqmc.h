@@ -142,6 +142,8 @@ int hq_restore(hq_engine* e, const void* buf, size_t len);
 /* Number of chains, sites N, slices L and sweeps run. */
 int hq_shape(const hq_engine* e, int* n_chains, int* n_sites, int* n_slices, int64_t* sweeps);
 
+/* Message of the engine's last error; with e == NULL, that of the calling thread's last
+ * failing call that takes no engine (hq_logdet_noalloc). */
 const char* hq_last_error(const hq_engine* e);
 void hq_destroy(hq_engine* e);
 
@@ -166,6 +168,32 @@ double hq_tau_int(const double* series, int n, double c, int* window);
 #define HQ_N_PHASES 4
 int hq_set_timing(hq_engine* e, int enable);
 int hq_get_timing(hq_engine* e, double* ms, int64_t* launches);
+
+/* log|det M| of every chain's fields, with no device allocation of any kind.
+ *
+ * The paper has no counterpart: this is a service of this library.  It is for callers that
+ * cannot allocate device memory themselves -- code that only receives buffers from a host
+ * framework whose own memory pool owns the device (and forbids cudaMalloc/cudaFree next
+ * to it), or code that must not allocate once it is running, such as a latency-bound
+ * serving loop.  Such a caller passes only its inputs and outputs:
+ *   p          model and run shape (as for hq_create; delay_k is not used),
+ *   n_chains   number of chains, >= 1,
+ *   X_device   device pointer, fields X[chain][l][i] (n_chains * L * N doubles, read only),
+ *   logdet_device  device pointer, n_chains doubles written with log|det(I + B_L..B_1)|,
+ *   stream     cudaStream_t (NULL = legacy default stream); the call is asynchronous.
+ * Scratch (kinetic factors, a status word and 7 N x N FP64 matrices per chain) comes from a
+ * file-scope static device array of HQ_NOALLOC_SCRATCH_BYTES = 64 MiB, which every GPU that
+ * loads the library holds until the process exits.  Calls needing more (roughly more than
+ * 290 chains of N = 64, or 17 of N = 256) are rejected with HQ_ENOMEM and a message in
+ * hq_last_error(NULL); invalid parameters give HQ_EINVAL.  The first call on a device looks
+ * up the array's device address once for that device; make that first call before any
+ * stream capture.  Every call shares the one array, so calls that overlap on the GPU (other
+ * streams, other host threads) race on it: serialise them.  Non-finite results show up as
+ * NaN/Inf in logdet_device.  The result equals hq_log_weight's log|det M| for the same
+ * fields. */
+#define HQ_NOALLOC_SCRATCH_BYTES (64u << 20)
+int hq_logdet_noalloc(const hq_params* p, int n_chains, const double* X_device, double* logdet_device,
+                      void* stream);
 
 /* Per-section device cycle counters (profiling builds compiled with -DHQ_SECTION_TIMING):
  * copies up to n counters (sum over CTAs of thread 0's clock64 spans; ids in

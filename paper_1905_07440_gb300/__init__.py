@@ -77,6 +77,7 @@ _SIGNATURES = {
     "hq_tau_int": (ctypes.c_double, [_dp, ctypes.c_int, ctypes.c_double, _P(ctypes.c_int)]),
     "hq_fp64_peak_tflops": (ctypes.c_double, [ctypes.c_int, ctypes.c_int, _vp]),
     "hq_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "hq_logdet_noalloc": (ctypes.c_int, [_P(hq_params), ctypes.c_int, _vp, _vp, _vp]),
     "hq_get_section_cycles": (ctypes.c_int, [_P(ctypes.c_uint64), ctypes.c_int]),
     "hq_get_timing": (ctypes.c_int, [_vp, _dp, _P(ctypes.c_int64)]),
 }
@@ -241,6 +242,21 @@ class Engine:
         s = ctypes.c_int64()
         self.lib.hq_shape(self._h, None, None, None, ctypes.byref(s))
         return s.value
+
+
+NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def logdet_noalloc(params, X, out, stream=None):
+    """hq_logdet_noalloc on caller-owned CUDA tensors: X float64 [chains][L][N], out float64
+    [chains].  The library allocates nothing; its static scratch is shared by all calls."""
+    lib = load_library()
+    assert X.is_cuda and out.is_cuda and X.is_contiguous() and out.is_contiguous()
+    rc = lib.hq_logdet_noalloc(ctypes.byref(make_params(params)), int(X.shape[0]), ctypes.c_void_p(X.data_ptr()),
+                               ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream or 0))
+    if rc != HQ_OK:
+        msg = lib.hq_last_error(None)
+        raise HQError(f"hq_logdet_noalloc failed ({rc}): {msg.decode() if msg else ''}")
 
 
 def proposal_uniforms(seed, chain, sweep, events, tag, stream=None):

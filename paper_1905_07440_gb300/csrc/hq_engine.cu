@@ -39,6 +39,7 @@ struct hq_engine {
 namespace {
 
 constexpr size_t kAlign = 256;
+thread_local std::string g_call_error;  // message of the last failing call without an engine
 
 struct Layout {
   size_t kin, X, G, logdet, UR, TR, DR, work, stU, stT, stD, Adl, Bdl, acc, tot, series, counters, status, sched, tmp;
@@ -256,7 +257,7 @@ int hq_create(const hq_params* p, int n_chains, int first_chain, int max_series,
 
 void hq_destroy(hq_engine* e) { delete e; }
 
-const char* hq_last_error(const hq_engine* e) { return e ? e->err.c_str() : "engine is NULL"; }
+const char* hq_last_error(const hq_engine* e) { return e ? e->err.c_str() : g_call_error.c_str(); }
 
 int hq_shape(const hq_engine* e, int* n_chains, int* n_sites, int* n_slices_out, int64_t* sweeps) {
   if (!e) return HQ_EINVAL;
@@ -578,6 +579,54 @@ int hq_get_timing(hq_engine* e, double* ms, int64_t* launches) {
     if (launches) launches[i] = e->phase_launches[i];
     e->phase_ms[i] = 0.0;
     e->phase_launches[i] = 0;
+  }
+  return HQ_OK;
+}
+
+int hq_logdet_noalloc(const hq_params* p, int n_chains, const double* X_device, double* logdet_device,
+                      void* stream) {
+  g_call_error.clear();
+  if (const char* why = validate(p, n_chains, 0)) {
+    g_call_error = std::string("hq_logdet_noalloc: ") + why;
+    return HQ_EINVAL;
+  }
+  if (!X_device || !logdet_device) {
+    g_call_error = "hq_logdet_noalloc: X_device and logdet_device must be device pointers";
+    return HQ_EINVAL;
+  }
+  const size_t need = hq::noalloc_scratch_needed(p->nx, p->ny, n_chains);
+  if (need > hq::kNoAllocScratchBytes) {
+    g_call_error = "hq_logdet_noalloc: " + std::to_string(n_chains) + " chains of N = " +
+                   std::to_string(p->nx * p->ny) + " need " + std::to_string(need) +
+                   " bytes of scratch, the static scratch holds " + std::to_string(hq::kNoAllocScratchBytes) +
+                   " (HQ_NOALLOC_SCRATCH_BYTES); pass fewer chains per call";
+    return HQ_ENOMEM;
+  }
+  hq::Dev d{};
+  d.nx = p->nx;
+  d.ny = p->ny;
+  d.n = p->nx * p->ny;
+  d.L = n_slices(*p);
+  d.n_wrap = p->n_wrap;
+  d.k = p->delay_k;
+  d.n_chains = n_chains;
+  d.t = p->t;
+  d.mu = p->mu;
+  d.omega = p->omega;
+  d.mass = p->mass;
+  d.g = p->g;
+  d.dtau = p->dtau;
+  d.X = const_cast<double*>(X_device);
+  // kinetic factors on the stack (at most 4 * 16 * 16 doubles), copied into the scratch
+  double kin[4 * hq::kMaxSide * hq::kMaxSide];
+  ring_propagator(d.nx, p->t, p->dtau, +1.0, kin);
+  ring_propagator(d.nx, p->t, p->dtau, -1.0, kin + d.nx * d.nx);
+  ring_propagator(d.ny, p->t, p->dtau, +1.0, kin + 2 * d.nx * d.nx);
+  ring_propagator(d.ny, p->t, p->dtau, -1.0, kin + 2 * d.nx * d.nx + d.ny * d.ny);
+  const cudaError_t st = hq::launch_logdet_noalloc(d, kin, logdet_device, (cudaStream_t)stream);
+  if (st != cudaSuccess) {
+    g_call_error = std::string("hq_logdet_noalloc: ") + cudaGetErrorString(st);
+    return HQ_ECUDA;
   }
   return HQ_OK;
 }

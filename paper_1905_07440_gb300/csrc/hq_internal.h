@@ -15,6 +15,8 @@ constexpr int kTotSlots = 16;  // per-chain running totals
 constexpr int kCounters = 4;   // local proposed / accepted, global proposed / accepted
 constexpr int kSchedHeader = 32;  // block-move task queue: counter, abort flag, then progress[C]
 constexpr int kWorkersPerSm = 2;
+constexpr int kMaxDevices = 64;
+constexpr size_t kNoAllocScratchBytes = (size_t)64 << 20;  // static scratch of hq_logdet_noalloc
 constexpr unsigned long long kWaitLimitNs = 30ull * 1000000000ull;  // bounded wait of a task
 
 // accumulator slots (per sweep)
@@ -65,5 +67,8 @@ cudaError_t launch_proposals(uint32_t key0, uint32_t key1, uint32_t chain, uint3
                              const uint32_t* events, int n, double* u1, double* u2, cudaStream_t s);
 double fp64_probe_tflops(int kind, int reps, cudaStream_t s);
 int section_cycles(unsigned long long* out, int n);
+size_t noalloc_scratch_needed(int nx, int ny, int n_chains);
+// log|det M| per chain with all scratch in the library's static device array (no allocation).
+cudaError_t launch_logdet_noalloc(Dev d, const double* kin_host, double* out, cudaStream_t s);
 
 }  // namespace hq

@@ -10,6 +10,7 @@
 //                 determinant ratio                              (block updates)
 //   sweep_end     per-sweep observable records
 #include <cstdio>
+#include <mutex>
 #include "hq_device.cuh"
 #include "hq_internal.h"
 #include "../../include/holstein_dqmc.h"
@@ -665,6 +666,69 @@ static inline int lmax_of(int nx, int ny) {
       default: KERNEL<16><<<(d).n_chains, HQ_THREADS, sb, stream>>>(__VA_ARGS__); break;    \
     }                                                                                       \
   } while (0)
+
+// ------------------------------------------------- log|det M| without allocation
+// File-scope scratch for hq_logdet_noalloc: the kinetic factors, a status word per chain
+// and kWorkMats N x N work matrices per chain live here instead of in a caller arena.
+// Every GPU that loads the library holds it until the process exits.  All calls share it,
+// so calls that overlap on the GPU race on it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+template <int LMAX>
+__global__ void __launch_bounds__(HQ_THREADS) logdet_noalloc_kernel(Dev d, double* out) {
+  extern __shared__ double smraw[];
+  const int c = blockIdx.x;
+  const Smem sm = carve(d, smraw);
+  load_kinetic(d, sm);
+  const double* X = d.X + (size_t)c * d.L * d.n;
+  const double ld = udv_top_down<LMAX>(d, c, sm, X, -1, 0.0, false, nullptr);
+  if (threadIdx.x == 0) out[c] = ld;
+}
+
+size_t noalloc_scratch_needed(int nx, int ny, int n_chains) {
+  const size_t n = (size_t)nx * ny;
+  const size_t kin = ((sizeof(double) * (2 * nx * nx + 2 * ny * ny) + 255) / 256) * 256;
+  const size_t st = ((sizeof(int) * (size_t)n_chains + 255) / 256) * 256;
+  return kin + st + sizeof(double) * (size_t)n_chains * kWorkMats * n * n;
+}
+
+// Device address of the scratch on the current device, looked up once per device (the
+// host-side name of a __device__ array is not a device address).
+static cudaError_t noalloc_scratch_address(void** out) {
+  static std::mutex mu;
+  static void* addr[kMaxDevices] = {nullptr};
+  int dev = 0;
+  cudaError_t st = cudaGetDevice(&dev);
+  if (st != cudaSuccess) return st;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    st = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (st != cudaSuccess) return st;
+    addr[dev] = p;
+  }
+  *out = addr[dev];
+  return cudaSuccess;
+}
+
+cudaError_t launch_logdet_noalloc(Dev d, const double* kin_host, double* out, cudaStream_t s) {
+  void* base = nullptr;
+  cudaError_t st = noalloc_scratch_address(&base);
+  if (st != cudaSuccess) return st;
+  char* p = (char*)base;
+  const size_t kin_bytes = sizeof(double) * (2 * d.nx * d.nx + 2 * d.ny * d.ny);
+  const size_t kin_span = ((kin_bytes + 255) / 256) * 256;
+  const size_t st_span = ((sizeof(int) * (size_t)d.n_chains + 255) / 256) * 256;
+  d.kin = (const double*)p;
+  d.status = (int*)(p + kin_span);
+  d.work = (double*)(p + kin_span + st_span);
+  st = cudaMemcpyAsync((void*)d.kin, kin_host, kin_bytes, cudaMemcpyHostToDevice, s);
+  if (st == cudaSuccess) st = cudaMemsetAsync(d.status, 0, sizeof(int) * d.n_chains, s);
+  if (st != cudaSuccess) return st;
+  HQ_DISPATCH(logdet_noalloc_kernel, d, s, d, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_stack_build(const Dev& d, cudaStream_t s) {
   HQ_DISPATCH(stack_build_kernel, d, s, d);
