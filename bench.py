@@ -191,13 +191,16 @@ def run_ours(args):
     import torch
     import paper_1905_07440_gb300 as hq
 
+    from paper_1905_07440_gb300 import replicas
+
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group(backend="nccl", device_id=dev)
     stream = torch.cuda.Stream(device=dev)
-    first = rank * chains
+    # weak scaling: every rank runs `chains` chains, with globally unique Philox chain ids
+    first, _ = replicas.shard(chains * world, world, rank)
     X0 = workloads.initial_fields(params, chains, seed=workloads.DEFAULT_SEED + first)
 
     with torch.cuda.stream(stream):
@@ -240,11 +243,7 @@ def run_ours(args):
         clk = clocks.stop()
         phases = eng.timing()
         eng.set_timing(False)
-        t_dev = sum(a.elapsed_time(b) for a, b in evs) / 1e3
-        if world > 1:
-            t = torch.tensor([t_dev], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            t_dev = float(t.item())
+        t_dev = replicas.max_over_ranks(sum(a.elapsed_time(b) for a, b in evs) / 1e3, dev)
         value = chains * world * args.steps / t_dev
 
         # ---- end to end through the C ABI with host buffers (pinned), copies timed
@@ -259,11 +258,7 @@ def run_ours(args):
             eng.sweep(1)
             eng.get_fields(Xh)
             obs = eng.observables()
-        t_e2e = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = replicas.max_over_ranks(time.perf_counter() - t0, dev)
         e2e = chains * world * args.steps / t_e2e
         status_ok = all(o["status"] == 0 for o in obs)
 
@@ -289,6 +284,13 @@ def run_ours(args):
     obs_bytes = 104 * chains
     acc_l = sum(o["local_accepted"] for o in obs) / max(1, sum(o["local_proposed"] for o in obs))
     acc_g = sum(o["global_accepted"] for o in obs) / max(1, sum(o["global_proposed"] for o in obs))
+    indep = None
+    tau_path = os.path.join(ROOT, "profiles", f"tau_int_{args.workload}.json")
+    if os.path.exists(tau_path):
+        with open(tau_path) as f:
+            tau = json.load(f)
+        indep = {"unit": "independent samples/s", "tau_source": os.path.relpath(tau_path, ROOT),
+                 **{k: value / (2.0 * v) for k, v in tau["tau_int"].items()}}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_dev * 1e3 / args.steps, "higher_is_better": True,
@@ -306,6 +308,7 @@ def run_ours(args):
                      "flops_per_launch": fl, "ms_per_launch": per_launch_s * 1e3,
                      "share": ms / total_ms if total_ms else None},
         "phases_ms": {k: v[0] for k, v in phases.items()},
+        "indep_samples_per_s": indep,
         "cpu_baseline": cpu,
         "clocks": clk,
         "acceptance": {"local": acc_l, "block": acc_g},
@@ -314,6 +317,40 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_tau(args):
+    """Integrated autocorrelation times of the per-sweep observables on the workload.
+
+    Runs args.warmup sweeps to equilibrate, then args.tau_sweeps measured sweeps of every
+    chain; tau_int of each chain's series (Madras-Sokal window, c = 6) averaged over chains.
+    """
+    import numpy as np
+    import torch
+    import paper_1905_07440_gb300 as hq
+    params, chains, wname = workload_params(args.workload)
+    if args.chains:
+        chains = args.chains
+    S = args.tau_sweeps
+    eng = hq.Engine(params, chains, max_series=args.warmup + S)
+    eng.set_fields(workloads.initial_fields(params, chains))
+    eng.sweep(args.warmup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    eng.sweep(S)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    out = {"workload": wname, "chains": chains, "warmup_sweeps": args.warmup, "sweeps": S,
+           "chain_sweeps_per_s": chains * S / wall, "tau_int": {}, "tau_int_stderr": {}, "mean": {}}
+    for oid, name in ((hq.HQ_OBS_X2, "x2"), (hq.HQ_OBS_DOUBLE_OCC, "double_occ"), (hq.HQ_OBS_SCDW, "s_cdw"),
+                      (hq.HQ_OBS_DENSITY, "density")):
+        ser = eng.series(oid)[:, args.warmup:]
+        taus = np.array([hq.tau_int(ser[c])[0] for c in range(chains)])
+        out["tau_int"][name] = float(taus.mean())
+        out["tau_int_stderr"][name] = float(taus.std(ddof=1) / math.sqrt(chains)) if chains > 1 else None
+        out["mean"][name] = float(ser.mean())
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -358,9 +395,12 @@ def main():
     ap.add_argument("--chains", type=int, default=0, help="override chains per rank (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--peaks", action="store_true", help="print the FP64/FP32 pipe probes and exit")
+    ap.add_argument("--tau-sweeps", type=int, default=0, help="measure tau_int over this many sweeps and exit")
     args = ap.parse_args()
     if args.peaks:
         sys.exit(run_peaks())
+    if args.tau_sweeps:
+        sys.exit(run_tau(args))
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up sweeps", file=sys.stderr)
     sys.exit(run_reference(args) if args.impl == "reference" else run_ours(args))
