@@ -139,6 +139,12 @@ int hq_checkpoint(hq_engine* e, void* buf, size_t* len);
 /* Restore a state written by hq_checkpoint for the same parameters and chain count. */
 int hq_restore(hq_engine* e, const void* buf, size_t len);
 
+/* Block-move algorithm chosen for this parameter set by an FP64 flop model: 0 = every
+ * slice applied through the separable exp(-dtau K) per move, 1 = chunk propagators (the
+ * n_wrap-slice products kept per chain, updated by a rank-n_wrap correction per move and
+ * applied with one GEMM per chunk).  Both give the same determinants up to rounding. */
+int hq_block_move_method(const hq_engine* e);
+
 /* Number of chains, sites N, slices L and sweeps run. */
 int hq_shape(const hq_engine* e, int* n_chains, int* n_sites, int* n_slices, int64_t* sweeps);
 

@@ -69,6 +69,7 @@ _SIGNATURES = {
     "hq_get_series": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _P(ctypes.c_int)]),
     "hq_checkpoint": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_size_t)]),
     "hq_restore": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+    "hq_block_move_method": (ctypes.c_int, [_vp]),
     "hq_shape": (ctypes.c_int, [_vp, _P(ctypes.c_int), _P(ctypes.c_int), _P(ctypes.c_int), _P(ctypes.c_int64)]),
     "hq_last_error": (ctypes.c_char_p, [_vp]),
     "hq_destroy": (None, [_vp]),
@@ -236,6 +237,11 @@ class Engine:
         n = (ctypes.c_int64 * HQ_N_PHASES)()
         self._check(self.lib.hq_get_timing(self._h, _dptr(ms), n), "hq_get_timing")
         return {PHASES[i]: (float(ms[i]), int(n[i])) for i in range(HQ_N_PHASES)}
+
+    @property
+    def block_move_method(self):
+        """0: separable slice applications per move; 1: chunk propagators."""
+        return int(self.lib.hq_block_move_method(self._h))
 
     @property
     def sweeps_done(self):

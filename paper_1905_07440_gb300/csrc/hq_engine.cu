@@ -42,7 +42,8 @@ constexpr size_t kAlign = 256;
 thread_local std::string g_call_error;  // message of the last failing call without an engine
 
 struct Layout {
-  size_t kin, X, G, logdet, UR, TR, DR, work, stU, stT, stD, Adl, Bdl, acc, tot, series, counters, status, sched, tmp;
+  size_t kin, X, G, logdet, UR, TR, DR, work, stU, stT, stD, Adl, Bdl, acc, tot, series, counters, status, sched, tmp,
+      expV, cmat, cbuf, corr;
   size_t total;
 };
 
@@ -96,6 +97,13 @@ Layout layout(const hq_params& p, int C, int max_series) {
   l.status = take(sizeof(int) * C);
   l.sched = take(sizeof(int) * (hq::kSchedHeader + C));
   l.tmp = take(sizeof(double) * C);
+  if (hq::chunk_propagators_pay(p.nx, p.ny, (int)L, p.n_wrap)) {
+    const size_t nch = (L + p.n_wrap - 1) / p.n_wrap;
+    l.expV = take(sizeof(double) * C * L * n);
+    l.cmat = take(sizeof(double) * C * 2 * nch * nn);
+    l.cbuf = take(sizeof(int) * C);
+    l.corr = take(sizeof(double) * C * (2 * n * p.n_wrap + L));
+  }
   l.total = off;
   return l;
 }
@@ -229,6 +237,14 @@ int hq_create(const hq_params* p, int n_chains, int first_chain, int max_series,
   d.counters = (long long*)(a + l.counters);
   d.status = (int*)(a + l.status);
   d.sched = (int*)(a + l.sched);
+  d.use_cm = hq::chunk_propagators_pay(d.nx, d.ny, d.L, d.n_wrap) ? 1 : 0;
+  d.n_chunks = (d.L + d.n_wrap - 1) / d.n_wrap;
+  if (d.use_cm) {
+    d.expV = (double*)(a + l.expV);
+    d.cmat = (double*)(a + l.cmat);
+    d.cbuf = (int*)(a + l.cbuf);
+    d.corr = (double*)(a + l.corr);
+  }
   e->tmp = (double*)(a + l.tmp);
 
   // kinetic propagators: exp(-dtau K) = E_x (x) E_y with ring factors
@@ -258,6 +274,8 @@ int hq_create(const hq_params* p, int n_chains, int first_chain, int max_series,
 void hq_destroy(hq_engine* e) { delete e; }
 
 const char* hq_last_error(const hq_engine* e) { return e ? e->err.c_str() : g_call_error.c_str(); }
+
+int hq_block_move_method(const hq_engine* e) { return e ? e->d.use_cm : HQ_EINVAL; }
 
 int hq_shape(const hq_engine* e, int* n_chains, int* n_sites, int* n_slices_out, int64_t* sweeps) {
   if (!e) return HQ_EINVAL;

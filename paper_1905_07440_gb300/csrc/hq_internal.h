@@ -52,7 +52,26 @@ struct Dev {
   long long* counters;  // [C][kCounters]
   int* status;        // [C]
   int* sched;         // [kSchedHeader + C] block-move task queue
+  // chunk propagators for block moves (used when use_cm != 0)
+  int use_cm, n_chunks;
+  double* expV;       // [C][L][N] exp(-dtau V) of the current fields
+  double* cmat;       // [C][2][n_chunks][N*N] chunk products, current and proposed
+  int* cbuf;          // [C] index of the current buffer
+  double* corr;       // [C][2 N n_wrap + L] rank-n_wrap correction vectors, shifted diagonal
 };
+
+// FP64 flop model of one chunk of a block move: n_wrap separable slice applications versus
+// the chunk-propagator update (rank-m correction vectors, rank-m update, one GEMM).
+inline bool chunk_propagators_pay(int nx, int ny, int L, int n_wrap) {
+  const double n = (double)nx * ny;
+  const int chunks = (L + n_wrap - 1) / n_wrap;
+  const double m = (double)L / chunks;
+  const double slice = 2.0 * n * n * (nx + ny) + n * n;
+  const double vec = 2.0 * n * (nx + ny) + n;
+  const double sep = m * slice;
+  const double cm = 2.0 * n * n * n + 2.0 * m * n * n + m * m * vec + n * n;
+  return cm < 0.9 * sep;
+}
 
 size_t smem_bytes(const Dev& d);
 

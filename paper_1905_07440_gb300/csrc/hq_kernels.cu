@@ -89,6 +89,38 @@ __device__ inline void flag_nonfinite(const Dev& d, int c, double v) {
   if (!isfinite(v)) d.status[c] = HQ_ENAN;
 }
 
+// log|det(I + U D T)| from the last UDV factors (D in sm.dv):
+// I + U D T = U Db (Db^-1 U^T + Ds T), so log|det| = sum log Db + log|det A|.  With G0,
+// also G_0 = (I + (B_L..B_1)^T)^-T = Y^T with Y = A^-1 Db^-1 U^T.
+__device__ double finish_logdet(const Dev& d, int c, const Smem& sm, const double* U, const double* Tc, double* G0) {
+  const int n = d.n;
+  HQ_TIC(ld);
+  double* A = chain_work(d, c, WK_M1);
+  double* Y = chain_work(d, c, WK_M2);
+  for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+    const int i = idx % n, col = idx / n;
+    const double D = sm.dv[i];
+    const double db = fmax(D, 1.0), ds = fmin(D, 1.0);
+    const double ut = U[(size_t)i * n + col] / db;
+    A[(size_t)col * n + i] = ut + ds * Tc[(size_t)col * n + i];
+    if (G0) Y[(size_t)col * n + i] = ut;
+  }
+  double lsum = 0.0;
+  for (int i = threadIdx.x; i < n; i += HQ_THREADS) lsum += log(fmax(sm.dv[i], 1.0));
+  const double lb = block_sum(lsum, sm.red);
+  const double la = lu_logdet(A, n, n, sm.piv, sm.sint, sm.red);
+  if (G0) {
+    lu_solve(A, n, n, sm.piv, Y);
+    for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+      const int r = idx % n, col = idx / n;
+      G0[(size_t)col * n + r] = Y[(size_t)r * n + col];
+    }
+    __syncthreads();
+  }
+  HQ_TOC(ld, SEC_LOGDET);
+  return lb + la;
+}
+
 // UDV factors of the transposed top-down product (B_L .. B_1)^T = B_1^T .. B_L^T, built
 // by left-multiplying B_s^T = exp(-dtau V_s) exp(-dtau K) for s = L-1 .. 0 and refactoring
 // by pivoted QR after every chunk that ends on a restabilisation boundary.  The field at
@@ -149,33 +181,7 @@ __device__ double udv_top_down(const Dev& d, int c, const Smem& sm, const double
     hi = lo;
     lo -= nw;
   }
-  // I + U D T = U Db (Db^-1 U^T + Ds T):  log|det| = sum log Db + log|det A|
-  HQ_TIC(ld);
-  double* A = chain_work(d, c, WK_M1);
-  double* Y = chain_work(d, c, WK_M2);
-  for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
-    const int i = idx % n, col = idx / n;
-    const double D = sm.dv[i];
-    const double db = fmax(D, 1.0), ds = fmin(D, 1.0);
-    const double ut = U[(size_t)i * n + col] / db;
-    A[(size_t)col * n + i] = ut + ds * Tc[(size_t)col * n + i];
-    if (G0) Y[(size_t)col * n + i] = ut;
-  }
-  double lsum = 0.0;
-  for (int i = threadIdx.x; i < n; i += HQ_THREADS) lsum += log(fmax(sm.dv[i], 1.0));
-  const double lb = block_sum(lsum, sm.red);
-  const double la = lu_logdet(A, n, n, sm.piv, sm.sint, sm.red);
-  if (G0) {
-    lu_solve(A, n, n, sm.piv, Y);
-    // Y = (I + (B_L..B_1)^T)^-1, so G_0 = Y^T
-    for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
-      const int r = idx % n, col = idx / n;
-      G0[(size_t)col * n + r] = Y[(size_t)r * n + col];
-    }
-    __syncthreads();
-  }
-  HQ_TOC(ld, SEC_LOGDET);
-  return lb + la;
+  return finish_logdet(d, c, sm, U, Tc, G0);
 }
 
 template <int LMAX>
@@ -461,6 +467,120 @@ local_chunk_kernel(Dev d, int s0, int s1, uint32_t sweep, int measure) {
   HQ_TOC(ms, SEC_MEASURE);
 }
 
+// -------------------------------------------- block moves with chunk propagators
+// For block moves the n_wrap-slice products M_q = B_lo^T .. B_{hi-1}^T (chunk q covers
+// slices [q n_wrap, min((q+1) n_wrap, L))) are formed once per block-move phase.  A move
+// X(i, .) += dX multiplies every exp(-dtau V_s) by (1 + delta e_i e_i^T),
+// delta = exp(-dtau g dX) - 1, so with A_s = B_s^T and A'_s its shifted version
+//   M'_q = A'_lo .. A'_{hi-1} = M_q + delta sum_s (A'_lo .. A'_{s-1} e_i)(e_i^T A_s .. A_{hi-1})
+// (telescoping; rank <= n_wrap), and the UDV chain needs one dense GEMM per chunk instead
+// of n_wrap slice applications.  The shifted M'_q go to the second buffer, which becomes
+// current when the move is accepted.
+
+__device__ inline double* chunk_mat(const Dev& d, int c, int buf, int q) {
+  return d.cmat + (((size_t)c * 2 + buf) * d.n_chunks + q) * (size_t)d.n * d.n;
+}
+
+// per chain: V (n x n_wrap), R (n x n_wrap), shifted diagonal entry per slice (L)
+__device__ inline double* chain_corr(const Dev& d, int c) {
+  return d.corr + (size_t)c * (2 * (size_t)d.n * d.n_wrap + d.L);
+}
+
+// exp(-dtau V) of every slice and the chunk products M_q of chain c (current buffer).
+template <int LMAX>
+__device__ void build_chunks(const Dev& d, const Smem& sm, int c) {
+  const int n = d.n, L = d.L, nw = d.n_wrap;
+  const double* X = d.X + (size_t)c * L * n;
+  double* ev = d.expV + (size_t)c * L * n;
+  for (int idx = threadIdx.x; idx < L * n; idx += HQ_THREADS) ev[idx] = exp(-d.dtau * (d.g * X[idx] - d.mu));
+  __syncthreads();
+  const int cur = d.cbuf[c];
+  for (int q = 0; q < d.n_chunks; ++q) {
+    const int lo = q * nw, hi = min(lo + nw, L);
+    double* M = chunk_mat(d, c, cur, q);
+    set_identity(M, n, n);
+    __syncthreads();
+    for (int s = hi - 1; s >= lo; --s)
+      kin_rows<LMAX, KIN_SCALE_AFTER>(M, n, n, sm.ex, sm.ey, d.nx, d.ny, ev + (size_t)s * n);
+  }
+}
+
+// log|det M(X')| for X' = X + dx e_site (all slices) from the chunk propagators.
+template <int LMAX>
+__device__ double udv_top_down_cm(const Dev& d, int c, const Smem& sm, int site, double dx) {
+  const int n = d.n, L = d.L, nw = d.n_wrap;
+  const double* X = d.X + (size_t)c * L * n;
+  const double* ev = d.expV + (size_t)c * L * n;
+  double* Vc = chain_corr(d, c);
+  double* Rc = Vc + (size_t)n * nw;
+  double* xs = Rc + (size_t)n * nw;
+  const int cur = d.cbuf[c];
+  double* P = chain_work(d, c, WK_P);
+  double* U = chain_work(d, c, WK_U);
+  double* Tc = chain_work(d, c, WK_T);
+  double* Tn = chain_work(d, c, WK_T2);
+  double* Q = chain_work(d, c, WK_M1);
+  double* Y = chain_work(d, c, WK_M2);
+  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint};
+  const double delta = expm1(-d.dtau * d.g * dx);
+  for (int s = threadIdx.x; s < L; s += HQ_THREADS) xs[s] = exp(-d.dtau * (d.g * (X[(size_t)s * n + site] + dx) - d.mu));
+  bool first = true;
+  for (int q = d.n_chunks - 1; q >= 0; --q) {
+    const int lo = q * nw, hi = min(lo + nw, L), m = hi - lo;
+    HQ_TIC(cv);
+    for (int idx = threadIdx.x; idx < n * m; idx += HQ_THREADS) {
+      const double e = (idx % n == site) ? 1.0 : 0.0;
+      Vc[idx] = e;
+      Rc[idx] = e;
+    }
+    __syncthreads();
+    // column k of V: A'_lo .. A'_{lo+k-1} e_site, A'_t = D'_t E (D'_t: shifted diagonal)
+    for (int t = hi - 2; t >= lo; --t) {
+      for (int r = threadIdx.x; r < n; r += HQ_THREADS) sm.dl[r] = (r == site) ? xs[t] : ev[(size_t)t * n + r];
+      const int k0 = t - lo + 1;  // dl is read in kin_rows' second pass, after its barrier
+      kin_rows<LMAX, KIN_SCALE_AFTER>(Vc + (size_t)k0 * n, n, m - k0, sm.ex, sm.ey, d.nx, d.ny, sm.dl);
+    }
+    // column k of R: A_{hi-1}^T .. A_{lo+k}^T e_site, A_t^T = E D_t
+    for (int t = lo; t < hi; ++t)
+      kin_rows<LMAX, KIN_SCALE_BEFORE>(Rc, n, t - lo + 1, sm.ex, sm.ey, d.nx, d.ny, ev + (size_t)t * n);
+    const double* M = chunk_mat(d, c, cur, q);
+    double* Mn = chunk_mat(d, c, 1 - cur, q);
+    for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+      const int r = idx % n, col = idx / n;
+      double a = 0.0;
+      for (int k = 0; k < m; ++k) a = fma(Vc[(size_t)k * n + r], Rc[(size_t)k * n + col], a);
+      Mn[idx] = fma(delta, a, M[idx]);
+    }
+    __syncthreads();
+    HQ_TOC(cv, SEC_DL);
+    HQ_TIC(gm);
+    if (first) {
+      copy_mat(P, Mn, n, n);
+    } else {
+      copy_scale_cols(Y, U, n, n, sm.dv);
+      __syncthreads();
+      gemm_nn<false, false>(n, Mn, Y, P, n);
+    }
+    __syncthreads();
+    HQ_TOC(gm, SEC_KIN);
+    HQ_TIC(pp);
+    prepivot(P, Q, n, n, qs, sm.norm2);
+    HQ_TOC(pp, SEC_PREPIVOT);
+    HQ_TIC(qr);
+    qr_householder(Q, n, n, qs);
+    HQ_TOC(qr, SEC_QR);
+    HQ_TIC(fq);
+    form_q(Q, n, n, U, qs);
+    HQ_TOC(fq, SEC_FORMQ);
+    HQ_TIC(tu);
+    t_update(Q, n, n, qs, sm.dv, first ? nullptr : Tc, Tn);
+    HQ_TOC(tu, SEC_TUPD);
+    double* t = Tc; Tc = Tn; Tn = t;
+    first = false;
+  }
+  return finish_logdet(d, c, sm, U, Tc, nullptr);
+}
+
 // One block move X(site, .) += dX of chain c: Philox draw, dtau dS_ph, the full stabilised
 // log|det M(X')| and the Metropolis decision (all threads of the CTA).
 template <int LMAX>
@@ -484,7 +604,8 @@ __device__ void block_move(const Dev& d, const Smem& sm, int c, int site, uint32
   a = block_sum(a, sm.red);
   const double dS = 0.5 * d.dtau * d.mass * (d.omega * d.omega) * a;
   HQ_TOC(mv, SEC_MOVE);
-  const double ld_new = udv_top_down<LMAX>(d, c, sm, X, site, dx, false, nullptr);
+  const double ld_new = d.use_cm ? udv_top_down_cm<LMAX>(d, c, sm, site, dx)
+                                 : udv_top_down<LMAX>(d, c, sm, X, site, dx, false, nullptr);
   if (threadIdx.x == 0) {
     const double arg = 2.0 * (ld_new - d.logdet[c]) - dS;
     const double prob = exp(fmin(arg, 709.0));
@@ -501,6 +622,13 @@ __device__ void block_move(const Dev& d, const Smem& sm, int c, int site, uint32
   __syncthreads();
   if (sm.sint[4]) {
     for (int s = threadIdx.x; s < L; s += HQ_THREADS) X[(size_t)s * n + site] = X[(size_t)s * n + site] + dx;
+    if (d.use_cm) {
+      // the shifted chunk propagators and diagonal become current
+      const double* xs = chain_corr(d, c) + 2 * (size_t)n * d.n_wrap;
+      double* ev = d.expV + (size_t)c * L * n;
+      for (int s = threadIdx.x; s < L; s += HQ_THREADS) ev[(size_t)s * n + site] = xs[s];
+      if (threadIdx.x == 0) d.cbuf[c] = 1 - d.cbuf[c];
+    }
   }
 }
 
@@ -510,8 +638,9 @@ __device__ __forceinline__ unsigned long long global_timer_ns() {
   return t;
 }
 
-// The block-move phase of a sweep as one persistent launch.  Task t = site * C + chain
-// (every chain's N moves in site order).  Workers take tasks from an atomic counter; a task
+// The block-move phase of a sweep as one persistent launch.  Task t = step * C + chain;
+// a chain's steps are its N moves in site order, preceded (with chunk propagators) by the
+// build of its propagators.  Workers take tasks from an atomic counter; a task
 // waits until its chain has finished the previous site (progress flag written with a
 // release fence after the move, read before the move with an acquire fence).  Faster SMs
 // take more tasks, so the load balances across SMs whatever C is.  The wait is bounded:
@@ -524,7 +653,7 @@ __global__ void __launch_bounds__(HQ_THREADS) global_phase_kernel(Dev d, uint32_
   __shared__ int s_task;
   const Smem sm = carve(d, smraw);
   load_kinetic(d, sm);
-  const int C = d.n_chains, ntask = d.n * C;
+  const int C = d.n_chains, ntask = (d.n + (d.use_cm ? 1 : 0)) * C;
   int* counter = d.sched;
   volatile int* abort_flag = d.sched + 1;
   volatile int* progress = d.sched + kSchedHeader;
@@ -559,8 +688,14 @@ __global__ void __launch_bounds__(HQ_THREADS) global_phase_kernel(Dev d, uint32_
     HQ_TOC(wait, SEC_WAIT);
     const int t = s_task;
     if (t < 0 || t >= ntask) break;
-    __threadfence();  // acquire: the previous move of this chain (possibly on another SM)
-    block_move<LMAX>(d, sm, t % C, t / C, sweep);
+    __threadfence();  // acquire: the previous step of this chain (possibly on another SM)
+    const int step = t / C;
+    if (d.use_cm) {
+      if (step == 0) build_chunks<LMAX>(d, sm, t % C);
+      else block_move<LMAX>(d, sm, t % C, step - 1, sweep);
+    } else {
+      block_move<LMAX>(d, sm, t % C, step, sweep);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();  // release the move before publishing it
@@ -752,7 +887,7 @@ static cudaError_t launch_phase(const Dev& d, uint32_t sweep, cudaStream_t s) {
   if (occ < 1) return cudaErrorInvalidConfiguration;
   // every worker must be resident (a waiting worker relies on the owner of the previous
   // task running), so the grid never exceeds one wave
-  const int ntask = d.n * d.n_chains;
+  const int ntask = (d.n + (d.use_cm ? 1 : 0)) * d.n_chains;
   int workers = sms * (occ < kWorkersPerSm ? occ : kWorkersPerSm);
   if (workers > ntask) workers = ntask;
   st = cudaMemsetAsync(d.sched, 0, sizeof(int) * (kSchedHeader + d.n_chains), s);

@@ -147,6 +147,18 @@ def test_sweeps_ragged_and_edge_shapes(hq, nx, beta, n_wrap, k):
     check_against_oracle(hq, p, X0, 2)
 
 
+@pytest.mark.parametrize("nx,beta,n_wrap,method", [(6, 1.0, 2, 0), (6, 1.0, 5, 1), (8, 2.0, 10, 1), (4, 1.0, 3, 0)])
+def test_block_move_methods_against_oracle(hq, nx, beta, n_wrap, method):
+    """Both block-move algorithms (separable slices per move / chunk propagators) agree with
+    the oracle; the flop model picks the one named for each shape."""
+    p = HolsteinParams(nx=nx, ny=nx, beta=beta, n_wrap=n_wrap, delay_k=8, seed=11)
+    eng = hq.Engine(p, 1)
+    assert eng.block_move_method == method
+    eng.close()
+    X0 = initial_fields(p, 2, seed=21)
+    check_against_oracle(hq, p, X0, 2, local=True, global_=True)
+
+
 def test_local_only_and_global_only(hq):
     p = HolsteinParams(nx=4, ny=4, beta=2.0, delay_k=5)
     X0 = initial_fields(p, 2, seed=9)
