@@ -35,18 +35,30 @@ L2_BYTES = 129 * 2 ** 20
 
 
 # ------------------------------------------------------------------ flop model
-def flops_block_move(p):
-    """FP64 flops of one block-move launch for one chain (global_move_kernel).
+def flops_block_move(p, method):
+    """FP64 flops of one block move of one chain, for the algorithm the engine uses.
 
-    Per slice: separable exp(-dtau K) on an N x N matrix, 2 N^2 (nx + ny), and the
-    exp(-dtau V) row scaling, N^2.  Per chunk of n_wrap slices: Householder QR (after a
-    one-time column ordering) 4/3 N^3, explicit Q 4/3 N^3, T update N^3 (not for the first
-    chunk).  Final LU 2/3 N^3.
+    Common part, per chunk of m <= n_wrap slices: Householder QR after a one-time column
+    ordering 4/3 N^3, explicit Q 4/3 N^3, T update N^3 (not for the first chunk); final LU
+    2/3 N^3.  method 0 (per-slice): each slice applies the separable exp(-dtau K),
+    2 N^2 (nx + ny), and the exp(-dtau V) scaling, N^2.  method 1 (chunk propagators): per
+    chunk the correction vectors (m(m-1)/2 + m(m+1)/2 vector slice applications of
+    2 N (nx + ny) + N), the rank-m update 2 m N^2, and a GEMM 2 N^3 (not for the first).
     """
-    n, L = p.n_sites, p.n_slices
-    chunks = math.ceil(L / p.n_wrap)
-    per_slice = 2.0 * n * n * (p.nx + p.ny) + n * n
-    return L * per_slice + chunks * (8.0 / 3.0) * n ** 3 + (chunks - 1) * n ** 3 + (2.0 / 3.0) * n ** 3
+    n, L, nw = p.n_sites, p.n_slices, p.n_wrap
+    chunks = [min(nw, L - q * nw) for q in range(math.ceil(L / nw))]
+    qr = len(chunks) * (8.0 / 3.0) * n ** 3 + (len(chunks) - 1) * n ** 3 + (2.0 / 3.0) * n ** 3
+    if method == 0:
+        return L * (2.0 * n * n * (p.nx + p.ny) + n * n) + qr
+    vec = 2.0 * n * (p.nx + p.ny) + n
+    corr = sum(m * m * vec + 2.0 * m * n * n for m in chunks)
+    return corr + (len(chunks) - 1) * 2.0 * n ** 3 + qr
+
+
+def flops_chunk_build(p):
+    """FP64 flops of building one chain's chunk propagators (L slice applications)."""
+    n = p.n_sites
+    return p.n_slices * (2.0 * n * n * (p.nx + p.ny) + n * n)
 
 
 # -------------------------------------------------------------- CPU baseline
@@ -273,8 +285,11 @@ def run_ours(args):
     per_launch_s = ms / 1e3 / max(launches, 1)
     kernel_names = {"block_moves": "global_phase_kernel", "local_chunk": "local_chunk_kernel",
                     "stack_build": "stack_build_kernel", "sweep_end": "sweep_end_kernel"}
+    method = eng.block_move_method
     if dom == "block_moves":
-        fl = flops_block_move(params) * chains * params.n_sites   # one launch = N moves per chain
+        # one launch = N moves per chain (+ the chunk-propagator build with method 1)
+        fl = chains * (params.n_sites * flops_block_move(params, method) +
+                       (flops_chunk_build(params) if method == 1 else 0.0))
     else:
         fl = None
     achieved = fl / per_launch_s / 1e12 if fl else None
@@ -296,6 +311,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": t_dev * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wname, "lattice": f"{params.nx}x{params.ny}", "beta": params.beta,
+                   "block_move_method": ["per-slice", "chunk propagators"][method],
                    "dtau": params.dtau, "L": params.n_slices, "chains_per_rank": chains, "delay_k": params.delay_k,
                    "n_wrap": params.n_wrap, "block_moves_per_sweep": params.n_sites,
                    "parallelism": f"replicas x{world}",
