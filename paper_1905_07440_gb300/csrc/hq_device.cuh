@@ -247,12 +247,17 @@ __device__ __forceinline__ void copy_mat(double* B, const double* A, int ld, int
 // Column work is spread over groups of 8 lanes (32 groups per CTA): each group reduces a
 // column's dot product with 3 shuffles, and every warp runs the same number of passes so
 // the shuffles always see all 32 lanes.
+constexpr int kQB = 8;  // reflectors per block when forming Q
+
 struct QrScratch {
   double* tau;   // [n] reflector scalars
   double* vs;    // [2n] Householder vectors (current and next)
   double* rinv;  // [n] 1 / D
   int* perm;     // [n] perm[j] = original column placed at position j
   int* sint;     // >= 1
+  double* vblk;  // [kQB n] block of reflector vectors
+  double* tblk;  // [kQB kQB] block reflector factor T
+  double* gram;  // [kQB kQB] inner products of the block's vectors
 };
 
 constexpr int kGroup = 8;
@@ -309,9 +314,13 @@ __device__ __forceinline__ void house_gen(double* P, int ld, int n, int j, doubl
   const double alpha = cj[j];
   double tj = 0.0, beta = alpha, scal = 0.0;
   if (a != 0.0) {
-    const double nrm = sqrt(fma(alpha, alpha, a));
+    // beta = -sign(alpha) ||x||, tau = (beta - alpha) / beta = 1 + |alpha| / ||x||,
+    // v = x / (alpha - beta) below the unit leading entry
+    const double s2 = fma(alpha, alpha, a);
+    const double rs = rsqrt(s2);
+    const double nrm = s2 * rs;
     beta = (alpha >= 0.0) ? -nrm : nrm;
-    tj = (beta - alpha) / beta;
+    tj = fma(fabs(alpha), rs, 1.0);
     scal = 1.0 / (alpha - beta);
   }
   for (int r = j + 1 + lane; r < n; r += 32) {
@@ -372,32 +381,85 @@ __device__ void qr_householder(double* P, int ld, int n, const QrScratch& s) {
 }
 
 // U <- Q = H_0 H_1 ... H_{n-1} (explicit), from the reflectors stored in P and tau.
-// One barrier per reflector: the next reflector's vector is staged into the other half of
-// `vs` while the current one is applied.
+// Backward accumulation in blocks of kQB reflectors, each applied as the compact WY form
+// I - V T V^T (T upper triangular, LAPACK xLARFT forward/columnwise convention): per
+// column one pass computes the kQB inner products V^T u (independent chains), T (V^T u)
+// and the update; one barrier per block instead of one per reflector.
 __device__ void form_q(const double* P, int ld, int n, double* U, const QrScratch& s) {
-  const int g = threadIdx.x / kGroup, sub = threadIdx.x % kGroup;
+  const int tid = threadIdx.x, g = tid / kGroup, sub = tid % kGroup;
   set_identity(U, ld, n);
-  const int jl = n - 1;
-  for (int r = jl + threadIdx.x; r < n; r += HQ_THREADS) s.vs[(jl & 1) * n + r] = 1.0;
-  __syncthreads();
-  for (int j = n - 1; j >= 0; --j) {
-    const double* vc = s.vs + (j & 1) * n;
-    if (j > 0) {
-      double* vn = s.vs + ((j - 1) & 1) * n;
-      for (int r = j - 1 + threadIdx.x; r < n; r += HQ_THREADS) vn[r] = (r == j - 1) ? 1.0 : P[(size_t)(j - 1) * ld + r];
+  const int nblk = (n + kQB - 1) / kQB;
+  for (int b = nblk - 1; b >= 0; --b) {
+    const int j0 = b * kQB;
+    const int nb = (n - j0 < kQB) ? n - j0 : kQB;
+    // stage V (column k = reflector j0 + k: zero above its unit entry); zero unused columns
+    for (int idx = tid; idx < kQB * n; idx += HQ_THREADS) {
+      const int k = idx / n, r = idx % n, j = j0 + k;
+      double v = 0.0;
+      if (k < nb) v = (r < j) ? 0.0 : (r == j ? 1.0 : P[(size_t)j * ld + r]);
+      s.vblk[idx] = v;
     }
-    const double tj = s.tau[j];
-    if (tj != 0.0) {
-      for (int base = j; base < n; base += kGroups) {
-        const int c = base + g;
-        double* uc = U + (size_t)c * ld;
-        double w = 0.0;
-        if (c < n)
-          for (int r = j + sub; r < n; r += kGroup) w = fma(vc[r], uc[r], w);
-        w = group_sum(w) * tj;
-        if (c < n)
-          for (int r = j + sub; r < n; r += kGroup) uc[r] = fma(-w, vc[r], uc[r]);
+    for (int idx = tid; idx < kQB * kQB; idx += HQ_THREADS) s.tblk[idx] = 0.0;
+    __syncthreads();
+    // Gram entries v_i . v_k, i < k (v_k vanishes above row j0 + k)
+    const int npairs = nb * (nb - 1) / 2;
+    for (int base = 0; base < npairs; base += kGroups) {
+      const int pidx = base + g;
+      int pi = 0, pk = 1;
+      if (pidx < npairs) {
+        int rem = pidx;
+        pk = 1;
+        while (rem >= pk) { rem -= pk; ++pk; }
+        pi = rem;
       }
+      double a = 0.0;
+      if (pidx < npairs)
+        for (int r = j0 + pk + sub; r < n; r += kGroup) a = fma(s.vblk[pi * n + r], s.vblk[pk * n + r], a);
+      a = group_sum(a);
+      if (pidx < npairs && sub == 0) s.gram[pi * kQB + pk] = a;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int i = 0; i < nb; ++i) {
+        const double ti = s.tau[j0 + i];
+        s.tblk[i * kQB + i] = ti;
+        for (int r = 0; r < i; ++r) {
+          double acc = 0.0;
+          for (int q = r; q < i; ++q) acc = fma(s.tblk[r * kQB + q], s.gram[q * kQB + i], acc);
+          s.tblk[r * kQB + i] = -ti * acc;
+        }
+      }
+    }
+    __syncthreads();
+    for (int base = j0; base < n; base += kGroups) {
+      const int c = base + g;
+      double* uc = U + (size_t)c * ld;
+      double w[kQB];
+#pragma unroll
+      for (int k = 0; k < kQB; ++k) w[k] = 0.0;
+      if (c < n)
+        for (int r = j0 + sub; r < n; r += kGroup) {
+          const double u = uc[r];
+#pragma unroll
+          for (int k = 0; k < kQB; ++k) w[k] = fma(s.vblk[k * n + r], u, w[k]);
+        }
+#pragma unroll
+      for (int k = 0; k < kQB; ++k) w[k] = group_sum(w[k]);
+      double z[kQB];
+#pragma unroll
+      for (int i = 0; i < kQB; ++i) {
+        double a = 0.0;
+#pragma unroll
+        for (int k = i; k < kQB; ++k) a = fma(s.tblk[i * kQB + k], w[k], a);
+        z[i] = a;
+      }
+      if (c < n)
+        for (int r = j0 + sub; r < n; r += kGroup) {
+          double a = uc[r];
+#pragma unroll
+          for (int k = 0; k < kQB; ++k) a = fma(-s.vblk[k * n + r], z[k], a);
+          uc[r] = a;
+        }
     }
     __syncthreads();
   }
@@ -425,8 +487,21 @@ __device__ void t_update(const double* P, int ld, int n, const QrScratch& s, dou
     for (int idx = threadIdx.x; idx < n * nq; idx += HQ_THREADS) {
       const int q = idx % nq, j = idx / nq;
       const double* t0 = Tprev + (size_t)(4 * q) * ld;
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-      for (int c = j; c < n; ++c) {
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
+      int c = j;
+      for (; c + 1 < n; c += 2) {  // two partial sums per output halve the dependent chain
+        const double r = P[(size_t)c * ld + j], r2 = P[(size_t)(c + 1) * ld + j];
+        const int pc = s.perm[c], pd = s.perm[c + 1];
+        a0 = fma(r, t0[pc], a0);
+        a1 = fma(r, t0[ld + pc], a1);
+        a2 = fma(r, t0[2 * (size_t)ld + pc], a2);
+        a3 = fma(r, t0[3 * (size_t)ld + pc], a3);
+        b0 = fma(r2, t0[pd], b0);
+        b1 = fma(r2, t0[ld + pd], b1);
+        b2 = fma(r2, t0[2 * (size_t)ld + pd], b2);
+        b3 = fma(r2, t0[3 * (size_t)ld + pd], b3);
+      }
+      if (c < n) {
         const double r = P[(size_t)c * ld + j];
         const int pc = s.perm[c];
         a0 = fma(r, t0[pc], a0);
@@ -436,10 +511,10 @@ __device__ void t_update(const double* P, int ld, int n, const QrScratch& s, dou
       }
       const double ri = s.rinv[j];
       double* o = Tout + (size_t)(4 * q) * ld + j;
-      o[0] = a0 * ri;
-      o[ld] = a1 * ri;
-      o[2 * (size_t)ld] = a2 * ri;
-      o[3 * (size_t)ld] = a3 * ri;
+      o[0] = (a0 + b0) * ri;
+      o[ld] = (a1 + b1) * ri;
+      o[2 * (size_t)ld] = (a2 + b2) * ri;
+      o[3 * (size_t)ld] = (a3 + b3) * ri;
     }
   }
   __syncthreads();

@@ -102,7 +102,7 @@ Layout layout(const hq_params& p, int C, int max_series) {
     l.expV = take(sizeof(double) * C * L * n);
     l.cmat = take(sizeof(double) * C * 2 * nch * nn);
     l.cbuf = take(sizeof(int) * C);
-    l.corr = take(sizeof(double) * C * (2 * n * p.n_wrap + L));
+    l.corr = take(sizeof(double) * C * (2 * n * L + L));
   }
   l.total = off;
   return l;

@@ -57,7 +57,7 @@ struct Dev {
   double* expV;       // [C][L][N] exp(-dtau V) of the current fields
   double* cmat;       // [C][2][n_chunks][N*N] chunk products, current and proposed
   int* cbuf;          // [C] index of the current buffer
-  double* corr;       // [C][2 N n_wrap + L] rank-n_wrap correction vectors, shifted diagonal
+  double* corr;       // [C][2 N L + L] correction vectors of every chunk, shifted diagonal
 };
 
 // FP64 flop model of one chunk of a block move: n_wrap separable slice applications versus

@@ -34,14 +34,14 @@ int section_cycles(unsigned long long* out, int n) {
 struct Smem {
   double *ex, *exi, *ey, *eyi;
   double *dl, *u2, *xn, *dlt, *es, *dcorr, *tau, *norm2, *rinv, *vs, *dv;
-  double *red, *scal;
+  double *red, *scal, *vblk, *tblk, *gram;
   int *perm, *piv, *sint;
 };
 
 static constexpr int kSmemVecs = 12;  // vs takes two
 
 __host__ __device__ inline size_t smem_layout_bytes(int nx, int ny, int n) {
-  return (size_t)(2 * nx * nx + 2 * ny * ny + kSmemVecs * n + 32 + 16) * sizeof(double) +
+  return (size_t)(2 * nx * nx + 2 * ny * ny + kSmemVecs * n + 32 + 16 + kQB * n + 2 * kQB * kQB) * sizeof(double) +
          (size_t)(2 * n + 8) * sizeof(int);
 }
 
@@ -68,6 +68,9 @@ __device__ inline Smem carve(const Dev& d, double* base) {
   s.dv = p; p += n;
   s.red = p; p += 32;
   s.scal = p; p += 16;
+  s.vblk = p; p += kQB * n;
+  s.tblk = p; p += kQB * kQB;
+  s.gram = p; p += kQB * kQB;
   int* q = reinterpret_cast<int*>(p);
   s.perm = q; q += n;
   s.piv = q; q += n;
@@ -136,7 +139,7 @@ __device__ double udv_top_down(const Dev& d, int c, const Smem& sm, const double
   double* Tc = chain_work(d, c, WK_T);
   double* Tn = chain_work(d, c, WK_T2);
   double* Q = chain_work(d, c, WK_M1);
-  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint};
+  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint, sm.vblk, sm.tblk, sm.gram};
   int hi = L, lo = ((L - 1) / nw) * nw;
   bool first = true;
   while (true) {
@@ -434,7 +437,7 @@ local_chunk_kernel(Dev d, int s0, int s1, uint32_t sweep, int measure) {
   HQ_TOC(rp, SEC_RESTAB_PROD);
   HQ_TIC(rq);
   double* Q = chain_work(d, c, WK_M1);
-  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint};
+  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint, sm.vblk, sm.tblk, sm.gram};
   prepivot(P, Q, n, n, qs, sm.norm2);
   qr_householder(Q, n, n, qs);
   form_q(Q, n, n, UR, qs);
@@ -481,9 +484,9 @@ __device__ inline double* chunk_mat(const Dev& d, int c, int buf, int q) {
   return d.cmat + (((size_t)c * 2 + buf) * d.n_chunks + q) * (size_t)d.n * d.n;
 }
 
-// per chain: V (n x n_wrap), R (n x n_wrap), shifted diagonal entry per slice (L)
+// per chain: V (n x L), R (n x L), shifted diagonal entry per slice (L)
 __device__ inline double* chain_corr(const Dev& d, int c) {
-  return d.corr + (size_t)c * (2 * (size_t)d.n * d.n_wrap + d.L);
+  return d.corr + (size_t)c * (2 * (size_t)d.n * d.L + d.L);
 }
 
 // exp(-dtau V) of every slice and the chunk products M_q of chain c (current buffer).
@@ -506,14 +509,76 @@ __device__ void build_chunks(const Dev& d, const Smem& sm, int c) {
 }
 
 // log|det M(X')| for X' = X + dx e_site (all slices) from the chunk propagators.
+// One step of the correction-vector chains of every chunk at once.  Column s of V (or R)
+// belongs to chunk q = s / n_wrap, position k = s - q n_wrap in a chunk of length m_q.
+//   V step (1 <= step < n_wrap): columns with k >= m_q - step get A'_t = D'_t E, t = hi_q - 1 - step
+//   R step (0 <= step < n_wrap): columns with k <= step get A_t^T = E D_t,      t = lo_q + step
+// D_t = exp(-dtau V_t) from the cache ev, D'_t the same with entry `site` replaced by xs[t].
+template <int LMAX, bool RCHAIN>
+__device__ void corr_step(const Dev& d, const Smem& sm, double* W, int step, int site, const double* ev,
+                          const double* xs) {
+  const int n = d.n, L = d.L, nw = d.n_wrap, nx = d.nx, ny = d.ny;
+  for (int line = threadIdx.x; line < ny * L; line += HQ_THREADS) {
+    const int y = line % ny, col = line / ny;
+    const int q = col / nw, k = col - q * nw, lo = q * nw, m = min(nw, L - lo);
+    const bool on = (step < m) && (RCHAIN ? (k <= step) : (k >= m - step));
+    if (!on) continue;
+    const int t = RCHAIN ? lo + step : lo + m - 1 - step;
+    double* base = W + (size_t)col * n + nx * y;
+    double v[LMAX];
+#pragma unroll
+    for (int b = 0; b < LMAX; ++b) {
+      v[b] = (b < nx) ? base[b] : 0.0;
+      if (RCHAIN && b < nx) v[b] *= ev[(size_t)t * n + nx * y + b];
+    }
+#pragma unroll
+    for (int a = 0; a < LMAX; ++a) {
+      if (a < nx) {
+        double acc = 0.0;
+#pragma unroll
+        for (int b = 0; b < LMAX; ++b)
+          if (b < nx) acc = fma(sm.ex[a * nx + b], v[b], acc);
+        base[a] = acc;
+      }
+    }
+  }
+  __syncthreads();
+  for (int line = threadIdx.x; line < nx * L; line += HQ_THREADS) {
+    const int x = line % nx, col = line / nx;
+    const int q = col / nw, k = col - q * nw, lo = q * nw, m = min(nw, L - lo);
+    const bool on = (step < m) && (RCHAIN ? (k <= step) : (k >= m - step));
+    if (!on) continue;
+    const int t = RCHAIN ? lo + step : lo + m - 1 - step;
+    double* base = W + (size_t)col * n + x;
+    double v[LMAX];
+#pragma unroll
+    for (int b = 0; b < LMAX; ++b) v[b] = (b < ny) ? base[b * nx] : 0.0;
+#pragma unroll
+    for (int a = 0; a < LMAX; ++a) {
+      if (a < ny) {
+        double acc = 0.0;
+#pragma unroll
+        for (int b = 0; b < LMAX; ++b)
+          if (b < ny) acc = fma(sm.ey[a * ny + b], v[b], acc);
+        if (!RCHAIN) {
+          const int r = x + nx * a;
+          acc *= (r == site) ? xs[t] : ev[(size_t)t * n + r];
+        }
+        base[a * nx] = acc;
+      }
+    }
+  }
+  __syncthreads();
+}
+
 template <int LMAX>
 __device__ double udv_top_down_cm(const Dev& d, int c, const Smem& sm, int site, double dx) {
   const int n = d.n, L = d.L, nw = d.n_wrap;
   const double* X = d.X + (size_t)c * L * n;
   const double* ev = d.expV + (size_t)c * L * n;
-  double* Vc = chain_corr(d, c);
-  double* Rc = Vc + (size_t)n * nw;
-  double* xs = Rc + (size_t)n * nw;
+  double* Vc = chain_corr(d, c);   // [L][n]: column s for slice s
+  double* Rc = Vc + (size_t)n * L;
+  double* xs = Rc + (size_t)n * L;
   const int cur = d.cbuf[c];
   double* P = chain_work(d, c, WK_P);
   double* U = chain_work(d, c, WK_U);
@@ -521,38 +586,46 @@ __device__ double udv_top_down_cm(const Dev& d, int c, const Smem& sm, int site,
   double* Tn = chain_work(d, c, WK_T2);
   double* Q = chain_work(d, c, WK_M1);
   double* Y = chain_work(d, c, WK_M2);
-  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint};
+  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint, sm.vblk, sm.tblk, sm.gram};
   const double delta = expm1(-d.dtau * d.g * dx);
+  HQ_TIC(cv);
   for (int s = threadIdx.x; s < L; s += HQ_THREADS) xs[s] = exp(-d.dtau * (d.g * (X[(size_t)s * n + site] + dx) - d.mu));
-  bool first = true;
-  for (int q = d.n_chunks - 1; q >= 0; --q) {
-    const int lo = q * nw, hi = min(lo + nw, L), m = hi - lo;
-    HQ_TIC(cv);
-    for (int idx = threadIdx.x; idx < n * m; idx += HQ_THREADS) {
-      const double e = (idx % n == site) ? 1.0 : 0.0;
-      Vc[idx] = e;
-      Rc[idx] = e;
-    }
-    __syncthreads();
-    // column k of V: A'_lo .. A'_{lo+k-1} e_site, A'_t = D'_t E (D'_t: shifted diagonal)
-    for (int t = hi - 2; t >= lo; --t) {
-      for (int r = threadIdx.x; r < n; r += HQ_THREADS) sm.dl[r] = (r == site) ? xs[t] : ev[(size_t)t * n + r];
-      const int k0 = t - lo + 1;  // dl is read in kin_rows' second pass, after its barrier
-      kin_rows<LMAX, KIN_SCALE_AFTER>(Vc + (size_t)k0 * n, n, m - k0, sm.ex, sm.ey, d.nx, d.ny, sm.dl);
-    }
-    // column k of R: A_{hi-1}^T .. A_{lo+k}^T e_site, A_t^T = E D_t
-    for (int t = lo; t < hi; ++t)
-      kin_rows<LMAX, KIN_SCALE_BEFORE>(Rc, n, t - lo + 1, sm.ex, sm.ey, d.nx, d.ny, ev + (size_t)t * n);
+  for (int idx = threadIdx.x; idx < n * L; idx += HQ_THREADS) {
+    const double e = (idx % n == site) ? 1.0 : 0.0;
+    Vc[idx] = e;
+    Rc[idx] = e;
+  }
+  __syncthreads();
+  // column s of V: A'_lo .. A'_{s-1} e_site; of R: A_{hi-1}^T .. A_s^T e_site (chunk [lo, hi))
+  for (int step = 1; step < nw; ++step) corr_step<LMAX, false>(d, sm, Vc, step, site, ev, xs);
+  for (int step = 0; step < nw; ++step) corr_step<LMAX, true>(d, sm, Rc, step, site, ev, xs);
+  // M'_q = M_q + delta sum_{s in q} V_s R_s^T for every chunk (four outputs per thread)
+  const int nn4 = (n * n) >> 2;
+  for (int idx = threadIdx.x; idx < d.n_chunks * nn4; idx += HQ_THREADS) {
+    const int q = idx / nn4, e0 = (idx - q * nn4) * 4;
+    const int lo = q * nw, m = min(nw, L - lo);
     const double* M = chunk_mat(d, c, cur, q);
     double* Mn = chunk_mat(d, c, 1 - cur, q);
-    for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
-      const int r = idx % n, col = idx / n;
-      double a = 0.0;
-      for (int k = 0; k < m; ++k) a = fma(Vc[(size_t)k * n + r], Rc[(size_t)k * n + col], a);
-      Mn[idx] = fma(delta, a, M[idx]);
+    const int col = e0 / n, r0 = e0 - col * n;  // four consecutive rows of one column (n % 4 == 0)
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (int k = 0; k < m; ++k) {
+      const double* vk = Vc + (size_t)(lo + k) * n + r0;
+      const double rk = Rc[(size_t)(lo + k) * n + col];
+      a0 = fma(vk[0], rk, a0);
+      a1 = fma(vk[1], rk, a1);
+      a2 = fma(vk[2], rk, a2);
+      a3 = fma(vk[3], rk, a3);
     }
-    __syncthreads();
-    HQ_TOC(cv, SEC_DL);
+    Mn[e0] = fma(delta, a0, M[e0]);
+    Mn[e0 + 1] = fma(delta, a1, M[e0 + 1]);
+    Mn[e0 + 2] = fma(delta, a2, M[e0 + 2]);
+    Mn[e0 + 3] = fma(delta, a3, M[e0 + 3]);
+  }
+  __syncthreads();
+  HQ_TOC(cv, SEC_DL);
+  bool first = true;
+  for (int q = d.n_chunks - 1; q >= 0; --q) {
+    double* Mn = chunk_mat(d, c, 1 - cur, q);
     HQ_TIC(gm);
     if (first) {
       copy_mat(P, Mn, n, n);
@@ -624,7 +697,7 @@ __device__ void block_move(const Dev& d, const Smem& sm, int c, int site, uint32
     for (int s = threadIdx.x; s < L; s += HQ_THREADS) X[(size_t)s * n + site] = X[(size_t)s * n + site] + dx;
     if (d.use_cm) {
       // the shifted chunk propagators and diagonal become current
-      const double* xs = chain_corr(d, c) + 2 * (size_t)n * d.n_wrap;
+      const double* xs = chain_corr(d, c) + 2 * (size_t)n * L;
       double* ev = d.expV + (size_t)c * L * n;
       for (int s = threadIdx.x; s < L; s += HQ_THREADS) ev[(size_t)s * n + site] = xs[s];
       if (threadIdx.x == 0) d.cbuf[c] = 1 - d.cbuf[c];
@@ -791,14 +864,20 @@ static inline int lmax_of(int nx, int ny) {
   return m <= 2 ? 2 : m <= 4 ? 4 : m <= 8 ? 8 : 16;
 }
 
+// Dynamic shared memory above the default 48 KB needs an opt-in per kernel.
+template <typename K>
+static inline void allow_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 #define HQ_DISPATCH(KERNEL, d, stream, ...)                                                  \
   do {                                                                                      \
     const size_t sb = smem_bytes(d);                                                        \
     switch (lmax_of((d).nx, (d).ny)) {                                                      \
-      case 2: KERNEL<2><<<(d).n_chains, HQ_THREADS, sb, stream>>>(__VA_ARGS__); break;      \
-      case 4: KERNEL<4><<<(d).n_chains, HQ_THREADS, sb, stream>>>(__VA_ARGS__); break;      \
-      case 8: KERNEL<8><<<(d).n_chains, HQ_THREADS, sb, stream>>>(__VA_ARGS__); break;      \
-      default: KERNEL<16><<<(d).n_chains, HQ_THREADS, sb, stream>>>(__VA_ARGS__); break;    \
+      case 2: allow_smem(KERNEL<2>, sb); KERNEL<2><<<(d).n_chains, HQ_THREADS, sb, stream>>>(__VA_ARGS__); break;   \
+      case 4: allow_smem(KERNEL<4>, sb); KERNEL<4><<<(d).n_chains, HQ_THREADS, sb, stream>>>(__VA_ARGS__); break;   \
+      case 8: allow_smem(KERNEL<8>, sb); KERNEL<8><<<(d).n_chains, HQ_THREADS, sb, stream>>>(__VA_ARGS__); break;   \
+      default: allow_smem(KERNEL<16>, sb); KERNEL<16><<<(d).n_chains, HQ_THREADS, sb, stream>>>(__VA_ARGS__); break; \
     }                                                                                       \
   } while (0)
 
@@ -878,6 +957,7 @@ cudaError_t launch_local_chunk(const Dev& d, int s0, int s1, uint32_t sweep, int
 template <int LMAX>
 static cudaError_t launch_phase(const Dev& d, uint32_t sweep, cudaStream_t s) {
   const size_t sb = smem_bytes(d);
+  allow_smem(global_phase_kernel<LMAX>, sb);
   int dev = 0, sms = 0, occ = 0;
   cudaError_t st = cudaGetDevice(&dev);
   if (st == cudaSuccess) st = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
