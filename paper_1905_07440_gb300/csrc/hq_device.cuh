@@ -247,17 +247,12 @@ __device__ __forceinline__ void copy_mat(double* B, const double* A, int ld, int
 // Column work is spread over groups of 8 lanes (32 groups per CTA): each group reduces a
 // column's dot product with 3 shuffles, and every warp runs the same number of passes so
 // the shuffles always see all 32 lanes.
-constexpr int kQB = 8;  // reflectors per block when forming Q
-
 struct QrScratch {
   double* tau;   // [n] reflector scalars
   double* vs;    // [2n] Householder vectors (current and next)
   double* rinv;  // [n] 1 / D
   int* perm;     // [n] perm[j] = original column placed at position j
   int* sint;     // >= 1
-  double* vblk;  // [kQB n] block of reflector vectors
-  double* tblk;  // [kQB kQB] block reflector factor T
-  double* gram;  // [kQB kQB] inner products of the block's vectors
 };
 
 constexpr int kGroup = 8;
@@ -381,85 +376,33 @@ __device__ void qr_householder(double* P, int ld, int n, const QrScratch& s) {
 }
 
 // U <- Q = H_0 H_1 ... H_{n-1} (explicit), from the reflectors stored in P and tau.
-// Backward accumulation in blocks of kQB reflectors, each applied as the compact WY form
-// I - V T V^T (T upper triangular, LAPACK xLARFT forward/columnwise convention): per
-// column one pass computes the kQB inner products V^T u (independent chains), T (V^T u)
-// and the update; one barrier per block instead of one per reflector.
+// One barrier per reflector: the next reflector's vector is staged into the other half of
+// `vs` while the current one is applied.  (A compact-WY blocked variant was measured slower
+// here: its serial T-factor build per block outweighs the barriers it saves.)
 __device__ void form_q(const double* P, int ld, int n, double* U, const QrScratch& s) {
-  const int tid = threadIdx.x, g = tid / kGroup, sub = tid % kGroup;
+  const int g = threadIdx.x / kGroup, sub = threadIdx.x % kGroup;
   set_identity(U, ld, n);
-  const int nblk = (n + kQB - 1) / kQB;
-  for (int b = nblk - 1; b >= 0; --b) {
-    const int j0 = b * kQB;
-    const int nb = (n - j0 < kQB) ? n - j0 : kQB;
-    // stage V (column k = reflector j0 + k: zero above its unit entry); zero unused columns
-    for (int idx = tid; idx < kQB * n; idx += HQ_THREADS) {
-      const int k = idx / n, r = idx % n, j = j0 + k;
-      double v = 0.0;
-      if (k < nb) v = (r < j) ? 0.0 : (r == j ? 1.0 : P[(size_t)j * ld + r]);
-      s.vblk[idx] = v;
+  const int jl = n - 1;
+  for (int r = jl + threadIdx.x; r < n; r += HQ_THREADS) s.vs[(jl & 1) * n + r] = 1.0;
+  __syncthreads();
+  for (int j = n - 1; j >= 0; --j) {
+    const double* vc = s.vs + (j & 1) * n;
+    if (j > 0) {
+      double* vn = s.vs + ((j - 1) & 1) * n;
+      for (int r = j - 1 + threadIdx.x; r < n; r += HQ_THREADS) vn[r] = (r == j - 1) ? 1.0 : P[(size_t)(j - 1) * ld + r];
     }
-    for (int idx = tid; idx < kQB * kQB; idx += HQ_THREADS) s.tblk[idx] = 0.0;
-    __syncthreads();
-    // Gram entries v_i . v_k, i < k (v_k vanishes above row j0 + k)
-    const int npairs = nb * (nb - 1) / 2;
-    for (int base = 0; base < npairs; base += kGroups) {
-      const int pidx = base + g;
-      int pi = 0, pk = 1;
-      if (pidx < npairs) {
-        int rem = pidx;
-        pk = 1;
-        while (rem >= pk) { rem -= pk; ++pk; }
-        pi = rem;
+    const double tj = s.tau[j];
+    if (tj != 0.0) {
+      for (int base = j; base < n; base += kGroups) {
+        const int c = base + g;
+        double* uc = U + (size_t)c * ld;
+        double w = 0.0;
+        if (c < n)
+          for (int r = j + sub; r < n; r += kGroup) w = fma(vc[r], uc[r], w);
+        w = group_sum(w) * tj;
+        if (c < n)
+          for (int r = j + sub; r < n; r += kGroup) uc[r] = fma(-w, vc[r], uc[r]);
       }
-      double a = 0.0;
-      if (pidx < npairs)
-        for (int r = j0 + pk + sub; r < n; r += kGroup) a = fma(s.vblk[pi * n + r], s.vblk[pk * n + r], a);
-      a = group_sum(a);
-      if (pidx < npairs && sub == 0) s.gram[pi * kQB + pk] = a;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      for (int i = 0; i < nb; ++i) {
-        const double ti = s.tau[j0 + i];
-        s.tblk[i * kQB + i] = ti;
-        for (int r = 0; r < i; ++r) {
-          double acc = 0.0;
-          for (int q = r; q < i; ++q) acc = fma(s.tblk[r * kQB + q], s.gram[q * kQB + i], acc);
-          s.tblk[r * kQB + i] = -ti * acc;
-        }
-      }
-    }
-    __syncthreads();
-    for (int base = j0; base < n; base += kGroups) {
-      const int c = base + g;
-      double* uc = U + (size_t)c * ld;
-      double w[kQB];
-#pragma unroll
-      for (int k = 0; k < kQB; ++k) w[k] = 0.0;
-      if (c < n)
-        for (int r = j0 + sub; r < n; r += kGroup) {
-          const double u = uc[r];
-#pragma unroll
-          for (int k = 0; k < kQB; ++k) w[k] = fma(s.vblk[k * n + r], u, w[k]);
-        }
-#pragma unroll
-      for (int k = 0; k < kQB; ++k) w[k] = group_sum(w[k]);
-      double z[kQB];
-#pragma unroll
-      for (int i = 0; i < kQB; ++i) {
-        double a = 0.0;
-#pragma unroll
-        for (int k = i; k < kQB; ++k) a = fma(s.tblk[i * kQB + k], w[k], a);
-        z[i] = a;
-      }
-      if (c < n)
-        for (int r = j0 + sub; r < n; r += kGroup) {
-          double a = uc[r];
-#pragma unroll
-          for (int k = 0; k < kQB; ++k) a = fma(-s.vblk[k * n + r], z[k], a);
-          uc[r] = a;
-        }
     }
     __syncthreads();
   }

@@ -34,14 +34,14 @@ int section_cycles(unsigned long long* out, int n) {
 struct Smem {
   double *ex, *exi, *ey, *eyi;
   double *dl, *u2, *xn, *dlt, *es, *dcorr, *tau, *norm2, *rinv, *vs, *dv;
-  double *red, *scal, *vblk, *tblk, *gram;
+  double *red, *scal;
   int *perm, *piv, *sint;
 };
 
 static constexpr int kSmemVecs = 12;  // vs takes two
 
 __host__ __device__ inline size_t smem_layout_bytes(int nx, int ny, int n) {
-  return (size_t)(2 * nx * nx + 2 * ny * ny + kSmemVecs * n + 32 + 16 + kQB * n + 2 * kQB * kQB) * sizeof(double) +
+  return (size_t)(2 * nx * nx + 2 * ny * ny + kSmemVecs * n + 32 + 16) * sizeof(double) +
          (size_t)(2 * n + 8) * sizeof(int);
 }
 
@@ -68,9 +68,6 @@ __device__ inline Smem carve(const Dev& d, double* base) {
   s.dv = p; p += n;
   s.red = p; p += 32;
   s.scal = p; p += 16;
-  s.vblk = p; p += kQB * n;
-  s.tblk = p; p += kQB * kQB;
-  s.gram = p; p += kQB * kQB;
   int* q = reinterpret_cast<int*>(p);
   s.perm = q; q += n;
   s.piv = q; q += n;
@@ -139,7 +136,7 @@ __device__ double udv_top_down(const Dev& d, int c, const Smem& sm, const double
   double* Tc = chain_work(d, c, WK_T);
   double* Tn = chain_work(d, c, WK_T2);
   double* Q = chain_work(d, c, WK_M1);
-  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint, sm.vblk, sm.tblk, sm.gram};
+  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint};
   int hi = L, lo = ((L - 1) / nw) * nw;
   bool first = true;
   while (true) {
@@ -437,7 +434,7 @@ local_chunk_kernel(Dev d, int s0, int s1, uint32_t sweep, int measure) {
   HQ_TOC(rp, SEC_RESTAB_PROD);
   HQ_TIC(rq);
   double* Q = chain_work(d, c, WK_M1);
-  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint, sm.vblk, sm.tblk, sm.gram};
+  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint};
   prepivot(P, Q, n, n, qs, sm.norm2);
   qr_householder(Q, n, n, qs);
   form_q(Q, n, n, UR, qs);
@@ -586,7 +583,7 @@ __device__ double udv_top_down_cm(const Dev& d, int c, const Smem& sm, int site,
   double* Tn = chain_work(d, c, WK_T2);
   double* Q = chain_work(d, c, WK_M1);
   double* Y = chain_work(d, c, WK_M2);
-  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint, sm.vblk, sm.tblk, sm.gram};
+  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint};
   const double delta = expm1(-d.dtau * d.g * dx);
   HQ_TIC(cv);
   for (int s = threadIdx.x; s < L; s += HQ_THREADS) xs[s] = exp(-d.dtau * (d.g * (X[(size_t)s * n + site] + dx) - d.mu));
