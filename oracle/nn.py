@@ -1,0 +1,185 @@
+"""Learned effective action for network-driven moves (CPU oracle, FP64).
+
+TEST INFRASTRUCTURE ONLY (see oracle/dqmc.py): imported by tests/ and bench.py's CPU legs.
+
+Paper: "Local Updates" (a fully connected network fed the change of the field and the fields
+at nearby spacetime points predicts the weight change of a move) and the cumulative update of
+the benchmark section: after a number of network-driven sweeps the whole proposal X -> X' is
+accepted with min(1, p_c), p_c = [W(X')/W(X)] [exp(-beta E_NN[X]) / exp(-beta E_NN[X'])].
+
+Readings (also in the design notes):
+  * p_c needs E_NN to be one scalar function of the configuration, so the network does not
+    predict a weight change directly: it defines F(X) = sum_{i,l} f(patch_{i,l}(X)), and the
+    learned weight is W_eff(X) = exp(-dtau S_ph(X) + 2 F(X)) -- the phonon action is exact, F
+    stands for log|det M(X)| (one spin species; both species give the factor 2).  The change
+    of F under any move is exact: only patches that contain a changed field contribute.
+  * patch_{i,l}: X at the 5-site cross {i, i+x, i-x, i+y, i-y} on the 5 slices l-2..l+2
+    (periodic in space and imaginary time), 25 inputs ordered (slice offset, cross site),
+    shifted by the mean field: z = X + g / (M Omega^2).
+  * f: 25 -> 64 -> 64 -> 1 with ReLU hidden layers and a linear output; weights are stored in
+    bfloat16 (round to nearest even from float32), arithmetic here is FP64.
+  * Training fits F(X_a) to log|det M(X_a)| minus its sample mean, by mean squared error.
+"""
+import math
+
+import numpy as np
+
+N_IN = 25
+N_H = 64
+CROSS = ((0, 0), (1, 0), (-1, 0), (0, 1), (0, -1))
+DT = (-2, -1, 0, 1, 2)
+
+# parameter layout (flat float vector): W1[25][64], b1[64], W2[64][64], b2[64], W3[64], b3
+SHAPES = (("W1", (N_IN, N_H)), ("b1", (N_H,)), ("W2", (N_H, N_H)), ("b2", (N_H,)), ("W3", (N_H,)), ("b3", ()))
+N_PARAMS = sum(int(np.prod(s)) for _, s in SHAPES)
+
+
+def unflatten(theta):
+    theta = np.asarray(theta, dtype=np.float64)
+    out, o = {}, 0
+    for name, shape in SHAPES:
+        k = int(np.prod(shape))
+        out[name] = theta[o:o + k].reshape(shape) if shape else theta[o]
+        o += k
+    return out
+
+
+def flatten(params):
+    return np.concatenate([np.atleast_1d(np.asarray(params[name], dtype=np.float64)).ravel() for name, _ in SHAPES])
+
+
+def to_bfloat16(x):
+    """Round float values to bfloat16 (round to nearest, ties to even) and back to float64."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> np.uint64(16)) & np.uint64(1)
+    r = ((u + np.uint64(0x7FFF) + lsb) >> np.uint64(16)) << np.uint64(16)
+    return (r.astype(np.uint32)).view(np.float32).astype(np.float64).reshape(np.shape(x))
+
+
+def init_params(seed):
+    """He-style random initialisation (seeded), output layer small."""
+    rng = np.random.default_rng(seed)
+    p = {"W1": rng.standard_normal((N_IN, N_H)) * math.sqrt(2.0 / N_IN), "b1": np.zeros(N_H),
+         "W2": rng.standard_normal((N_H, N_H)) * math.sqrt(2.0 / N_H), "b2": np.zeros(N_H),
+         "W3": rng.standard_normal(N_H) * 0.01, "b3": 0.0}
+    return flatten(p)
+
+
+def x_shift(p):
+    """Mean-field shift of the inputs, z = X - x0 with x0 = -g / (M Omega^2)."""
+    return -p.g / (p.mass * p.omega ** 2)
+
+
+def patch_index(nx, ny, L):
+    """Flat indices into X[L][N] of every patch: array [L*N][25], row l*N + i."""
+    N = nx * ny
+    idx = np.empty((L * N, N_IN), dtype=np.int64)
+    for l in range(L):
+        for i in range(N):
+            x, y = i % nx, i // nx
+            k = 0
+            for dl in DT:
+                ll = (l + dl) % L
+                for cx, cy in CROSS:
+                    j = (x + cx) % nx + nx * ((y + cy) % ny)
+                    idx[l * N + i, k] = ll * N + j
+                    k += 1
+    return idx
+
+
+def mlp(theta, Z):
+    """f for a batch of inputs Z [B][25]; returns (out [B], cache for backprop)."""
+    P = unflatten(theta)
+    a1 = Z @ P["W1"] + P["b1"]
+    h1 = np.maximum(a1, 0.0)
+    a2 = h1 @ P["W2"] + P["b2"]
+    h2 = np.maximum(a2, 0.0)
+    out = h2 @ P["W3"] + P["b3"]
+    return out, (Z, a1, h1, a2, h2)
+
+
+def mlp_backward(theta, cache, dout):
+    """Gradient of sum_b dout[b] f(Z_b) with respect to the flat parameters."""
+    P = unflatten(theta)
+    Z, a1, h1, a2, h2 = cache
+    g = {"W3": h2.T @ dout, "b3": float(np.sum(dout))}
+    d2 = np.outer(dout, P["W3"]) * (a2 > 0)
+    g["W2"] = h1.T @ d2
+    g["b2"] = d2.sum(axis=0)
+    d1 = (d2 @ P["W2"].T) * (a1 > 0)
+    g["W1"] = Z.T @ d1
+    g["b1"] = d1.sum(axis=0)
+    return flatten(g)
+
+
+class EffectiveAction:
+    """F(X) = sum of f over all patches, for one lattice shape and parameter vector."""
+
+    def __init__(self, p, theta):
+        self.p = p
+        self.theta = np.asarray(theta, dtype=np.float64)
+        self.idx = patch_index(p.nx, p.ny, p.n_slices)
+        self.x0 = x_shift(p)
+
+    def inputs(self, X, rows=None):
+        Xf = np.asarray(X, dtype=np.float64).reshape(-1) - self.x0
+        ix = self.idx if rows is None else self.idx[rows]
+        return Xf[ix]
+
+    def patch_values(self, X):
+        return mlp(self.theta, self.inputs(X))[0]
+
+    def F(self, X):
+        return float(np.sum(self.patch_values(X)))
+
+    def rows_touching(self, sites_slices):
+        """Patch rows whose 25 inputs include any of the given (slice, site) points."""
+        pts = {l * self.p.n_sites + i for l, i in sites_slices}
+        return np.array([r for r in range(self.idx.shape[0]) if pts.intersection(self.idx[r])], dtype=np.int64)
+
+    def delta_local(self, X, l, i, x_new):
+        """F(X') - F(X) for X'(i, l) = x_new, from the 25 patches that contain (i, l)."""
+        rows = self._local_rows(l, i)
+        Xn = np.array(X, dtype=np.float64, copy=True)
+        Xn[l, i] = x_new
+        return float(np.sum(mlp(self.theta, self.inputs(Xn, rows))[0] - mlp(self.theta, self.inputs(X, rows))[0]))
+
+    def delta_block(self, X, i, dx):
+        """F(X') - F(X) for X'(i, .) = X(i, .) + dx, from the 5 L patches that contain site i."""
+        rows = self._block_rows(i)
+        Xn = np.array(X, dtype=np.float64, copy=True)
+        Xn[:, i] += dx
+        return float(np.sum(mlp(self.theta, self.inputs(Xn, rows))[0] - mlp(self.theta, self.inputs(X, rows))[0]))
+
+    def _local_rows(self, l, i):
+        p = self.p
+        x, y = i % p.nx, i // p.nx
+        rows = []
+        for dl in DT:
+            ll = (l - dl) % p.n_slices
+            for cx, cy in CROSS:
+                j = (x - cx) % p.nx + p.nx * ((y - cy) % p.ny)
+                rows.append(ll * p.n_sites + j)
+        return np.array(sorted(set(rows)), dtype=np.int64)
+
+    def _block_rows(self, i):
+        p = self.p
+        x, y = i % p.nx, i // p.nx
+        centers = sorted({(x - cx) % p.nx + p.nx * ((y - cy) % p.ny) for cx, cy in CROSS})
+        return np.array([l * p.n_sites + j for l in range(p.n_slices) for j in centers], dtype=np.int64)
+
+
+def loss_and_grad(p, theta, Xs, ys):
+    """Mean squared error (1/B) sum_a (F(X_a) - y_a)^2 and its gradient."""
+    act = EffectiveAction(p, theta)
+    B = len(Xs)
+    loss = 0.0
+    grad = np.zeros(N_PARAMS)
+    for X, y in zip(Xs, ys):
+        Z = act.inputs(X)
+        out, cache = mlp(theta, Z)
+        r = float(np.sum(out)) - y
+        loss += r * r / B
+        grad += mlp_backward(theta, cache, np.full(out.shape, 2.0 * r / B))
+    return loss, grad
