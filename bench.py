@@ -306,6 +306,16 @@ def run_ours(args):
             tau = json.load(f)
         indep = {"unit": "independent samples/s", "tau_source": os.path.relpath(tau_path, ROOT),
                  **{k: value / (2.0 * v) for k, v in tau["tau_int"].items()}}
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", f"traffic_global_phase_{args.workload}.json")
+    if dom == "block_moves" and os.path.exists(tr_path):
+        import hashlib
+        with open(tr_path) as f:
+            tr = json.load(f)
+        src = b"".join(open(os.path.join(ROOT, "paper_1905_07440_gb300", "csrc", x), "rb").read()
+                       for x in ("hq_kernels.cu", "hq_device.cuh"))
+        if hashlib.sha256(src).hexdigest()[:16] == tr["source_hash"] and chains == workload_params(args.workload)[1]:
+            traffic = tr["dram_bytes_per_launch"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_dev * 1e3 / args.steps, "higher_is_better": True,
@@ -319,7 +329,8 @@ def run_ours(args):
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": xbytes, "d2h_bytes_per_step": xbytes + obs_bytes},
         "gpu_launches": gpu_launches,
         "roofline": {"bound": "alu", "kernel": kernel_names[dom], "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, profiles/" + os.path.basename(tr_path),
                      "peak_source": "FP64 DFMA probe measured in this run (hq_fp64_peak_tflops)",
                      "flops_per_launch": fl, "ms_per_launch": per_launch_s * 1e3,
                      "share": ms / total_ms if total_ms else None},

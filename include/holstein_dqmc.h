@@ -201,6 +201,63 @@ int hq_get_timing(hq_engine* e, double* ms, int64_t* launches);
 int hq_logdet_noalloc(const hq_params* p, int n_chains, const double* X_device, double* logdet_device,
                       void* stream);
 
+/* ------------------------------------------------------------------------------------
+ * Learned effective action and cumulative (network-driven) moves.
+ *
+ * Paper, "Local Updates" and the cumulative update of the benchmark section: a network
+ * trained on configurations of the conventional sampler drives many moves, and the whole
+ * proposal X -> X' is then accepted with min(1, p_c),
+ *   p_c = [W(X')/W(X)] [exp(-beta E_NN[X]) / exp(-beta E_NN[X'])],
+ * so the chain samples the exact weight.  Here E_NN is the scalar
+ *   F(X) = sum_{i,l} f(patch_{i,l}(X)),  patch = X on the 5-site cross x 5 slices around
+ *   (i, l) minus the mean field -g/(M Omega^2),  f: 25 -> 64 -> 64 -> 1, ReLU, linear out,
+ * with bfloat16 weights and FP32 arithmetic; the inner chain samples exp(-dtau S_ph + 2F)
+ * with the exact phonon action and p_c = exp(2 [log|det M(X')| - log|det M(X)|] - 2 [F(X') - F(X)]).
+ * Parameters are a flat float vector: W1[25][64] (input k, unit u at k*64+u), b1[64],
+ * W2[64][64] (v*64+u), b2[64], W3[64], b3.  Inputs are ordered (slice offset -2..2) x
+ * (cross site: centre, +x, -x, +y, -y).  Requires nx, ny >= 4 and L >= 5.
+ * Random numbers: Philox tags 2 (inner local, event l*N+i), 3 (inner block, event i) with
+ * counter word 1 = step * n_inner + inner sweep, and 4 (cumulative accept, event 0, word 1 =
+ * step, u = the first uniform).
+ * ------------------------------------------------------------------------------------ */
+#define HQ_NN_PARAMS 5889
+
+typedef struct hq_learned_stats {   /* per chain, since the network state was attached */
+  int64_t inner_local_proposed, inner_local_accepted;
+  int64_t inner_block_proposed, inner_block_accepted;
+  int64_t cumulative_proposed, cumulative_accepted;
+  double last_pc;                    /* p_c of the last cumulative step */
+} hq_learned_stats;
+
+/* Device bytes of the network state for training minibatches of up to max_batch samples out
+ * of sets of up to max_samples (0 if the engine's lattice is too small for the patches). */
+size_t hq_nn_arena_bytes(const hq_engine* e, int max_batch, int max_samples);
+/* Attach a caller-owned, 256-byte aligned device arena of hq_nn_arena_bytes() bytes. */
+int hq_nn_attach(hq_engine* e, void* device_arena, size_t bytes, int max_batch, int max_samples);
+/* Set the parameters from HQ_NN_PARAMS host floats (rounded to bfloat16 for use; the FP32
+ * values are kept as the training master copy; the optimiser state is reset). */
+int hq_nn_set_params(hq_engine* e, const float* theta_host);
+/* FP32 master parameters, or with bf16 != 0 the bfloat16 values the kernels use. */
+int hq_nn_get_params(hq_engine* e, float* theta_host, int bf16);
+/* F(X) of every chain's current fields (host, n_chains doubles).  Synchronises. */
+int hq_nn_eval(hq_engine* e, double* F_host);
+/* Adam training (lr, beta1 0.9, beta2 0.999) of F towards targets y on samples X:
+ * X_device [n_samples][L][N] doubles and y_device [n_samples] doubles, device pointers of the
+ * engine's lattice; loss (1/B) sum (F(X_a) - y_a)^2 per minibatch of `batch` samples; epoch
+ * order from `seed`.  loss_host (optional): mean loss of each epoch.  Synchronises. */
+int hq_nn_train(hq_engine* e, const double* X_device, const double* y_device, int n_samples, int epochs,
+                int batch, float lr, uint64_t seed, double* loss_host);
+/* Gradient of (1/n) sum_a (F(X_a) - y_a)^2 over all n_samples (<= max_batch), no update:
+ * grad_host HQ_NN_PARAMS floats, loss_host one double.  Synchronises. */
+int hq_nn_gradient(hq_engine* e, const double* X_device, const double* y_device, int n_samples, float* grad_host,
+                   double* loss_host);
+/* n_steps cumulative steps of every chain: n_inner network-driven sweeps (flags HQ_LOCAL:
+ * a local move at every (l, i); HQ_GLOBAL: a block move at every site), then the exact
+ * accept of the cumulative move; HQ_MEASURE also records electronic observables after each
+ * step (one more stabilised G per step).  Asynchronous. */
+int hq_cumulative_sweep(hq_engine* e, int n_steps, int n_inner, unsigned flags);
+int hq_get_learned_stats(hq_engine* e, hq_learned_stats* out);
+
 /* Per-section device cycle counters (profiling builds compiled with -DHQ_SECTION_TIMING):
  * copies up to n counters (sum over CTAs of thread 0's clock64 spans; ids in
  * csrc/hq_device.cuh) to out and clears them.  Returns the number copied; 0 in normal

@@ -24,7 +24,7 @@ enum {
   SEC_COUNT
 };
 #ifdef HQ_SECTION_TIMING
-__device__ unsigned long long g_section_cycles[SEC_COUNT];  // one translation unit includes this header
+static __device__ unsigned long long g_section_cycles[SEC_COUNT];  // per translation unit
 #define HQ_TIC(name) const long long hq_tic_##name = clock64()
 #define HQ_TOC(name, slot)                                                              \
   do {                                                                                \
@@ -119,7 +119,7 @@ enum { KIN_PLAIN = 0, KIN_SCALE_BEFORE = 1, KIN_SCALE_AFTER = 2 };
 // KIN_SCALE_BEFORE the rows are first multiplied by d (P <- E diag(d) P, a slice matrix
 // B = exp(-dtau K) exp(-dtau V)); with KIN_SCALE_AFTER afterwards (P <- diag(d) E P = B^T P).
 template <int LMAX, int MODE>
-__device__ void kin_rows(double* P, int ld, int ncols, const double* ex, const double* ey, int nx, int ny,
+__device__ inline void kin_rows(double* P, int ld, int ncols, const double* ex, const double* ey, int nx, int ny,
                          const double* d = nullptr) {
   for (int line = threadIdx.x; line < ny * ncols; line += HQ_THREADS) {
     const int y = line % ny, j = line / ny;
@@ -165,7 +165,7 @@ __device__ void kin_rows(double* P, int ld, int ncols, const double* ex, const d
 
 // P <- P (F_x (x) F_y)  (acts on the column index of every row); F given row-major.
 template <int LMAX>
-__device__ void kin_cols(double* P, int ld, int nrows, const double* fx, const double* fy, int nx, int ny) {
+__device__ inline void kin_cols(double* P, int ld, int nrows, const double* fx, const double* fy, int nx, int ny) {
   for (int line = threadIdx.x; line < nrows * ny; line += HQ_THREADS) {
     const int r = line % nrows, y = line / nrows;
     double* base = P + (size_t)(nx * y) * ld + r;
@@ -268,7 +268,7 @@ __device__ __forceinline__ double group_sum(double v) {
 // Q <- columns of P ordered by decreasing norm (stable: ties keep index order); perm
 // records the order.  Norms are compared through their IEEE bit patterns, which order
 // non-negative doubles exactly like their values.  `norm2` is n doubles of scratch.
-__device__ void prepivot(const double* P, double* Q, int ld, int n, const QrScratch& s, double* norm2) {
+__device__ inline void prepivot(const double* P, double* Q, int ld, int n, const QrScratch& s, double* norm2) {
   const int g = threadIdx.x / kGroup, sub = threadIdx.x % kGroup;
   for (int base = 0; base < n; base += kGroups) {
     const int c = base + g;
@@ -337,7 +337,7 @@ __device__ __forceinline__ void house_gen(double* P, int ld, int n, int j, doubl
 // One barrier per column with look-ahead: during step j, warp 0 applies reflector j to
 // column j+1 and builds reflector j+1 while warps 1.. apply reflector j to columns j+2..
 // (two vector buffers in `vs`, 2n doubles).
-__device__ void qr_householder(double* P, int ld, int n, const QrScratch& s) {
+__device__ inline void qr_householder(double* P, int ld, int n, const QrScratch& s) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = (tid - 32) / kGroup, sub = tid % kGroup;  // groups of warps 1..
   constexpr int kTailGroups = (HQ_THREADS - 32) / kGroup;
@@ -379,7 +379,7 @@ __device__ void qr_householder(double* P, int ld, int n, const QrScratch& s) {
 // One barrier per reflector: the next reflector's vector is staged into the other half of
 // `vs` while the current one is applied.  (A compact-WY blocked variant was measured slower
 // here: its serial T-factor build per block outweighs the barriers it saves.)
-__device__ void form_q(const double* P, int ld, int n, double* U, const QrScratch& s) {
+__device__ inline void form_q(const double* P, int ld, int n, double* U, const QrScratch& s) {
   const int g = threadIdx.x / kGroup, sub = threadIdx.x % kGroup;
   set_identity(U, ld, n);
   const int jl = n - 1;
@@ -412,7 +412,7 @@ __device__ void form_q(const double* P, int ld, int n, double* U, const QrScratc
 // (T' = D^-1 R Pi^T).  With Tprev == nullptr, Tout = T'.  Each thread produces four
 // outputs of one row j (four independent FMA chains); lanes of a warp share j or j+1, so
 // trip counts stay nearly uniform.
-__device__ void t_update(const double* P, int ld, int n, const QrScratch& s, double* D,
+__device__ inline void t_update(const double* P, int ld, int n, const QrScratch& s, double* D,
                          const double* Tprev, double* Tout) {
   for (int j = threadIdx.x; j < n; j += HQ_THREADS) {
     const double dj = fabs(P[(size_t)j * ld + j]);
@@ -466,7 +466,7 @@ __device__ void t_update(const double* P, int ld, int n, const QrScratch& s, dou
 // ------------------------------------------------------------- LU and triangular solves
 // In-place LU with partial (row) pivoting.  piv[j] = row swapped with j at step j.
 // Returns sum_j log|U_jj| (same value in every thread).
-__device__ double lu_logdet(double* A, int ld, int n, int* piv, int* sint, double* red) {
+__device__ inline double lu_logdet(double* A, int ld, int n, int* piv, int* sint, double* red) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int j = 0; j < n; ++j) {
     double* aj = A + (size_t)j * ld;
@@ -515,7 +515,7 @@ __device__ double lu_logdet(double* A, int ld, int n, int* piv, int* sint, doubl
 }
 
 // Y <- A^-1 Y for the LU factors from lu_logdet (n right-hand sides, one warp per column).
-__device__ void lu_solve(const double* A, int ld, int n, const int* piv, double* Y) {
+__device__ inline void lu_solve(const double* A, int ld, int n, const int* piv, double* Y) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int c = warp; c < n; c += HQ_WARPS) {
     double* y = Y + (size_t)c * ld;
@@ -548,7 +548,7 @@ __device__ void lu_solve(const double* A, int ld, int n, const int* piv, double*
 // C = op(A) op(B) for n x n column-major operands (n a multiple of 4: n = nx*ny with
 // even sides); each thread accumulates 4x4 tiles.
 template <bool TA, bool TB>
-__device__ void gemm_nn(int n, const double* A, const double* B, double* C, int ld) {
+__device__ inline void gemm_nn(int n, const double* A, const double* B, double* C, int ld) {
   const int tiles = n >> 2;
   for (int t = threadIdx.x; t < tiles * tiles; t += HQ_THREADS) {
     const int r0 = (t % tiles) * 4, c0 = (t / tiles) * 4;

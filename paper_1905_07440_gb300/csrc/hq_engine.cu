@@ -30,6 +30,12 @@ struct hq_engine {
   std::vector<cudaEvent_t> spare;
   double phase_ms[HQ_N_PHASES] = {0, 0, 0, 0};
   long long phase_launches[HQ_N_PHASES] = {0, 0, 0, 0};
+  // learned effective action (optional)
+  bool nn_on = false;
+  hq::NNState nn{};
+  int nn_max_batch = 0, nn_max_samples = 0;
+  long long cum_steps = 0;
+  int nn_t_step = 0;
   ~hq_engine() {
     for (auto& s : spans) { cudaEventDestroy(s.a); cudaEventDestroy(s.b); }
     for (auto ev : spare) cudaEventDestroy(ev);
@@ -645,6 +651,261 @@ int hq_logdet_noalloc(const hq_params* p, int n_chains, const double* X_device, 
   if (st != cudaSuccess) {
     g_call_error = std::string("hq_logdet_noalloc: ") + cudaGetErrorString(st);
     return HQ_ECUDA;
+  }
+  return HQ_OK;
+}
+
+// ----------------------------------------------------------------- learned moves
+namespace {
+
+constexpr int kNNParamsPad = (HQ_NN_PARAMS + 3) & ~3;
+
+struct NNLayout {
+  size_t wbf, master, grad, am, av, partials, fcache, fnew, X0, ld0, F0, F1, pc, Fb, loss, idx, counters, total;
+};
+
+NNLayout nn_layout(const hq::Dev& d, int max_batch, int max_samples) {
+  NNLayout l{};
+  const size_t C = d.n_chains, NL = (size_t)d.n * d.L, P = kNNParamsPad;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes); return o; };
+  l.wbf = take(2 * P);
+  l.master = take(4 * P);
+  l.grad = take(4 * P);
+  l.am = take(4 * P);
+  l.av = take(4 * P);
+  l.partials = take(4 * P * hq::kNNTrainCtas);
+  l.fcache = take(4 * C * NL);
+  l.fnew = take(4 * C * 5 * d.L);
+  l.X0 = take(8 * C * NL);
+  l.ld0 = take(8 * C);
+  l.F0 = take(8 * C);
+  l.F1 = take(8 * C);
+  l.pc = take(8 * C);
+  l.Fb = take(8 * (size_t)max_batch);
+  l.loss = take(8);
+  l.idx = take(4 * (size_t)max_samples);
+  l.counters = take(8 * C * hq::kNNCounters);
+  l.total = off;
+  return l;
+}
+
+bool nn_shape_ok(const hq::Dev& d) { return d.nx >= 4 && d.ny >= 4 && d.L >= 5; }
+
+int nn_ready(hq_engine* e) {
+  if (!e) return HQ_EINVAL;
+  if (!e->nn_on) return set_err(e, HQ_EINVAL, "no network state attached (hq_nn_attach)");
+  return HQ_OK;
+}
+
+uint64_t splitmix64(uint64_t& x) {
+  uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+}  // namespace
+
+size_t hq_nn_arena_bytes(const hq_engine* e, int max_batch, int max_samples) {
+  if (!e || max_batch < 1 || max_samples < max_batch || !nn_shape_ok(e->d)) return 0;
+  return nn_layout(e->d, max_batch, max_samples).total;
+}
+
+int hq_nn_attach(hq_engine* e, void* arena, size_t bytes, int max_batch, int max_samples) {
+  if (!e || max_batch < 1 || max_samples < max_batch) return HQ_EINVAL;
+  if (!nn_shape_ok(e->d)) return set_err(e, HQ_EINVAL, "learned moves need nx, ny >= 4 and L >= 5");
+  const NNLayout l = nn_layout(e->d, max_batch, max_samples);
+  if (!arena || bytes < l.total || ((uintptr_t)arena % kAlign) != 0) return HQ_ENOMEM;
+  char* a = (char*)arena;
+  hq::NNState& nn = e->nn;
+  nn.wbf = (uint16_t*)(a + l.wbf);
+  nn.master = (float*)(a + l.master);
+  nn.grad = (float*)(a + l.grad);
+  nn.adam_m = (float*)(a + l.am);
+  nn.adam_v = (float*)(a + l.av);
+  nn.partials = (float*)(a + l.partials);
+  nn.fcache = (float*)(a + l.fcache);
+  nn.fnew = (float*)(a + l.fnew);
+  nn.X0 = (double*)(a + l.X0);
+  nn.ld0 = (double*)(a + l.ld0);
+  nn.F0 = (double*)(a + l.F0);
+  nn.F1 = (double*)(a + l.F1);
+  nn.last_pc = (double*)(a + l.pc);
+  nn.Fb = (double*)(a + l.Fb);
+  nn.loss = (double*)(a + l.loss);
+  nn.idx = (int*)(a + l.idx);
+  nn.counters = (long long*)(a + l.counters);
+  nn.x0 = -e->p.g / (e->p.mass * e->p.omega * e->p.omega);
+  int rc = cuda_check(e, cudaMemsetAsync(a, 0, l.total, e->stream), "nn arena clear");
+  if (rc) return rc;
+  e->nn_on = true;
+  e->nn_max_batch = max_batch;
+  e->nn_max_samples = max_samples;
+  e->cum_steps = 0;
+  e->nn_t_step = 0;
+  return HQ_OK;
+}
+
+int hq_nn_set_params(hq_engine* e, const float* theta_host) {
+  int rc = nn_ready(e);
+  if (rc) return rc;
+  if (!theta_host) return HQ_EINVAL;
+  rc = cuda_check(e, cudaMemcpyAsync(e->nn.partials, theta_host, sizeof(float) * HQ_NN_PARAMS,
+                                     cudaMemcpyHostToDevice, e->stream), "nn params upload");
+  rc = rc ? rc : cuda_check(e, hq::nn_launch_set(e->nn, e->nn.partials, e->stream), "nn set");
+  rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "nn set sync");
+  e->nn_t_step = 0;
+  return rc;
+}
+
+int hq_nn_get_params(hq_engine* e, float* theta_host, int bf16) {
+  int rc = nn_ready(e);
+  if (rc) return rc;
+  if (!theta_host) return HQ_EINVAL;
+  if (bf16) {
+    std::vector<uint16_t> h(HQ_NN_PARAMS);
+    rc = cuda_check(e, cudaMemcpyAsync(h.data(), e->nn.wbf, 2 * HQ_NN_PARAMS, cudaMemcpyDeviceToHost, e->stream),
+                    "nn params copy");
+    rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "nn params sync");
+    if (rc) return rc;
+    for (int k = 0; k < HQ_NN_PARAMS; ++k) {
+      const uint32_t u = (uint32_t)h[k] << 16;
+      std::memcpy(&theta_host[k], &u, 4);
+    }
+    return HQ_OK;
+  }
+  rc = cuda_check(e, cudaMemcpyAsync(theta_host, e->nn.master, 4 * HQ_NN_PARAMS, cudaMemcpyDeviceToHost, e->stream),
+                  "nn params copy");
+  return rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "nn params sync");
+}
+
+int hq_nn_eval(hq_engine* e, double* F_host) {
+  int rc = nn_ready(e);
+  if (rc) return rc;
+  if (!F_host) return HQ_EINVAL;
+  rc = cuda_check(e, hq::nn_launch_eval(e->d, e->nn, e->d.X, e->nn.F0, 1, e->stream), "nn eval");
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(F_host, e->nn.F0, sizeof(double) * e->d.n_chains,
+                                               cudaMemcpyDeviceToHost, e->stream), "nn eval copy");
+  return rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "nn eval sync");
+}
+
+int hq_nn_gradient(hq_engine* e, const double* X_device, const double* y_device, int n_samples, float* grad_host,
+                   double* loss_host) {
+  int rc = nn_ready(e);
+  if (rc) return rc;
+  if (!X_device || !y_device || n_samples < 1 || n_samples > e->nn_max_batch) return HQ_EINVAL;
+  std::vector<int> idx(n_samples);
+  for (int a = 0; a < n_samples; ++a) idx[a] = a;
+  rc = cuda_check(e, cudaMemcpyAsync(e->nn.idx, idx.data(), sizeof(int) * n_samples, cudaMemcpyHostToDevice,
+                                     e->stream), "nn idx");
+  rc = rc ? rc : cuda_check(e, cudaMemsetAsync(e->nn.loss, 0, sizeof(double), e->stream), "nn loss clear");
+  rc = rc ? rc : cuda_check(e, hq::nn_launch_batch(e->d, e->nn, X_device, y_device, e->nn.idx, n_samples, 0.f, 1,
+                                                    e->stream), "nn batch");
+  rc = rc ? rc : cuda_check(e, hq::nn_launch_loss(e->nn, y_device, e->nn.idx, n_samples, 1.0 / n_samples, e->stream),
+                            "nn loss");
+  if (!rc && grad_host)
+    rc = cuda_check(e, cudaMemcpyAsync(grad_host, e->nn.grad, 4 * HQ_NN_PARAMS, cudaMemcpyDeviceToHost, e->stream),
+                    "nn grad copy");
+  if (!rc && loss_host)
+    rc = cuda_check(e, cudaMemcpyAsync(loss_host, e->nn.loss, sizeof(double), cudaMemcpyDeviceToHost, e->stream),
+                    "nn loss copy");
+  return rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "nn grad sync");
+}
+
+int hq_nn_train(hq_engine* e, const double* X_device, const double* y_device, int n_samples, int epochs, int batch,
+                float lr, uint64_t seed, double* loss_host) {
+  int rc = nn_ready(e);
+  if (rc) return rc;
+  if (!X_device || !y_device || n_samples < 1 || n_samples > e->nn_max_samples || epochs < 0 || batch < 1 ||
+      batch > e->nn_max_batch || !(lr > 0.f))
+    return HQ_EINVAL;
+  std::vector<int> order(n_samples);
+  uint64_t st = seed;
+  for (int ep = 0; ep < epochs; ++ep) {
+    for (int a = 0; a < n_samples; ++a) order[a] = a;
+    for (int a = n_samples - 1; a > 0; --a) {  // Fisher-Yates with splitmix64
+      const int b = (int)(splitmix64(st) % (uint64_t)(a + 1));
+      std::swap(order[a], order[b]);
+    }
+    rc = cuda_check(e, cudaMemcpyAsync(e->nn.idx, order.data(), sizeof(int) * n_samples, cudaMemcpyHostToDevice,
+                                       e->stream), "nn order");
+    rc = rc ? rc : cuda_check(e, cudaMemsetAsync(e->nn.loss, 0, sizeof(double), e->stream), "nn loss clear");
+    if (rc) return rc;
+    for (int a0 = 0; a0 + batch <= n_samples; a0 += batch) {
+      rc = cuda_check(e, hq::nn_launch_batch(e->d, e->nn, X_device, y_device, e->nn.idx + a0, batch, lr,
+                                             ++e->nn_t_step, e->stream), "nn batch");
+      rc = rc ? rc : cuda_check(e, hq::nn_launch_loss(e->nn, y_device, e->nn.idx + a0, batch,
+                                                      1.0 / (double)(n_samples / batch * batch), e->stream), "nn loss");
+      if (rc) return rc;
+    }
+    if (loss_host) {
+      rc = cuda_check(e, cudaMemcpyAsync(&loss_host[ep], e->nn.loss, sizeof(double), cudaMemcpyDeviceToHost,
+                                         e->stream), "nn loss copy");
+      rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "nn epoch sync");
+      if (rc) return rc;
+    }
+  }
+  return cuda_check(e, cudaStreamSynchronize(e->stream), "nn train sync");
+}
+
+int hq_cumulative_sweep(hq_engine* e, int n_steps, int n_inner, unsigned flags) {
+  int rc = nn_ready(e);
+  if (rc) return rc;
+  if (n_steps < 0 || n_inner < 1 || (flags & ~(HQ_LOCAL | HQ_GLOBAL | HQ_MEASURE))) return HQ_EINVAL;
+  const hq::Dev& d = e->d;
+  const size_t fbytes = sizeof(double) * (size_t)d.n_chains * d.L * d.n;
+  for (int k = 0; k < n_steps; ++k) {
+    if (!e->logdet_valid) {
+      rc = ensure_state(e);
+      if (rc) return rc;
+    }
+    const uint32_t step = (uint32_t)e->cum_steps;
+    rc = cuda_check(e, cudaMemcpyAsync(e->nn.X0, d.X, fbytes, cudaMemcpyDeviceToDevice, e->stream), "X0 copy");
+    rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(e->nn.ld0, d.logdet, sizeof(double) * d.n_chains,
+                                                 cudaMemcpyDeviceToDevice, e->stream), "ld0 copy");
+    rc = rc ? rc : cuda_check(e, hq::nn_launch_eval(d, e->nn, d.X, e->nn.F0, 1, e->stream), "nn eval F0");
+    rc = rc ? rc : cuda_check(e, hq::nn_launch_inner(d, e->nn, n_inner, step * (uint32_t)n_inner,
+                                                     (flags & HQ_LOCAL) ? 1 : 0, (flags & HQ_GLOBAL) ? 1 : 0,
+                                                     e->stream), "nn inner");
+    rc = rc ? rc : cuda_check(e, hq::nn_launch_eval(d, e->nn, d.X, e->nn.F1, 0, e->stream), "nn eval F1");
+    e->stack_valid = false;
+    rc = rc ? rc : ensure_state(e);  // log|det M(X')| (and G, stack of X')
+    rc = rc ? rc : cuda_check(e, hq::nn_launch_decide(d, e->nn, step, e->stream), "nn decide");
+    if (rc) return rc;
+    e->stack_valid = e->green_valid = false;  // fields may have been restored to X
+    e->logdet_valid = true;
+    const bool meas = flags & HQ_MEASURE;
+    if (meas) {
+      rc = ensure_state(e);
+      rc = rc ? rc : cuda_check(e, hq::launch_measure_g0(d, e->stream), "measure");
+      if (rc) return rc;
+    }
+    const int slot = e->series_len < d.max_series ? e->series_len : -1;
+    rc = cuda_check(e, hq::launch_sweep_end(d, slot, meas ? 1 : 0, e->stream), "sweep_end launch");
+    if (rc) return rc;
+    if (slot >= 0) e->series_len++;
+    e->cum_steps++;
+  }
+  return HQ_OK;
+}
+
+int hq_get_learned_stats(hq_engine* e, hq_learned_stats* out) {
+  int rc = nn_ready(e);
+  if (rc) return rc;
+  if (!out) return HQ_EINVAL;
+  const size_t C = e->d.n_chains;
+  std::vector<long long> cnt(C * hq::kNNCounters);
+  std::vector<double> pc(C);
+  rc = cuda_check(e, cudaMemcpyAsync(cnt.data(), e->nn.counters, sizeof(long long) * cnt.size(),
+                                     cudaMemcpyDeviceToHost, e->stream), "nn counters");
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(pc.data(), e->nn.last_pc, sizeof(double) * C, cudaMemcpyDeviceToHost,
+                                               e->stream), "nn pc");
+  rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "nn stats sync");
+  if (rc) return rc;
+  for (size_t c = 0; c < C; ++c) {
+    const long long* k = cnt.data() + c * hq::kNNCounters;
+    out[c] = hq_learned_stats{k[0], k[1], k[2], k[3], k[4], k[5], pc[c]};
   }
   return HQ_OK;
 }

@@ -73,6 +73,30 @@ inline bool chunk_propagators_pay(int nx, int ny, int L, int n_wrap) {
   return cm < 0.9 * sep;
 }
 
+// State of the learned effective action and the cumulative sampler (separate device arena).
+constexpr int kNNCounters = 6;   // inner local prop/acc, inner block prop/acc, cumulative prop/acc
+constexpr int kNNTrainCtas = 256;
+struct NNState {
+  uint16_t* wbf;        // bfloat16 weights used by every kernel
+  float* master;        // FP32 master weights (training)
+  float* grad;          // last gradient
+  float* adam_m;
+  float* adam_v;
+  float* partials;      // [kNNTrainCtas][padded params] per-CTA gradient partials
+  float* fcache;        // [C][L N] f of every patch of the current fields
+  float* fnew;          // [C][5 L] block-move scratch
+  double* X0;           // [C][L N] fields at the start of a cumulative step
+  double* ld0;          // [C]
+  double* F0;           // [C]
+  double* F1;           // [C]
+  double* last_pc;      // [C]
+  double* Fb;           // [max batch] minibatch F
+  double* loss;         // [1] epoch loss accumulator
+  int* idx;             // [max samples] minibatch order
+  long long* counters;  // [C][kNNCounters]
+  double x0;            // input shift -g/(M Omega^2)
+};
+
 size_t smem_bytes(const Dev& d);
 
 // Launchers (asynchronous on the stream).  Return cudaGetLastError().
@@ -85,6 +109,16 @@ cudaError_t launch_log_weight(const Dev& d, double* out_logw, cudaStream_t s);
 cudaError_t launch_proposals(uint32_t key0, uint32_t key1, uint32_t chain, uint32_t sweep, uint32_t tag,
                              const uint32_t* events, int n, double* u1, double* u2, cudaStream_t s);
 double fp64_probe_tflops(int kind, int reps, cudaStream_t s);
+cudaError_t launch_measure_g0(const Dev& d, cudaStream_t s);
+cudaError_t nn_launch_eval(const Dev& d, const NNState& nn, const double* X, double* F, int write_cache,
+                           cudaStream_t s);
+cudaError_t nn_launch_inner(const Dev& d, const NNState& nn, int n_inner, uint32_t first_isweep, int do_local,
+                            int do_block, cudaStream_t s);
+cudaError_t nn_launch_decide(const Dev& d, const NNState& nn, uint32_t step, cudaStream_t s);
+cudaError_t nn_launch_set(const NNState& nn, const float* src_device, cudaStream_t s);
+cudaError_t nn_launch_batch(const Dev& d, const NNState& nn, const double* Xs, const double* ys, const int* idx,
+                            int B, float lr, int t_step, cudaStream_t s);
+cudaError_t nn_launch_loss(const NNState& nn, const double* ys, const int* idx, int B, double scale, cudaStream_t s);
 int section_cycles(unsigned long long* out, int n);
 size_t noalloc_scratch_needed(int nx, int ny, int n_chains);
 // log|det M| per chain with all scratch in the library's static device array (no allocation).

@@ -816,6 +816,15 @@ __global__ void __launch_bounds__(HQ_THREADS) sweep_end_kernel(Dev d, int slot, 
   }
 }
 
+// Electronic observables from G_0 of every chain (after a stack build).
+template <int LMAX>
+__global__ void __launch_bounds__(HQ_THREADS) measure_g0_kernel(Dev d) {
+  extern __shared__ double smraw[];
+  const Smem sm = carve(d, smraw);
+  const int c = blockIdx.x;
+  measure_green(d, c, sm, d.G + (size_t)c * d.n * d.n);
+}
+
 __global__ void reset_acc_kernel(Dev d) {
   const int c = blockIdx.x;
   for (int o = threadIdx.x; o < kAccSlots; o += blockDim.x) d.acc[(size_t)c * kAccSlots + o] = 0.0;
@@ -980,6 +989,11 @@ cudaError_t launch_global_phase(const Dev& d, uint32_t sweep, cudaStream_t s) {
     case 8: return launch_phase<8>(d, sweep, s);
     default: return launch_phase<16>(d, sweep, s);
   }
+}
+
+cudaError_t launch_measure_g0(const Dev& d, cudaStream_t s) {
+  HQ_DISPATCH(measure_g0_kernel, d, s, d);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sweep_end(const Dev& d, int slot, int measured, cudaStream_t s) {
