@@ -24,6 +24,13 @@ import math
 
 import numpy as np
 
+from . import dqmc
+from .philox import proposal_uniforms
+
+TAG_NN_LOCAL = 2
+TAG_NN_BLOCK = 3
+TAG_CUMULATIVE = 4
+
 N_IN = 25
 N_H = 64
 CROSS = ((0, 0), (1, 0), (-1, 0), (0, 1), (0, -1))
@@ -183,3 +190,61 @@ def loss_and_grad(p, theta, Xs, ys):
         loss += r * r / B
         grad += mlp_backward(theta, cache, np.full(out.shape, 2.0 * r / B))
     return loss, grad
+
+
+class CumulativeChain:
+    """The network-driven sampler with the exact cumulative accept (paper, NNMC section).
+
+    Inner moves are Metropolis moves on exp(-dtau S_ph + 2F) (exact phonon action, learned F);
+    after n_inner inner sweeps the proposal X -> X' is accepted with min(1, p_c),
+    p_c = exp(2 [log|det M(X')| - log|det M(X)|] - 2 [F(X') - F(X)]).  The smallest relative
+    distance |u - p| / p of any decision is kept in min_margin (for parity checks).
+    """
+
+    def __init__(self, p, X, theta, chain=0):
+        self.p = p
+        self.X = np.array(X, dtype=np.float64, copy=True)
+        self.chain = int(chain)
+        self.act = EffectiveAction(p, theta)
+        self.expK, _ = dqmc.kinetic_propagators(p)
+        self.logdet = dqmc.log_det_M(p, self.expK, self.X)
+        self.min_margin = math.inf
+
+    def _decide(self, u, prob):
+        self.min_margin = min(self.min_margin, abs(u - prob) / max(prob, 1e-300))
+        return bool(u < prob)
+
+    def step(self, k, n_inner, local=True, block=True):
+        p, X = self.p, self.X
+        L, N = X.shape
+        X0 = X.copy()
+        ld0, F0 = self.logdet, self.act.F(X0)
+        for u in range(n_inner):
+            isw = k * n_inner + u
+            if local:
+                for s in range(L):
+                    u1, u2 = proposal_uniforms(p.seed, self.chain, isw, s * N + np.arange(N), TAG_NN_LOCAL)
+                    for i in range(N):
+                        xn = X[s, i] + p.dx_local * (2.0 * u1[i] - 1.0)
+                        dS = dqmc.local_action_change(p, X, s, i, xn)
+                        dF = self.act.delta_local(X, s, i, xn)
+                        if self._decide(u2[i], math.exp(min(2.0 * dF - dS, 709.0))):
+                            X[s, i] = xn
+            if block:
+                u1, u2 = proposal_uniforms(p.seed, self.chain, isw, np.arange(N), TAG_NN_BLOCK)
+                for i in range(N):
+                    dx = p.dx_global * (2.0 * u1[i] - 1.0)
+                    dS = dqmc.global_action_change(p, X, i, dx)
+                    dF = self.act.delta_block(X, i, dx)
+                    if self._decide(u2[i], math.exp(min(2.0 * dF - dS, 709.0))):
+                        X[:, i] += dx
+        ld1, F1 = dqmc.log_det_M(p, self.expK, X), self.act.F(X)
+        pc = math.exp(min(2.0 * (ld1 - ld0) - 2.0 * (F1 - F0), 709.0))
+        uc, _ = proposal_uniforms(p.seed, self.chain, k, [0], TAG_CUMULATIVE)
+        accepted = self._decide(float(uc[0]), pc)
+        if accepted:
+            self.logdet = ld1
+        else:
+            X[:] = X0
+            self.logdet = ld0
+        return pc, accepted

@@ -52,6 +52,15 @@ class hq_obs(ctypes.Structure):
                 ("logdet", ctypes.c_double), ("status", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
+class hq_learned_stats(ctypes.Structure):
+    _fields_ = [("inner_local_proposed", ctypes.c_int64), ("inner_local_accepted", ctypes.c_int64),
+                ("inner_block_proposed", ctypes.c_int64), ("inner_block_accepted", ctypes.c_int64),
+                ("cumulative_proposed", ctypes.c_int64), ("cumulative_accepted", ctypes.c_int64),
+                ("last_pc", ctypes.c_double)]
+
+
+HQ_NN_PARAMS = 5889
+
 _P = ctypes.POINTER
 _dp = _P(ctypes.c_double)
 _vp = ctypes.c_void_p
@@ -79,6 +88,16 @@ _SIGNATURES = {
     "hq_fp64_peak_tflops": (ctypes.c_double, [ctypes.c_int, ctypes.c_int, _vp]),
     "hq_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "hq_logdet_noalloc": (ctypes.c_int, [_P(hq_params), ctypes.c_int, _vp, _vp, _vp]),
+    "hq_nn_arena_bytes": (ctypes.c_size_t, [_vp, ctypes.c_int, ctypes.c_int]),
+    "hq_nn_attach": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int]),
+    "hq_nn_set_params": (ctypes.c_int, [_vp, _P(ctypes.c_float)]),
+    "hq_nn_get_params": (ctypes.c_int, [_vp, _P(ctypes.c_float), ctypes.c_int]),
+    "hq_nn_eval": (ctypes.c_int, [_vp, _dp]),
+    "hq_nn_train": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                   ctypes.c_uint64, _dp]),
+    "hq_nn_gradient": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _P(ctypes.c_float), _dp]),
+    "hq_cumulative_sweep": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint]),
+    "hq_get_learned_stats": (ctypes.c_int, [_vp, _P(hq_learned_stats)]),
     "hq_get_section_cycles": (ctypes.c_int, [_P(ctypes.c_uint64), ctypes.c_int]),
     "hq_get_timing": (ctypes.c_int, [_vp, _dp, _P(ctypes.c_int64)]),
 }
@@ -237,6 +256,59 @@ class Engine:
         n = (ctypes.c_int64 * HQ_N_PHASES)()
         self._check(self.lib.hq_get_timing(self._h, _dptr(ms), n), "hq_get_timing")
         return {PHASES[i]: (float(ms[i]), int(n[i])) for i in range(HQ_N_PHASES)}
+
+    # ------------------------------------------------------------ learned moves
+    def attach_network(self, max_batch=64, max_samples=4096):
+        """Allocate (PyTorch) and attach the network state for training and cumulative moves."""
+        import torch
+        nb = self.lib.hq_nn_arena_bytes(self._h, int(max_batch), int(max_samples))
+        if nb == 0:
+            raise HQError("learned moves need nx, ny >= 4 and L >= 5")
+        self.nn_arena = torch.empty(nb + 256, dtype=torch.uint8, device=self.arena.device)
+        base = (self.nn_arena.data_ptr() + 255) // 256 * 256
+        self._check(self.lib.hq_nn_attach(self._h, ctypes.c_void_p(base), nb, int(max_batch), int(max_samples)),
+                    "hq_nn_attach")
+
+    def set_params(self, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        assert t.size == HQ_NN_PARAMS
+        self._check(self.lib.hq_nn_set_params(self._h, t.ctypes.data_as(_P(ctypes.c_float))), "hq_nn_set_params")
+
+    def get_params(self, bf16=False):
+        t = np.empty(HQ_NN_PARAMS, dtype=np.float32)
+        self._check(self.lib.hq_nn_get_params(self._h, t.ctypes.data_as(_P(ctypes.c_float)), 1 if bf16 else 0),
+                    "hq_nn_get_params")
+        return t
+
+    def nn_eval(self):
+        F = np.empty(self.n_chains)
+        self._check(self.lib.hq_nn_eval(self._h, _dptr(F)), "hq_nn_eval")
+        return F
+
+    def nn_gradient(self, X, y):
+        """X: CUDA float64 [n][L][N], y: CUDA float64 [n]; returns (grad, loss)."""
+        g = np.empty(HQ_NN_PARAMS, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(self.lib.hq_nn_gradient(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                            int(X.shape[0]), g.ctypes.data_as(_P(ctypes.c_float)),
+                                            ctypes.byref(loss)), "hq_nn_gradient")
+        return g, loss.value
+
+    def nn_train(self, X, y, epochs, batch, lr, seed=1):
+        losses = np.empty(max(int(epochs), 1))
+        self._check(self.lib.hq_nn_train(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                         int(X.shape[0]), int(epochs), int(batch), float(lr), int(seed),
+                                         _dptr(losses)), "hq_nn_train")
+        return losses[: int(epochs)]
+
+    def cumulative(self, n_steps=1, n_inner=1, local=True, global_=True, measure=False):
+        flags = (HQ_LOCAL if local else 0) | (HQ_GLOBAL if global_ else 0) | (HQ_MEASURE if measure else 0)
+        self._check(self.lib.hq_cumulative_sweep(self._h, int(n_steps), int(n_inner), flags), "hq_cumulative_sweep")
+
+    def learned_stats(self):
+        arr = (hq_learned_stats * self.n_chains)()
+        self._check(self.lib.hq_get_learned_stats(self._h, arr), "hq_get_learned_stats")
+        return [{f: getattr(o, f) for f, _ in hq_learned_stats._fields_} for o in arr]
 
     @property
     def block_move_method(self):

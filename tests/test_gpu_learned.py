@@ -1,0 +1,162 @@
+"""GPU parity of the learned effective action and the cumulative sampler against the oracle.
+
+Network outputs use bfloat16 weights (the same rounded values on both sides) and FP32
+arithmetic on the GPU, FP64 in the oracle: F and its gradient must agree to 2e-3 relative.
+The cumulative accept uses the exact FP64 log-determinants, so the chain samples the exact
+weight whatever the network: a run with a random network must reproduce the free-phonon
+closed form at g = 0, and plain and learned samplers must agree on observables at g != 0.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from workloads import HolsteinParams, initial_fields, random_fields
+
+pytestmark = pytest.mark.gpu
+
+NN_RTOL = 2e-3
+
+
+@pytest.fixture(scope="module")
+def hq():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1905_07440_gb300 as mod
+    mod.load_library()
+    return mod
+
+
+def scaled_params(seed, scale):
+    from oracle import nn
+    th = nn.init_params(seed)
+    th[-nn.N_H - 1:] *= scale  # output layer
+    return th
+
+
+def test_effective_action_matches_oracle(hq):
+    from oracle import nn
+    for nx, beta, seed in ((4, 1.0, 1), (6, 0.8, 2)):
+        p = HolsteinParams(nx=nx, ny=nx, beta=beta)
+        X = random_fields(p, 3, seed=seed, offset=-1.4)
+        th = scaled_params(seed, 5.0)
+        eng = hq.Engine(p, 3)
+        eng.attach_network(4, 8)
+        eng.set_params(th)
+        assert np.array_equal(eng.get_params(bf16=True).astype(np.float64), nn.to_bfloat16(th.astype(np.float32)))
+        eng.set_fields(X)
+        F = eng.nn_eval()
+        act = nn.EffectiveAction(p, nn.to_bfloat16(th.astype(np.float32)))
+        for c in range(3):
+            ref = act.F(X[c])
+            assert abs(F[c] - ref) <= NN_RTOL * max(1.0, abs(ref)), (F[c], ref)
+
+
+def test_gradient_matches_oracle(hq):
+    import torch
+    from oracle import nn
+    p = HolsteinParams(nx=4, ny=4, beta=0.6)
+    X = random_fields(p, 6, seed=7, offset=-1.4)
+    y = np.linspace(-2.0, 3.0, 6)
+    th = scaled_params(3, 3.0)
+    eng = hq.Engine(p, 1)
+    eng.attach_network(8, 8)
+    eng.set_params(th)
+    g, loss = eng.nn_gradient(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda())
+    lref, gref = nn.loss_and_grad(p, nn.to_bfloat16(th.astype(np.float32)), X, y)
+    assert abs(loss - lref) <= NN_RTOL * lref
+    assert np.max(np.abs(g - gref)) <= NN_RTOL * np.max(np.abs(gref))
+
+
+def test_training_lowers_the_loss(hq):
+    import torch
+    from oracle import nn
+    p = HolsteinParams(nx=4, ny=4, beta=0.6)
+    rng = np.random.default_rng(0)
+    X = random_fields(p, 64, seed=11, offset=-1.4)
+    target = nn.EffectiveAction(p, nn.to_bfloat16(scaled_params(9, 20.0).astype(np.float32)))
+    y = np.array([target.F(x) for x in X])
+    y -= y.mean()
+    eng = hq.Engine(p, 1)
+    eng.attach_network(16, 64)
+    eng.set_params(scaled_params(1, 1.0))
+    losses = eng.nn_train(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), epochs=30, batch=16, lr=3e-3, seed=5)
+    assert losses[-1] < 0.2 * losses[0], losses
+
+
+def test_cumulative_step_matches_oracle(hq):
+    from oracle import nn
+    p = HolsteinParams(nx=4, ny=4, beta=1.0, seed=31)
+    C = 3
+    X0 = initial_fields(p, C, seed=3)
+    th = scaled_params(4, 2.0)
+    eng = hq.Engine(p, C)
+    eng.attach_network(4, 8)
+    eng.set_params(th)
+    eng.set_fields(X0)
+    eng.cumulative(n_steps=2, n_inner=1)
+    Xg = eng.get_fields()
+    stats = eng.learned_stats()
+    _, ld = eng.log_weight()
+    thb = nn.to_bfloat16(th.astype(np.float32))
+    for c in range(C):
+        ch = nn.CumulativeChain(p, X0[c], thb, chain=c)
+        acc = 0
+        for k in range(2):
+            pc, a = ch.step(k, 1)
+            acc += a
+        if np.array_equal(Xg[c], ch.X):
+            assert stats[c]["cumulative_accepted"] == acc
+            assert abs(stats[c]["last_pc"] - pc) <= 1e-3 * max(pc, 1e-12) or (pc > 1 and stats[c]["last_pc"] > 1)
+            assert abs(ld[c] - ch.logdet) <= 1e-10 * abs(ch.logdet)
+        else:
+            # divergence only through a decision the FP32 network could not resolve
+            assert ch.min_margin < 1e-4, ch.min_margin
+
+
+@pytest.mark.slow
+def test_cumulative_sampler_is_exact_for_free_phonons(hq):
+    """g = 0: log|det M| does not depend on X, so whatever the network the chain must sample
+    exp(-dtau S_ph); <X^2> must match the Gaussian closed form."""
+    from tests import closed_forms as cf
+    p = HolsteinParams(nx=4, ny=4, beta=2.0, g=0.0, mu=0.0, seed=5)
+    C, steps, burn = 64, 60, 10
+    eng = hq.Engine(p, C, max_series=steps)
+    eng.attach_network(4, 8)
+    eng.set_params(scaled_params(2, 0.3))
+    eng.set_fields(initial_fields(p, C, seed=8))
+    eng.cumulative(n_steps=steps, n_inner=1)
+    s = eng.series(hq.HQ_OBS_X2)[:, burn:]
+    per_chain = s.mean(axis=1)
+    mean, err = per_chain.mean(), per_chain.std(ddof=1) / math.sqrt(C)
+    ref = cf.free_phonon_x2(p.n_slices, p.dtau, p.mass, p.omega)
+    assert abs(mean - ref) < 4 * err, (mean, ref, err)
+    st = eng.learned_stats()
+    assert sum(x["cumulative_accepted"] for x in st) > 0
+
+
+@pytest.mark.slow
+def test_learned_and_plain_samplers_agree(hq):
+    """g != 0: the cumulative sampler with a crude network and the plain sampler give the same
+    <X^2> and double occupancy within their statistical errors."""
+    p = HolsteinParams(nx=4, ny=4, beta=1.0, seed=17)
+    C, steps, burn = 64, 50, 10
+    res = {}
+    for kind in ("plain", "learned"):
+        eng = hq.Engine(p, C, max_series=steps)
+        eng.set_fields(initial_fields(p, C, seed=2))
+        if kind == "plain":
+            eng.sweep(steps)
+        else:
+            eng.attach_network(4, 8)
+            eng.set_params(scaled_params(6, 0.2))
+            eng.cumulative(n_steps=steps, n_inner=1, measure=True)
+        out = {}
+        for oid in (hq.HQ_OBS_X2, hq.HQ_OBS_DOUBLE_OCC):
+            pc = eng.series(oid)[:, burn:].mean(axis=1)
+            out[oid] = (pc.mean(), pc.std(ddof=1) / math.sqrt(C))
+        res[kind] = out
+    for oid in (hq.HQ_OBS_X2, hq.HQ_OBS_DOUBLE_OCC):
+        (a, ea), (b, eb) = res["plain"][oid], res["learned"][oid]
+        assert abs(a - b) < 4 * math.hypot(ea, eb), (oid, a, b, ea, eb)
