@@ -215,32 +215,40 @@ class CumulativeChain:
         return bool(u < prob)
 
     def step(self, k, n_inner, local=True, block=True):
+        """One cumulative step.  The inner moves run forward (local moves l, i ascending, then
+        block moves i ascending) or as the exact reverse of that sequence, each with
+        probability 1/2 (second uniform of the step's tag-4 Philox block): a fixed order of
+        reversible moves is not reversible, and p_c relies on a reversible proposal."""
         p, X = self.p, self.X
         L, N = X.shape
         X0 = X.copy()
         ld0, F0 = self.logdet, self.act.F(X0)
+        uc, ud = proposal_uniforms(p.seed, self.chain, k, [0], TAG_CUMULATIVE)
+        fwd = bool(ud[0] < 0.5)
+        order = (lambda m: range(m)) if fwd else (lambda m: range(m - 1, -1, -1))
         for u in range(n_inner):
             isw = k * n_inner + u
-            if local:
-                for s in range(L):
-                    u1, u2 = proposal_uniforms(p.seed, self.chain, isw, s * N + np.arange(N), TAG_NN_LOCAL)
-                    for i in range(N):
-                        xn = X[s, i] + p.dx_local * (2.0 * u1[i] - 1.0)
-                        dS = dqmc.local_action_change(p, X, s, i, xn)
-                        dF = self.act.delta_local(X, s, i, xn)
+            parts = ("local", "block") if fwd else ("block", "local")
+            for part in parts:
+                if part == "local" and local:
+                    for s in order(L):
+                        u1, u2 = proposal_uniforms(p.seed, self.chain, isw, s * N + np.arange(N), TAG_NN_LOCAL)
+                        for i in order(N):
+                            xn = X[s, i] + p.dx_local * (2.0 * u1[i] - 1.0)
+                            dS = dqmc.local_action_change(p, X, s, i, xn)
+                            dF = self.act.delta_local(X, s, i, xn)
+                            if self._decide(u2[i], math.exp(min(2.0 * dF - dS, 709.0))):
+                                X[s, i] = xn
+                if part == "block" and block:
+                    u1, u2 = proposal_uniforms(p.seed, self.chain, isw, np.arange(N), TAG_NN_BLOCK)
+                    for i in order(N):
+                        dx = p.dx_global * (2.0 * u1[i] - 1.0)
+                        dS = dqmc.global_action_change(p, X, i, dx)
+                        dF = self.act.delta_block(X, i, dx)
                         if self._decide(u2[i], math.exp(min(2.0 * dF - dS, 709.0))):
-                            X[s, i] = xn
-            if block:
-                u1, u2 = proposal_uniforms(p.seed, self.chain, isw, np.arange(N), TAG_NN_BLOCK)
-                for i in range(N):
-                    dx = p.dx_global * (2.0 * u1[i] - 1.0)
-                    dS = dqmc.global_action_change(p, X, i, dx)
-                    dF = self.act.delta_block(X, i, dx)
-                    if self._decide(u2[i], math.exp(min(2.0 * dF - dS, 709.0))):
-                        X[:, i] += dx
+                            X[:, i] += dx
         ld1, F1 = dqmc.log_det_M(p, self.expK, X), self.act.F(X)
         pc = math.exp(min(2.0 * (ld1 - ld0) - 2.0 * (F1 - F0), 709.0))
-        uc, _ = proposal_uniforms(p.seed, self.chain, k, [0], TAG_CUMULATIVE)
         accepted = self._decide(float(uc[0]), pc)
         if accepted:
             self.logdet = ld1

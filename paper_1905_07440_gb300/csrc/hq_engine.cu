@@ -865,7 +865,7 @@ int hq_cumulative_sweep(hq_engine* e, int n_steps, int n_inner, unsigned flags) 
     rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(e->nn.ld0, d.logdet, sizeof(double) * d.n_chains,
                                                  cudaMemcpyDeviceToDevice, e->stream), "ld0 copy");
     rc = rc ? rc : cuda_check(e, hq::nn_launch_eval(d, e->nn, d.X, e->nn.F0, 1, e->stream), "nn eval F0");
-    rc = rc ? rc : cuda_check(e, hq::nn_launch_inner(d, e->nn, n_inner, step * (uint32_t)n_inner,
+    rc = rc ? rc : cuda_check(e, hq::nn_launch_inner(d, e->nn, n_inner, step,
                                                      (flags & HQ_LOCAL) ? 1 : 0, (flags & HQ_GLOBAL) ? 1 : 0,
                                                      e->stream), "nn inner");
     rc = rc ? rc : cuda_check(e, hq::nn_launch_eval(d, e->nn, d.X, e->nn.F1, 0, e->stream), "nn eval F1");

@@ -112,7 +112,7 @@ double fp64_probe_tflops(int kind, int reps, cudaStream_t s);
 cudaError_t launch_measure_g0(const Dev& d, cudaStream_t s);
 cudaError_t nn_launch_eval(const Dev& d, const NNState& nn, const double* X, double* F, int write_cache,
                            cudaStream_t s);
-cudaError_t nn_launch_inner(const Dev& d, const NNState& nn, int n_inner, uint32_t first_isweep, int do_local,
+cudaError_t nn_launch_inner(const Dev& d, const NNState& nn, int n_inner, uint32_t step, int do_local,
                             int do_block, cudaStream_t s);
 cudaError_t nn_launch_decide(const Dev& d, const NNState& nn, uint32_t step, cudaStream_t s);
 cudaError_t nn_launch_set(const NNState& nn, const float* src_device, cudaStream_t s);

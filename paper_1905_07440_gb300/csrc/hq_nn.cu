@@ -165,7 +165,11 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_eval_kernel(Dev d, NNState nn, 
 
 // n_inner network-driven sweeps of every chain: local moves at every (l, i), then block
 // moves at every site, each accepted on exp(2 dF - dtau dS_ph) with the exact phonon action.
-__global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn, int n_inner, uint32_t first_isweep,
+// A fixed visiting order of reversible moves is not reversible as a whole, and the
+// cumulative accept needs a reversible proposal; so each step draws a direction (second
+// uniform of the step's Philox block, tag 4): forward (l, i ascending, then block moves i
+// ascending) or the exact reverse of that sequence, with probability 1/2 each.
+__global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn, int n_inner, uint32_t step,
                                                               int do_local, int do_block) {
   extern __shared__ __align__(16) char nraw[];
   const int c = blockIdx.x, n = d.n, L = d.L, NL = n * L;
@@ -180,10 +184,16 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
   const uint32_t chain = (uint32_t)(d.first_chain + c);
   long long nl_acc = 0, nb_acc = 0;
   const double kfac = d.mass / (2.0 * d.dtau), pfac = 0.5 * d.dtau * d.mass * (d.omega * d.omega);
+  double du1, du2;
+  proposal_uniforms(d.key0, d.key1, 0u, step, chain, 4u, du1, du2);
+  const bool fwd = du2 < 0.5;
   for (int u = 0; u < n_inner; ++u) {
-    const uint32_t isw = first_isweep + (uint32_t)u;
-    if (do_local) {
-      for (int sl = 0; sl < L; ++sl) {
+    const uint32_t isw = step * (uint32_t)n_inner + (uint32_t)u;
+    for (int part = 0; part < 2; ++part) {
+    const bool local_part = (part == 0) == fwd;
+    if (local_part && do_local) {
+      for (int sl0 = 0; sl0 < L; ++sl0) {
+        const int sl = fwd ? sl0 : L - 1 - sl0;
         for (int i = threadIdx.x; i < n; i += HQ_THREADS) {
           double u1, u2;
           proposal_uniforms(d.key0, d.key1, (uint32_t)(sl * n + i), isw, chain, 2u, u1, u2);
@@ -196,7 +206,8 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
           s.pds[i] = kfac * kin + pfac * (xn * xn - xo * xo);
         }
         __syncthreads();
-        for (int i = 0; i < n; ++i) {
+        for (int i0 = 0; i0 < n; ++i0) {
+          const int i = fwd ? i0 : n - 1 - i0;
           // the 25 patches containing (sl, i): centres (sl - dl, i - c), one per group
           float f = 0.f;
           int row = -1;
@@ -226,8 +237,9 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
         }
       }
     }
-    if (do_block) {
-      for (int i = 0; i < n; ++i) {
+    if (!local_part && do_block) {
+      for (int i0 = 0; i0 < n; ++i0) {
+        const int i = fwd ? i0 : n - 1 - i0;
         if (threadIdx.x == 0) {
           double u1, u2;
           proposal_uniforms(d.key0, d.key1, (uint32_t)i, isw, chain, 3u, u1, u2);
@@ -285,6 +297,7 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
         }
         __syncthreads();
       }
+    }
     }
   }
   if (threadIdx.x == 0) {
@@ -541,11 +554,11 @@ cudaError_t nn_launch_eval(const Dev& d, const NNState& nn, const double* X, dou
   return cudaGetLastError();
 }
 
-cudaError_t nn_launch_inner(const Dev& d, const NNState& nn, int n_inner, uint32_t first_isweep, int do_local,
+cudaError_t nn_launch_inner(const Dev& d, const NNState& nn, int n_inner, uint32_t step, int do_local,
                             int do_block, cudaStream_t s) {
   const size_t sb = nn_smem_bytes(d.n);
   smem_opt_in((const void*)nn_inner_kernel, sb);
-  nn_inner_kernel<<<d.n_chains, HQ_THREADS, sb, s>>>(d, nn, n_inner, first_isweep, do_local, do_block);
+  nn_inner_kernel<<<d.n_chains, HQ_THREADS, sb, s>>>(d, nn, n_inner, step, do_local, do_block);
   return cudaGetLastError();
 }
 
