@@ -381,6 +381,108 @@ def run_tau(args):
     return 0
 
 
+def run_learned(args):
+    """Learned vs plain sampler on the batched workload (8x8, beta = 8, 256 chains).
+
+    1. Plain sampler: warm-up, then training samples (fields and exact log|det M|).
+    2. Network training on those samples (the library's kernels).
+    3. Learned sampler (cumulative steps of args.n_inner network sweeps, exact accept) from the
+       equilibrated plain fields: timed steps/s, then tau_int of the per-step series.
+    4. Plain sampler timed on the same fields; its tau_int from the committed measurement.
+    Independent samples/s = chains * (steps or sweeps)/s / (2 tau_int), per observable.
+    """
+    import numpy as np
+    import torch
+    import paper_1905_07440_gb300 as hq
+    params, C, wname = workload_params("batched")
+    if args.chains:
+        C = args.chains
+    dev = torch.device("cuda", 0)
+    t_all = time.perf_counter()
+    eng = hq.Engine(params, C, max_series=8)
+    eng.set_fields(workloads.initial_fields(params, C))
+    eng.sweep(args.train_warmup)
+    Xs, ys = [], []
+    for _ in range(args.train_snapshots):
+        eng.sweep(2)
+        Xs.append(eng.get_fields())
+        ys.append(eng.log_weight()[1])
+    Xtr = np.concatenate(Xs)
+    ytr = np.concatenate(ys)
+    ytr -= ytr.mean()
+    X_eq = eng.get_fields()
+    eng.close()
+    net = hq.Engine(params, 1)
+    net.attach_network(64, Xtr.shape[0])
+    from oracle import nn as nn_oracle  # initial weights only (seeded He initialisation)
+    net.set_params(nn_oracle.init_params(args.nn_seed))
+    Xd, yd = torch.from_numpy(Xtr).to(dev), torch.from_numpy(ytr).to(dev)
+    t0 = time.perf_counter()
+    # learning rate halved every third of the epochs (Adam state carries over)
+    losses = []
+    for k in range(3):
+        ep = args.epochs // 3 + (args.epochs % 3 if k == 2 else 0)
+        losses.extend(net.nn_train(Xd, yd, epochs=ep, batch=64, lr=args.lr * 0.5 ** k, seed=args.nn_seed + k))
+    t_train = time.perf_counter() - t0
+    theta = net.get_params()
+    del Xd, yd
+    net.close()
+    # learned sampler
+    steps = args.tau_steps
+    lrn = hq.Engine(params, C, max_series=steps + args.warmup + args.steps + 4)
+    lrn.attach_network(4, 8)
+    lrn.set_params(theta)
+    lrn.set_fields(X_eq)
+    lrn.cumulative(args.warmup, args.n_inner, measure=True)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    lrn.cumulative(args.steps, args.n_inner, measure=True)
+    b.record()
+    torch.cuda.synchronize()
+    step_rate = C * args.steps / (a.elapsed_time(b) / 1e3)
+    lrn.cumulative(steps, args.n_inner, measure=True)
+    st = lrn.learned_stats()
+    acc = sum(x["cumulative_accepted"] for x in st) / max(1, sum(x["cumulative_proposed"] for x in st))
+    inner_l = sum(x["inner_local_accepted"] for x in st) / max(1, sum(x["inner_local_proposed"] for x in st))
+    inner_b = sum(x["inner_block_accepted"] for x in st) / max(1, sum(x["inner_block_proposed"] for x in st))
+    first = args.warmup + args.steps
+    tau_l, indep_l, means = {}, {}, {}
+    for oid, name in ((hq.HQ_OBS_X2, "x2"), (hq.HQ_OBS_DOUBLE_OCC, "double_occ"), (hq.HQ_OBS_SCDW, "s_cdw")):
+        ser = lrn.series(oid)[:, first:]
+        tau_l[name] = float(np.mean([hq.tau_int(ser[c])[0] for c in range(C)]))
+        indep_l[name] = step_rate / (2.0 * tau_l[name])
+        means[name] = float(ser.mean())
+    # plain sampler, same fields
+    pl = hq.Engine(params, C, max_series=8)
+    pl.set_fields(X_eq)
+    pl.sweep(1)
+    torch.cuda.synchronize()
+    a.record()
+    pl.sweep(args.steps)
+    b.record()
+    torch.cuda.synchronize()
+    sweep_rate = C * args.steps / (a.elapsed_time(b) / 1e3)
+    with open(os.path.join(ROOT, "profiles", "tau_int_batched.json")) as f:
+        tau_p = json.load(f)["tau_int"]
+    indep_p = {k: sweep_rate / (2.0 * tau_p[k]) for k in indep_l}
+    line = {"metric": METRIC, "mode": "learned vs plain", "value": indep_l["s_cdw"],
+            "unit": "independent samples/s of S_CDW(pi,pi) (learned)", "higher_is_better": True,
+            "dtype": "f64 weights, bf16-weight/fp32 network", "data": "synthetic",
+            "config": {"workload": wname, "chains": C, "n_inner": args.n_inner, "train_samples": int(Xtr.shape[0]),
+                       "epochs": args.epochs, "lr": args.lr},
+            "learned": {"cumulative_steps_per_s": step_rate, "tau_int_steps": tau_l, "indep_samples_per_s": indep_l,
+                        "cumulative_acceptance": acc, "inner_local_acceptance": inner_l,
+                        "inner_block_acceptance": inner_b, "means": means},
+            "plain": {"chain_sweeps_per_s": sweep_rate, "tau_int_sweeps": tau_p, "indep_samples_per_s": indep_p},
+            "gain": {k: indep_l[k] / indep_p[k] for k in indep_l},
+            "training": {"seconds": t_train, "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+                         "target_variance": float(np.var(ytr))},
+            "wall_s": time.perf_counter() - t_all}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_peaks():
     """FP64 pipe evidence: DFMA and DMMA probes of the library, cuBLAS DGEMM/SGEMM via torch."""
     import torch
@@ -423,7 +525,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--peaks", action="store_true", help="print the FP64/FP32 pipe probes and exit")
     ap.add_argument("--tau-sweeps", type=int, default=0, help="measure tau_int over this many sweeps and exit")
+    ap.add_argument("--n-inner", type=int, default=1, help="learned mode: network sweeps per cumulative step")
+    ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--nn-seed", type=int, default=1)
+    ap.add_argument("--train-warmup", type=int, default=30)
+    ap.add_argument("--train-snapshots", type=int, default=32)
+    ap.add_argument("--tau-steps", type=int, default=150)
     args = ap.parse_args()
+    if args.workload == "learned":
+        sys.exit(run_learned(args))
     if args.peaks:
         sys.exit(run_peaks())
     if args.tau_sweeps:
