@@ -483,6 +483,89 @@ def run_learned(args):
     return 0
 
 
+SERVING_KINDS = (("4x4 beta=2", dict(nx=4, ny=4, beta=2.0)), ("6x6 beta=2", dict(nx=6, ny=6, beta=2.0)),
+                 ("8x8 beta=4", dict(nx=8, ny=8, beta=4.0)))
+
+
+def run_serving(args):
+    """Continuous-batching service under Poisson arrivals (plain sampler).
+
+    Requests of three lattice shapes (scaled down from the batched workload so that a request
+    finishes in about a second) arrive at args.rate per second for args.duration seconds, each
+    asking for args.req_sweeps sweeps of one chain with its own seed, chain word and initial
+    fields.  Reported: served chain-sweeps/s over the whole run, request latency (arrival to
+    result on the host) percentiles, queueing delay, and, for reference, the latency of a few
+    requests served alone on an idle GPU.
+    """
+    import numpy as np
+    import torch
+    from paper_1905_07440_gb300.serving import GpuBackend, Request, Server
+
+    rng = np.random.default_rng(args.serve_seed)
+    reqs, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / args.rate)
+        if t > args.duration:
+            break
+        k = len(reqs)
+        kind, shape = SERVING_KINDS[rng.integers(len(SERVING_KINDS))]
+        p = workloads.HolsteinParams(**shape, seed=workloads.BATCHED.seed + 7919 * k)
+        reqs.append(Request(rid=k, params=p, X0=workloads.initial_fields(p, 1, seed=10_000 + k)[0],
+                            sweeps=args.req_sweeps, chain_id=k, arrival=t))
+        reqs[-1].kind = kind
+    backend = GpuBackend()
+    # warm-up: one request of each kind (kernel loading, allocator)
+    warm = [Request(rid=-1 - j, params=workloads.HolsteinParams(**sh), X0=workloads.initial_fields(
+        workloads.HolsteinParams(**sh), 1)[0], sweeps=1) for j, (_, sh) in enumerate(SERVING_KINDS)]
+    Server(backend, args.hbm_budget, args.slots).run(warm)
+    torch.cuda.synchronize()
+    peak = [0]
+
+    class Tracking(Server):
+        def poll(self):
+            super().poll()
+            peak[0] = max(peak[0], self.used)
+
+    srv = Tracking(backend, args.hbm_budget, args.slots)
+    sampler = ClockSampler()
+    sampler.start()
+    t0 = time.perf_counter()
+    done = srv.run(reqs)
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    lat = np.array([r.done - r.arrival for r in done]) * 1e3
+    wait = np.array([r.admitted - r.arrival for r in done]) * 1e3
+    by_kind = {}
+    for kind, _ in SERVING_KINDS:
+        lk = np.array([r.done - r.arrival for r in done if r.kind == kind]) * 1e3
+        if lk.size:
+            by_kind[kind] = {"n": int(lk.size), "p50": float(np.percentile(lk, 50)), "p99": float(np.percentile(lk, 99))}
+    # the same kinds served alone (one request at a time, idle GPU)
+    alone = {}
+    for kind, sh in SERVING_KINDS:
+        ts = []
+        for j in range(3):
+            p = workloads.HolsteinParams(**sh, seed=123 + j)
+            r = Request(rid=j, params=p, X0=workloads.initial_fields(p, 1, seed=j)[0], sweeps=args.req_sweeps)
+            a = time.perf_counter()
+            Server(backend, args.hbm_budget, 1).run([r])
+            ts.append((time.perf_counter() - a) * 1e3)
+        alone[kind] = float(np.median(ts))
+    served = sum(r.sweeps for r in done)
+    pct = lambda a, q: float(np.percentile(a, q))
+    line = {"metric": METRIC, "mode": "serving", "value": served / wall, "unit": "chain-sweeps/s (served)",
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "Poisson mix of " + ", ".join(k for k, _ in SERVING_KINDS) + " (L = beta/0.1)",
+                       "rate_per_s": args.rate, "duration_s": args.duration, "sweeps_per_request": args.req_sweeps,
+                       "slots_per_pool": args.slots, "hbm_budget_bytes": args.hbm_budget},
+            "requests": len(done), "wall_s": wall, "requests_per_s": len(done) / wall,
+            "latency_ms": {"p50": pct(lat, 50), "p90": pct(lat, 90), "p99": pct(lat, 99), "max": float(lat.max())},
+            "queue_ms": {"p50": pct(wait, 50), "p99": pct(wait, 99)}, "latency_by_kind_ms": by_kind,
+            "alone_latency_ms": alone, "peak_pool_bytes": int(peak[0]), "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_peaks():
     """FP64 pipe evidence: DFMA and DMMA probes of the library, cuBLAS DGEMM/SGEMM via torch."""
     import torch
@@ -532,9 +615,17 @@ def main():
     ap.add_argument("--train-warmup", type=int, default=30)
     ap.add_argument("--train-snapshots", type=int, default=32)
     ap.add_argument("--tau-steps", type=int, default=150)
+    ap.add_argument("--rate", type=float, default=40.0, help="serving mode: requests per second")
+    ap.add_argument("--duration", type=float, default=10.0, help="serving mode: seconds of arrivals")
+    ap.add_argument("--req-sweeps", type=int, default=10, help="serving mode: sweeps per request")
+    ap.add_argument("--slots", type=int, default=32, help="serving mode: chain slots per pool")
+    ap.add_argument("--hbm-budget", type=int, default=8 << 30, help="serving mode: bytes for pool state")
+    ap.add_argument("--serve-seed", type=int, default=3)
     args = ap.parse_args()
     if args.workload == "learned":
         sys.exit(run_learned(args))
+    if args.workload == "serving":
+        sys.exit(run_serving(args))
     if args.peaks:
         sys.exit(run_peaks())
     if args.tau_sweeps:

@@ -130,7 +130,8 @@ int hq_get_green(hq_engine* e, int chain, double* G_host, int* slice);
 int hq_get_observables(hq_engine* e, hq_obs* out);
 
 /* Per-sweep series of one observable: out[chain][s] for s < *n_out (host, n_chains *
- * max_series doubles).  NaN where the sweep had no electronic measurement. */
+ * max_series doubles; *n_out = the longest chain record).  NaN where the sweep had no
+ * electronic measurement or beyond a chain's own record. */
 int hq_get_series(hq_engine* e, int obs_id, double* out, int* n_out);
 
 /* Serialise the chain state (fields, sweep counter, counters, accumulators, series).
@@ -144,6 +145,16 @@ int hq_restore(hq_engine* e, const void* buf, size_t len);
  * n_wrap-slice products kept per chain, updated by a rank-n_wrap correction per move and
  * applied with one GEMM per chunk).  Both give the same determinants up to rounding. */
 int hq_block_move_method(const hq_engine* e);
+
+/* Slots.  Every chain slot carries its own Philox key, chain word and sweep counter (set by
+ * hq_create to seed, first_chain + slot, 0; the counter advances by one per sweep or
+ * cumulative step of that chain), so a chain's trajectory depends only on its own fields and
+ * identity, not on which slot it occupies or what else runs in the engine.
+ * hq_set_chain loads one slot (fields X_host [L][N], key `seed`, chain word, counter), clears
+ * its counters, totals and series, and makes it active; hq_set_active(e, slot, 0) idles a slot
+ * (it takes no work until reactivated or reloaded).  Both synchronise the stream. */
+int hq_set_chain(hq_engine* e, int slot, const double* X_host, uint64_t seed, uint32_t chain_id, uint32_t sweep);
+int hq_set_active(hq_engine* e, int slot, int active);
 
 /* Number of chains, sites N, slices L and sweeps run. */
 int hq_shape(const hq_engine* e, int* n_chains, int* n_sites, int* n_slices, int64_t* sweeps);

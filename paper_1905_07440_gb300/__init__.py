@@ -79,6 +79,8 @@ _SIGNATURES = {
     "hq_checkpoint": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_size_t)]),
     "hq_restore": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "hq_block_move_method": (ctypes.c_int, [_vp]),
+    "hq_set_chain": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]),
+    "hq_set_active": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "hq_shape": (ctypes.c_int, [_vp, _P(ctypes.c_int), _P(ctypes.c_int), _P(ctypes.c_int), _P(ctypes.c_int64)]),
     "hq_last_error": (ctypes.c_char_p, [_vp]),
     "hq_destroy": (None, [_vp]),
@@ -256,6 +258,16 @@ class Engine:
         n = (ctypes.c_int64 * HQ_N_PHASES)()
         self._check(self.lib.hq_get_timing(self._h, _dptr(ms), n), "hq_get_timing")
         return {PHASES[i]: (float(ms[i]), int(n[i])) for i in range(HQ_N_PHASES)}
+
+    def set_chain(self, slot, X, seed, chain_id, sweep=0):
+        """Load one slot: fields X [L][N], Philox key `seed`, chain word, sweep counter."""
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        assert X.shape == self.field_shape[1:]
+        self._check(self.lib.hq_set_chain(self._h, int(slot), _dptr(X), int(seed), int(chain_id), int(sweep)),
+                    "hq_set_chain")
+
+    def set_active(self, slot, active):
+        self._check(self.lib.hq_set_active(self._h, int(slot), 1 if active else 0), "hq_set_active")
 
     # ------------------------------------------------------------ learned moves
     def attach_network(self, max_batch=64, max_samples=4096):

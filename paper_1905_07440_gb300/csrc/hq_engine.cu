@@ -49,7 +49,7 @@ thread_local std::string g_call_error;  // message of the last failing call with
 
 struct Layout {
   size_t kin, X, G, logdet, UR, TR, DR, work, stU, stT, stD, Adl, Bdl, acc, tot, series, counters, status, sched, tmp,
-      expV, cmat, cbuf, corr;
+      expV, cmat, cbuf, corr, cid, active, slen;
   size_t total;
 };
 
@@ -103,6 +103,9 @@ Layout layout(const hq_params& p, int C, int max_series) {
   l.status = take(sizeof(int) * C);
   l.sched = take(sizeof(int) * (hq::kSchedHeader + C));
   l.tmp = take(sizeof(double) * C);
+  l.cid = take(sizeof(uint32_t) * 4 * C);
+  l.active = take(sizeof(int) * C);
+  l.slen = take(sizeof(int) * C);
   if (hq::chunk_propagators_pay(p.nx, p.ny, (int)L, p.n_wrap)) {
     const size_t nch = (L + p.n_wrap - 1) / p.n_wrap;
     l.expV = take(sizeof(double) * C * L * n);
@@ -243,6 +246,9 @@ int hq_create(const hq_params* p, int n_chains, int first_chain, int max_series,
   d.counters = (long long*)(a + l.counters);
   d.status = (int*)(a + l.status);
   d.sched = (int*)(a + l.sched);
+  d.cid = (uint32_t*)(a + l.cid);
+  d.active = (int*)(a + l.active);
+  d.slen = (int*)(a + l.slen);
   d.use_cm = hq::chunk_propagators_pay(d.nx, d.ny, d.L, d.n_wrap) ? 1 : 0;
   d.n_chunks = (d.L + d.n_wrap - 1) / d.n_wrap;
   if (d.use_cm) {
@@ -264,6 +270,19 @@ int hq_create(const hq_params* p, int n_chains, int first_chain, int max_series,
   rc = rc ? rc : cuda_check(e, cudaMemsetAsync(a, 0, l.total, e->stream), "arena clear");
   rc = rc ? rc : cuda_check(e, cudaMemcpyAsync((void*)d.kin, kin.data(), kin.size() * sizeof(double),
                                                cudaMemcpyHostToDevice, e->stream), "kinetic upload");
+  // per-chain identity: key = seed, chain word = first_chain + c, counter 0; all active
+  std::vector<uint32_t> cid(4 * (size_t)n_chains);
+  std::vector<int> act((size_t)n_chains, 1);
+  for (int c = 0; c < n_chains; ++c) {
+    cid[4 * c] = d.key0;
+    cid[4 * c + 1] = d.key1;
+    cid[4 * c + 2] = (uint32_t)(first_chain + c);
+    cid[4 * c + 3] = 0u;
+  }
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(d.cid, cid.data(), cid.size() * 4, cudaMemcpyHostToDevice, e->stream),
+                            "chain ids");
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(d.active, act.data(), act.size() * 4, cudaMemcpyHostToDevice,
+                                               e->stream), "active flags");
   rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "create sync");
   if (rc) {
     std::fprintf(stderr, "hq_create: %s\n", e->err.c_str());
@@ -322,7 +341,6 @@ int hq_sweep(hq_engine* e, int n_sweeps, unsigned flags) {
   const bool do_local = flags & HQ_LOCAL, do_global = flags & HQ_GLOBAL, meas = flags & HQ_MEASURE;
   const hq::Dev& d = e->d;
   for (int it = 0; it < n_sweeps; ++it) {
-    const uint32_t sw = (uint32_t)e->sweeps;
     int rc = HQ_OK;
     if (do_local || !e->logdet_valid) rc = ensure_state(e);
     if (rc) return rc;
@@ -330,7 +348,7 @@ int hq_sweep(hq_engine* e, int n_sweeps, unsigned flags) {
       PhaseTimer pt(e, 1, (d.L + d.n_wrap - 1) / d.n_wrap);
       for (int s0 = 0; s0 < d.L; s0 += d.n_wrap) {
         const int s1 = s0 + d.n_wrap < d.L ? s0 + d.n_wrap : d.L;
-        rc = cuda_check(e, hq::launch_local_chunk(d, s0, s1, sw, meas ? 1 : 0, e->stream), "local_chunk launch");
+        rc = cuda_check(e, hq::launch_local_chunk(d, s0, s1, meas ? 1 : 0, e->stream), "local_chunk launch");
         if (rc) return rc;
       }
       e->stack_valid = false;  // fields changed; G_0 and log|det M| are fresh (restabilised at l = L)
@@ -338,18 +356,16 @@ int hq_sweep(hq_engine* e, int n_sweeps, unsigned flags) {
     }
     if (do_global) {
       PhaseTimer pt(e, 2, 1);
-      rc = cuda_check(e, hq::launch_global_phase(d, sw, e->stream), "global_phase launch");
+      rc = cuda_check(e, hq::launch_global_phase(d, e->stream), "global_phase launch");
       if (rc) return rc;
       e->stack_valid = false;
       e->green_valid = false;  // log|det M| is kept current by the accepted moves
     }
-    const int slot = e->series_len < d.max_series ? e->series_len : -1;
     {
       PhaseTimer pt(e, 3, 1);
-      rc = cuda_check(e, hq::launch_sweep_end(d, slot, (meas && do_local) ? 1 : 0, e->stream), "sweep_end launch");
+      rc = cuda_check(e, hq::launch_sweep_end(d, (meas && do_local) ? 1 : 0, e->stream), "sweep_end launch");
     }
     if (rc) return rc;
-    if (slot >= 0) e->series_len++;
     e->sweeps++;
   }
   return HQ_OK;
@@ -438,16 +454,61 @@ int hq_get_observables(hq_engine* e, hq_obs* out) {
 int hq_get_series(hq_engine* e, int obs_id, double* out, int* n_out) {
   if (!e || !out || obs_id < 0 || obs_id >= HQ_N_OBS) return HQ_EINVAL;
   const size_t C = (size_t)e->d.n_chains, M = (size_t)e->d.max_series;
-  if (n_out) *n_out = e->series_len;
+  if (n_out) *n_out = 0;
   if (M == 0) return HQ_OK;
   std::vector<double> all(C * HQ_N_OBS * M);
+  std::vector<int> len(C);
   int rc = cuda_check(e, cudaMemcpyAsync(all.data(), e->d.series, all.size() * sizeof(double),
                                          cudaMemcpyDeviceToHost, e->stream), "series copy");
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(len.data(), e->d.slen, C * sizeof(int), cudaMemcpyDeviceToHost,
+                                               e->stream), "series length copy");
   rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "series sync");
   if (rc) return rc;
+  int nmax = 0;
+  for (size_t c = 0; c < C; ++c) nmax = len[c] > nmax ? len[c] : nmax;
   for (size_t c = 0; c < C; ++c)
-    for (int s = 0; s < e->series_len; ++s) out[c * M + s] = all[(c * HQ_N_OBS + obs_id) * M + s];
+    for (int s = 0; s < nmax; ++s) out[c * M + s] = s < len[c] ? all[(c * HQ_N_OBS + obs_id) * M + s] : NAN;
+  if (n_out) *n_out = nmax;
   return HQ_OK;
+}
+
+int hq_set_chain(hq_engine* e, int slot, const double* X_host, uint64_t seed, uint32_t chain_id, uint32_t sweep) {
+  if (!e || !X_host || slot < 0 || slot >= e->d.n_chains) return HQ_EINVAL;
+  const hq::Dev& d = e->d;
+  const size_t NL = (size_t)d.L * d.n;
+  const uint32_t id[4] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), chain_id, sweep};
+  const int one = 1, zero = 0;
+  cudaStream_t st = e->stream;
+  int rc = cuda_check(e, cudaMemcpyAsync(d.X + slot * NL, X_host, NL * sizeof(double), cudaMemcpyHostToDevice, st),
+                      "set_chain fields");
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(d.cid + 4 * (size_t)slot, id, sizeof(id), cudaMemcpyHostToDevice, st),
+                            "set_chain id");
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(d.active + slot, &one, sizeof(int), cudaMemcpyHostToDevice, st),
+                            "set_chain active");
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(d.slen + slot, &zero, sizeof(int), cudaMemcpyHostToDevice, st),
+                            "set_chain series");
+  rc = rc ? rc : cuda_check(e, cudaMemsetAsync(d.acc + (size_t)slot * hq::kAccSlots, 0, sizeof(double) * hq::kAccSlots, st),
+                            "set_chain acc");
+  rc = rc ? rc : cuda_check(e, cudaMemsetAsync(d.tot + (size_t)slot * hq::kTotSlots, 0, sizeof(double) * hq::kTotSlots, st),
+                            "set_chain totals");
+  rc = rc ? rc : cuda_check(e, cudaMemsetAsync(d.counters + (size_t)slot * hq::kCounters, 0,
+                                               sizeof(long long) * hq::kCounters, st), "set_chain counters");
+  rc = rc ? rc : cuda_check(e, cudaMemsetAsync(d.status + slot, 0, sizeof(int), st), "set_chain status");
+  if (d.use_cm) rc = rc ? rc : cuda_check(e, cudaMemsetAsync(d.cbuf + slot, 0, sizeof(int), st), "set_chain cbuf");
+  // the host values above are on the stack: make the copies complete before returning
+  rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(st), "set_chain sync");
+  e->stack_valid = e->logdet_valid = e->green_valid = false;
+  return rc;
+}
+
+int hq_set_active(hq_engine* e, int slot, int active) {
+  if (!e || slot < 0 || slot >= e->d.n_chains) return HQ_EINVAL;
+  const int v = active ? 1 : 0;
+  int rc = cuda_check(e, cudaMemcpyAsync(e->d.active + slot, &v, sizeof(int), cudaMemcpyHostToDevice, e->stream),
+                      "set_active");
+  rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "set_active sync");
+  if (v) e->stack_valid = e->logdet_valid = e->green_valid = false;
+  return rc;
 }
 
 // checkpoint: header, then X, counters, totals, series (host byte order).
@@ -461,7 +522,8 @@ struct CkHeader {
 static size_t ck_len(const hq_engine* e) {
   const size_t C = (size_t)e->d.n_chains;
   return sizeof(CkHeader) + field_bytes(e) + C * hq::kCounters * sizeof(long long) +
-         C * hq::kTotSlots * sizeof(double) + C * HQ_N_OBS * (size_t)e->d.max_series * sizeof(double);
+         C * hq::kTotSlots * sizeof(double) + C * HQ_N_OBS * (size_t)e->d.max_series * sizeof(double) +
+         C * (4 * sizeof(uint32_t) + 2 * sizeof(int));
 }
 
 int hq_checkpoint(hq_engine* e, void* buf, size_t* len) {
@@ -475,8 +537,8 @@ int hq_checkpoint(hq_engine* e, void* buf, size_t* len) {
   *len = need;
   const size_t C = (size_t)e->d.n_chains;
   CkHeader h{};
-  std::memcpy(h.magic, "HQCKPT1", 8);
-  h.version = 1;
+  std::memcpy(h.magic, "HQCKPT2", 8);
+  h.version = 2;
   h.n_chains = e->d.n_chains;
   h.first_chain = e->d.first_chain;
   h.max_series = e->d.max_series;
@@ -497,6 +559,15 @@ int hq_checkpoint(hq_engine* e, void* buf, size_t* len) {
   if (e->d.max_series > 0)
     rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(o, e->d.series, C * HQ_N_OBS * (size_t)e->d.max_series * sizeof(double),
                                                  cudaMemcpyDeviceToHost, e->stream), "ck series");
+  o += C * HQ_N_OBS * (size_t)e->d.max_series * sizeof(double);
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(o, e->d.cid, C * 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, e->stream),
+                            "ck ids");
+  o += C * 4 * sizeof(uint32_t);
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(o, e->d.active, C * sizeof(int), cudaMemcpyDeviceToHost, e->stream),
+                            "ck active");
+  o += C * sizeof(int);
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(o, e->d.slen, C * sizeof(int), cudaMemcpyDeviceToHost, e->stream),
+                            "ck series lengths");
   return rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "checkpoint sync");
 }
 
@@ -504,7 +575,7 @@ int hq_restore(hq_engine* e, const void* buf, size_t len) {
   if (!e || !buf || len < sizeof(CkHeader)) return HQ_EINVAL;
   CkHeader h;
   std::memcpy(&h, buf, sizeof h);
-  if (std::memcmp(h.magic, "HQCKPT1", 8) != 0 || h.version != 1) return set_err(e, HQ_EINVAL, "not a checkpoint");
+  if (std::memcmp(h.magic, "HQCKPT2", 8) != 0 || h.version != 2) return set_err(e, HQ_EINVAL, "not a checkpoint");
   if (h.n_chains != e->d.n_chains || h.max_series != e->d.max_series ||
       std::memcmp(&h.params, &e->p, sizeof(hq_params)) != 0)
     return set_err(e, HQ_EINVAL, "checkpoint is for another parameter set or chain count");
@@ -522,6 +593,15 @@ int hq_restore(hq_engine* e, const void* buf, size_t len) {
   if (e->d.max_series > 0)
     rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(e->d.series, o, C * HQ_N_OBS * (size_t)e->d.max_series * sizeof(double),
                                                  cudaMemcpyHostToDevice, e->stream), "rs series");
+  o += C * HQ_N_OBS * (size_t)e->d.max_series * sizeof(double);
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(e->d.cid, o, C * 4 * sizeof(uint32_t), cudaMemcpyHostToDevice, e->stream),
+                            "rs ids");
+  o += C * 4 * sizeof(uint32_t);
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(e->d.active, o, C * sizeof(int), cudaMemcpyHostToDevice, e->stream),
+                            "rs active");
+  o += C * sizeof(int);
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(e->d.slen, o, C * sizeof(int), cudaMemcpyHostToDevice, e->stream),
+                            "rs series lengths");
   rc = rc ? rc : cuda_check(e, hq::launch_reset_acc(e->d, e->stream), "rs acc");
   rc = rc ? rc : cuda_check(e, cudaMemsetAsync(e->d.status, 0, C * sizeof(int), e->stream), "rs status");
   rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "restore sync");
@@ -860,18 +940,16 @@ int hq_cumulative_sweep(hq_engine* e, int n_steps, int n_inner, unsigned flags) 
       rc = ensure_state(e);
       if (rc) return rc;
     }
-    const uint32_t step = (uint32_t)e->cum_steps;
     rc = cuda_check(e, cudaMemcpyAsync(e->nn.X0, d.X, fbytes, cudaMemcpyDeviceToDevice, e->stream), "X0 copy");
     rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(e->nn.ld0, d.logdet, sizeof(double) * d.n_chains,
                                                  cudaMemcpyDeviceToDevice, e->stream), "ld0 copy");
     rc = rc ? rc : cuda_check(e, hq::nn_launch_eval(d, e->nn, d.X, e->nn.F0, 1, e->stream), "nn eval F0");
-    rc = rc ? rc : cuda_check(e, hq::nn_launch_inner(d, e->nn, n_inner, step,
-                                                     (flags & HQ_LOCAL) ? 1 : 0, (flags & HQ_GLOBAL) ? 1 : 0,
-                                                     e->stream), "nn inner");
+    rc = rc ? rc : cuda_check(e, hq::nn_launch_inner(d, e->nn, n_inner, (flags & HQ_LOCAL) ? 1 : 0,
+                                                     (flags & HQ_GLOBAL) ? 1 : 0, e->stream), "nn inner");
     rc = rc ? rc : cuda_check(e, hq::nn_launch_eval(d, e->nn, d.X, e->nn.F1, 0, e->stream), "nn eval F1");
     e->stack_valid = false;
     rc = rc ? rc : ensure_state(e);  // log|det M(X')| (and G, stack of X')
-    rc = rc ? rc : cuda_check(e, hq::nn_launch_decide(d, e->nn, step, e->stream), "nn decide");
+    rc = rc ? rc : cuda_check(e, hq::nn_launch_decide(d, e->nn, e->stream), "nn decide");
     if (rc) return rc;
     e->stack_valid = e->green_valid = false;  // fields may have been restored to X
     e->logdet_valid = true;
@@ -881,10 +959,8 @@ int hq_cumulative_sweep(hq_engine* e, int n_steps, int n_inner, unsigned flags) 
       rc = rc ? rc : cuda_check(e, hq::launch_measure_g0(d, e->stream), "measure");
       if (rc) return rc;
     }
-    const int slot = e->series_len < d.max_series ? e->series_len : -1;
-    rc = cuda_check(e, hq::launch_sweep_end(d, slot, meas ? 1 : 0, e->stream), "sweep_end launch");
+    rc = cuda_check(e, hq::launch_sweep_end(d, meas ? 1 : 0, e->stream), "sweep_end launch");
     if (rc) return rc;
-    if (slot >= 0) e->series_len++;
     e->cum_steps++;
   }
   return HQ_OK;

@@ -52,6 +52,9 @@ struct Dev {
   long long* counters;  // [C][kCounters]
   int* status;        // [C]
   int* sched;         // [kSchedHeader + C] block-move task queue
+  uint32_t* cid;      // [C][4] per chain: Philox key (2 words), chain word, sweep/step counter
+  int* active;        // [C] 0: the slot takes no work
+  int* slen;          // [C] per-sweep records kept for the chain
   // chunk propagators for block moves (used when use_cm != 0)
   int use_cm, n_chunks;
   double* expV;       // [C][L][N] exp(-dtau V) of the current fields
@@ -101,9 +104,9 @@ size_t smem_bytes(const Dev& d);
 
 // Launchers (asynchronous on the stream).  Return cudaGetLastError().
 cudaError_t launch_stack_build(const Dev& d, cudaStream_t s);
-cudaError_t launch_local_chunk(const Dev& d, int s0, int s1, uint32_t sweep, int measure, cudaStream_t s);
-cudaError_t launch_global_phase(const Dev& d, uint32_t sweep, cudaStream_t s);
-cudaError_t launch_sweep_end(const Dev& d, int series_slot, int measured, cudaStream_t s);
+cudaError_t launch_local_chunk(const Dev& d, int s0, int s1, int measure, cudaStream_t s);
+cudaError_t launch_global_phase(const Dev& d, cudaStream_t s);
+cudaError_t launch_sweep_end(const Dev& d, int measured, cudaStream_t s);
 cudaError_t launch_reset_acc(const Dev& d, cudaStream_t s);
 cudaError_t launch_log_weight(const Dev& d, double* out_logw, cudaStream_t s);
 cudaError_t launch_proposals(uint32_t key0, uint32_t key1, uint32_t chain, uint32_t sweep, uint32_t tag,
@@ -112,9 +115,9 @@ double fp64_probe_tflops(int kind, int reps, cudaStream_t s);
 cudaError_t launch_measure_g0(const Dev& d, cudaStream_t s);
 cudaError_t nn_launch_eval(const Dev& d, const NNState& nn, const double* X, double* F, int write_cache,
                            cudaStream_t s);
-cudaError_t nn_launch_inner(const Dev& d, const NNState& nn, int n_inner, uint32_t step, int do_local,
+cudaError_t nn_launch_inner(const Dev& d, const NNState& nn, int n_inner, int do_local,
                             int do_block, cudaStream_t s);
-cudaError_t nn_launch_decide(const Dev& d, const NNState& nn, uint32_t step, cudaStream_t s);
+cudaError_t nn_launch_decide(const Dev& d, const NNState& nn, cudaStream_t s);
 cudaError_t nn_launch_set(const NNState& nn, const float* src_device, cudaStream_t s);
 cudaError_t nn_launch_batch(const Dev& d, const NNState& nn, const double* Xs, const double* ys, const int* idx,
                             int B, float lr, int t_step, cudaStream_t s);

@@ -188,6 +188,7 @@ template <int LMAX>
 __global__ void __launch_bounds__(HQ_THREADS) stack_build_kernel(Dev d) {
   extern __shared__ double smraw[];
   const int c = blockIdx.x;
+  if (!d.active[c]) return;
   const Smem sm = carve(d, smraw);
   load_kinetic(d, sm);
   const double* X = d.X + (size_t)c * d.L * d.n;
@@ -291,9 +292,10 @@ __device__ void measure_green(const Dev& d, int c, const Smem& sm, const double*
 
 template <int LMAX>
 __global__ void __launch_bounds__(HQ_THREADS)
-local_chunk_kernel(Dev d, int s0, int s1, uint32_t sweep, int measure) {
+local_chunk_kernel(Dev d, int s0, int s1, int measure) {
   extern __shared__ double smraw[];
   const int c = blockIdx.x;
+  if (!d.active[c]) return;
   const int n = d.n, L = d.L, k = d.k;
   const Smem sm = carve(d, smraw);
   load_kinetic(d, sm);
@@ -301,7 +303,8 @@ local_chunk_kernel(Dev d, int s0, int s1, uint32_t sweep, int measure) {
   double* G = d.G + (size_t)c * n * n;
   double* A = d.Adl + (size_t)c * k * n;
   double* B = d.Bdl + (size_t)c * k * n;
-  const uint32_t chain = (uint32_t)(d.first_chain + c);
+  const uint32_t* id = d.cid + 4 * (size_t)c;
+  const uint32_t key0 = id[0], key1 = id[1], chain = id[2], sweep = id[3];
   long long n_acc = 0;
 
   for (int s = s0; s < s1; ++s) {
@@ -311,7 +314,7 @@ local_chunk_kernel(Dev d, int s0, int s1, uint32_t sweep, int measure) {
     // exp(-dtau dS_ph) are prepared in parallel; only the ratio needs the running G.
     for (int i = threadIdx.x; i < n; i += HQ_THREADS) {
       double u1, u2;
-      proposal_uniforms(d.key0, d.key1, (uint32_t)(s * n + i), sweep, chain, 0u, u1, u2);
+      proposal_uniforms(key0, key1, (uint32_t)(s * n + i), sweep, chain, 0u, u1, u2);
       const double dx = d.dx_local * (2.0 * u1 - 1.0);
       const double xo = X[(size_t)s * n + i];
       const double xnew = xo + dx;
@@ -654,13 +657,14 @@ __device__ double udv_top_down_cm(const Dev& d, int c, const Smem& sm, int site,
 // One block move X(site, .) += dX of chain c: Philox draw, dtau dS_ph, the full stabilised
 // log|det M(X')| and the Metropolis decision (all threads of the CTA).
 template <int LMAX>
-__device__ void block_move(const Dev& d, const Smem& sm, int c, int site, uint32_t sweep) {
+__device__ void block_move(const Dev& d, const Smem& sm, int c, int site) {
   const int n = d.n, L = d.L;
   double* X = d.X + (size_t)c * L * n;
   HQ_TIC(mv);
   if (threadIdx.x == 0) {
     double u1, u2;
-    proposal_uniforms(d.key0, d.key1, (uint32_t)site, sweep, (uint32_t)(d.first_chain + c), 1u, u1, u2);
+    const uint32_t* id = d.cid + 4 * (size_t)c;
+    proposal_uniforms(id[0], id[1], (uint32_t)site, id[3], id[2], 1u, u1, u2);
     sm.scal[0] = d.dx_global * (2.0 * u1 - 1.0);
     sm.scal[1] = u2;
   }
@@ -718,7 +722,7 @@ __device__ __forceinline__ unsigned long long global_timer_ns() {
 // every worker stops taking tasks.  sched = [counter, abort, ..., progress[C] at
 // kSchedHeader], zeroed before the launch.
 template <int LMAX>
-__global__ void __launch_bounds__(HQ_THREADS) global_phase_kernel(Dev d, uint32_t sweep) {
+__global__ void __launch_bounds__(HQ_THREADS) global_phase_kernel(Dev d) {
   extern __shared__ double smraw[];
   __shared__ int s_task;
   const Smem sm = carve(d, smraw);
@@ -760,11 +764,13 @@ __global__ void __launch_bounds__(HQ_THREADS) global_phase_kernel(Dev d, uint32_
     if (t < 0 || t >= ntask) break;
     __threadfence();  // acquire: the previous step of this chain (possibly on another SM)
     const int step = t / C;
-    if (d.use_cm) {
-      if (step == 0) build_chunks<LMAX>(d, sm, t % C);
-      else block_move<LMAX>(d, sm, t % C, step - 1, sweep);
-    } else {
-      block_move<LMAX>(d, sm, t % C, step, sweep);
+    if (d.active[t % C]) {
+      if (d.use_cm) {
+        if (step == 0) build_chunks<LMAX>(d, sm, t % C);
+        else block_move<LMAX>(d, sm, t % C, step - 1);
+      } else {
+        block_move<LMAX>(d, sm, t % C, step);
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -774,9 +780,10 @@ __global__ void __launch_bounds__(HQ_THREADS) global_phase_kernel(Dev d, uint32_
   }
 }
 
-__global__ void __launch_bounds__(HQ_THREADS) sweep_end_kernel(Dev d, int slot, int measured) {
+__global__ void __launch_bounds__(HQ_THREADS) sweep_end_kernel(Dev d, int measured) {
   __shared__ double red[HQ_WARPS];
   const int c = blockIdx.x;
+  if (!d.active[c]) return;
   const int n = d.n, L = d.L;
   const double* X = d.X + (size_t)c * L * n;
   double s1 = 0.0, s2 = 0.0;
@@ -800,8 +807,12 @@ __global__ void __launch_bounds__(HQ_THREADS) sweep_end_kernel(Dev d, int slot, 
     vals[HQ_OBS_X_MEAN] = xm;
     vals[HQ_OBS_X2] = x2;
     vals[HQ_OBS_WRAP_ERR] = acc[ACC_WRAP];
-    if (slot >= 0 && slot < d.max_series)
+    const int slot = d.slen[c];
+    if (slot < d.max_series) {
       for (int o = 0; o < HQ_N_OBS; ++o) d.series[((size_t)c * HQ_N_OBS + o) * d.max_series + slot] = vals[o];
+      d.slen[c] = slot + 1;
+    }
+    d.cid[4 * (size_t)c + 3] += 1u;  // the chain's sweep (or cumulative step) counter
     if (has) {
       tot[TOT_DENSITY] += vals[HQ_OBS_DENSITY];
       tot[TOT_DOCC] += vals[HQ_OBS_DOUBLE_OCC];
@@ -822,6 +833,7 @@ __global__ void __launch_bounds__(HQ_THREADS) measure_g0_kernel(Dev d) {
   extern __shared__ double smraw[];
   const Smem sm = carve(d, smraw);
   const int c = blockIdx.x;
+  if (!d.active[c]) return;
   measure_green(d, c, sm, d.G + (size_t)c * d.n * d.n);
 }
 
@@ -955,13 +967,13 @@ cudaError_t launch_stack_build(const Dev& d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_local_chunk(const Dev& d, int s0, int s1, uint32_t sweep, int measure, cudaStream_t s) {
-  HQ_DISPATCH(local_chunk_kernel, d, s, d, s0, s1, sweep, measure);
+cudaError_t launch_local_chunk(const Dev& d, int s0, int s1, int measure, cudaStream_t s) {
+  HQ_DISPATCH(local_chunk_kernel, d, s, d, s0, s1, measure);
   return cudaGetLastError();
 }
 
 template <int LMAX>
-static cudaError_t launch_phase(const Dev& d, uint32_t sweep, cudaStream_t s) {
+static cudaError_t launch_phase(const Dev& d, cudaStream_t s) {
   const size_t sb = smem_bytes(d);
   allow_smem(global_phase_kernel<LMAX>, sb);
   int dev = 0, sms = 0, occ = 0;
@@ -971,23 +983,24 @@ static cudaError_t launch_phase(const Dev& d, uint32_t sweep, cudaStream_t s) {
     st = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, global_phase_kernel<LMAX>, HQ_THREADS, sb);
   if (st != cudaSuccess) return st;
   if (occ < 1) return cudaErrorInvalidConfiguration;
-  // every worker must be resident (a waiting worker relies on the owner of the previous
-  // task running), so the grid never exceeds one wave
-  const int ntask = (d.n + (d.use_cm ? 1 : 0)) * d.n_chains;
+  // One wave at most.  A worker only waits for a task that an earlier, running worker has
+  // taken, so progress never depends on a block that is not resident (other streams may hold
+  // SMs).  The steps of one chain are sequential, so at most C tasks run at once: more
+  // workers than chains would only wait, holding SMs that concurrent launches could use.
   int workers = sms * (occ < kWorkersPerSm ? occ : kWorkersPerSm);
-  if (workers > ntask) workers = ntask;
+  if (workers > d.n_chains) workers = d.n_chains;
   st = cudaMemsetAsync(d.sched, 0, sizeof(int) * (kSchedHeader + d.n_chains), s);
   if (st != cudaSuccess) return st;
-  global_phase_kernel<LMAX><<<workers, HQ_THREADS, sb, s>>>(d, sweep);
+  global_phase_kernel<LMAX><<<workers, HQ_THREADS, sb, s>>>(d);
   return cudaGetLastError();
 }
 
-cudaError_t launch_global_phase(const Dev& d, uint32_t sweep, cudaStream_t s) {
+cudaError_t launch_global_phase(const Dev& d, cudaStream_t s) {
   switch (lmax_of(d.nx, d.ny)) {
-    case 2: return launch_phase<2>(d, sweep, s);
-    case 4: return launch_phase<4>(d, sweep, s);
-    case 8: return launch_phase<8>(d, sweep, s);
-    default: return launch_phase<16>(d, sweep, s);
+    case 2: return launch_phase<2>(d, s);
+    case 4: return launch_phase<4>(d, s);
+    case 8: return launch_phase<8>(d, s);
+    default: return launch_phase<16>(d, s);
   }
 }
 
@@ -996,8 +1009,8 @@ cudaError_t launch_measure_g0(const Dev& d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_sweep_end(const Dev& d, int slot, int measured, cudaStream_t s) {
-  sweep_end_kernel<<<d.n_chains, HQ_THREADS, 0, s>>>(d, slot, measured);
+cudaError_t launch_sweep_end(const Dev& d, int measured, cudaStream_t s) {
+  sweep_end_kernel<<<d.n_chains, HQ_THREADS, 0, s>>>(d, measured);
   return cudaGetLastError();
 }
 

@@ -169,10 +169,11 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_eval_kernel(Dev d, NNState nn, 
 // cumulative accept needs a reversible proposal; so each step draws a direction (second
 // uniform of the step's Philox block, tag 4): forward (l, i ascending, then block moves i
 // ascending) or the exact reverse of that sequence, with probability 1/2 each.
-__global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn, int n_inner, uint32_t step,
-                                                              int do_local, int do_block) {
+__global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn, int n_inner, int do_local,
+                                                              int do_block) {
   extern __shared__ __align__(16) char nraw[];
   const int c = blockIdx.x, n = d.n, L = d.L, NL = n * L;
+  if (!d.active[c]) return;
   const NNSmem s = nn_carve(n, nraw);
   load_weights(nn.wbf, s.w);
   double* X = d.X + (size_t)c * NL;
@@ -181,11 +182,12 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
   const int g = threadIdx.x / 8, sub = threadIdx.x % 8;
   float* z = s.z + g * (NN_IN + 3);
   float* h1 = s.h1 + g * NN_H;
-  const uint32_t chain = (uint32_t)(d.first_chain + c);
+  const uint32_t* id = d.cid + 4 * (size_t)c;
+  const uint32_t key0 = id[0], key1 = id[1], chain = id[2], step = id[3];
   long long nl_acc = 0, nb_acc = 0;
   const double kfac = d.mass / (2.0 * d.dtau), pfac = 0.5 * d.dtau * d.mass * (d.omega * d.omega);
   double du1, du2;
-  proposal_uniforms(d.key0, d.key1, 0u, step, chain, 4u, du1, du2);
+  proposal_uniforms(key0, key1, 0u, step, chain, 4u, du1, du2);
   const bool fwd = du2 < 0.5;
   for (int u = 0; u < n_inner; ++u) {
     const uint32_t isw = step * (uint32_t)n_inner + (uint32_t)u;
@@ -196,7 +198,7 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
         const int sl = fwd ? sl0 : L - 1 - sl0;
         for (int i = threadIdx.x; i < n; i += HQ_THREADS) {
           double u1, u2;
-          proposal_uniforms(d.key0, d.key1, (uint32_t)(sl * n + i), isw, chain, 2u, u1, u2);
+          proposal_uniforms(key0, key1, (uint32_t)(sl * n + i), isw, chain, 2u, u1, u2);
           const double dx = d.dx_local * (2.0 * u1 - 1.0);
           const double xo = X[(size_t)sl * n + i], xn = xo + dx;
           const double xp = X[(size_t)((sl + 1) % L) * n + i], xm = X[(size_t)((sl - 1 + L) % L) * n + i];
@@ -242,7 +244,7 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
         const int i = fwd ? i0 : n - 1 - i0;
         if (threadIdx.x == 0) {
           double u1, u2;
-          proposal_uniforms(d.key0, d.key1, (uint32_t)i, isw, chain, 3u, u1, u2);
+          proposal_uniforms(key0, key1, (uint32_t)i, isw, chain, 3u, u1, u2);
           s.scal[1] = d.dx_global * (2.0 * u1 - 1.0);
           s.scal[2] = u2;
         }
@@ -311,12 +313,14 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
 
 // Cumulative accept of X' (fields now in d.X, log|det M(X')| in d.logdet after the stack
 // build) against X (saved in nn.X0 with nn.ld0, nn.F0): p_c = exp(2 dlog|det M| - 2 dF).
-__global__ void __launch_bounds__(HQ_THREADS) nn_decide_kernel(Dev d, NNState nn, uint32_t step) {
+__global__ void __launch_bounds__(HQ_THREADS) nn_decide_kernel(Dev d, NNState nn) {
   const int c = blockIdx.x, NL = d.n * d.L;
+  if (!d.active[c]) return;
   __shared__ int acc;
   if (threadIdx.x == 0) {
     double u1, u2;
-    proposal_uniforms(d.key0, d.key1, 0u, step, (uint32_t)(d.first_chain + c), 4u, u1, u2);
+    const uint32_t* id = d.cid + 4 * (size_t)c;
+    proposal_uniforms(id[0], id[1], 0u, id[3], id[2], 4u, u1, u2);
     const double ld1 = d.logdet[c], ld0 = nn.ld0[c];
     const double arg = 2.0 * (ld1 - ld0) - 2.0 * (nn.F1[c] - nn.F0[c]);
     const double pc = exp(fmin(arg, 709.0));
@@ -554,16 +558,16 @@ cudaError_t nn_launch_eval(const Dev& d, const NNState& nn, const double* X, dou
   return cudaGetLastError();
 }
 
-cudaError_t nn_launch_inner(const Dev& d, const NNState& nn, int n_inner, uint32_t step, int do_local,
-                            int do_block, cudaStream_t s) {
+cudaError_t nn_launch_inner(const Dev& d, const NNState& nn, int n_inner, int do_local, int do_block,
+                            cudaStream_t s) {
   const size_t sb = nn_smem_bytes(d.n);
   smem_opt_in((const void*)nn_inner_kernel, sb);
-  nn_inner_kernel<<<d.n_chains, HQ_THREADS, sb, s>>>(d, nn, n_inner, step, do_local, do_block);
+  nn_inner_kernel<<<d.n_chains, HQ_THREADS, sb, s>>>(d, nn, n_inner, do_local, do_block);
   return cudaGetLastError();
 }
 
-cudaError_t nn_launch_decide(const Dev& d, const NNState& nn, uint32_t step, cudaStream_t s) {
-  nn_decide_kernel<<<d.n_chains, HQ_THREADS, 0, s>>>(d, nn, step);
+cudaError_t nn_launch_decide(const Dev& d, const NNState& nn, cudaStream_t s) {
+  nn_decide_kernel<<<d.n_chains, HQ_THREADS, 0, s>>>(d, nn);
   return cudaGetLastError();
 }
 

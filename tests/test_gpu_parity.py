@@ -270,3 +270,26 @@ def test_invalid_arguments_are_rejected(hq):
         eng.green(5)
     out = ctypes.c_void_p()
     assert lib.hq_create(ctypes.byref(hq.make_params(p)), 1, 0, 0, None, 0, None, ctypes.byref(out)) == hq.HQ_ENOMEM
+
+
+def test_slot_identity_matches_oracle_and_is_position_independent(hq):
+    """A chain loaded into slot 2 of a mixed engine (own key, chain word, sweep counter; other
+    slots busy or idle) follows the oracle chain with that identity, bit for bit."""
+    from oracle import dqmc
+    p = HolsteinParams(nx=4, ny=4, beta=1.5, delay_k=4)
+    X = initial_fields(p, 4, seed=12)
+    eng = hq.Engine(p, 4, max_series=4)
+    eng.set_fields(X)
+    eng.set_chain(2, X[3], seed=987654321, chain_id=77, sweep=5)
+    eng.set_active(1, False)
+    eng.sweep(2)
+    Xg = eng.get_fields()
+    assert np.array_equal(Xg[1], X[1])  # idle slot untouched
+    ch = dqmc.OracleChain(p.with_(seed=987654321), X[3], chain=77, sweep=5)
+    ch.sweep()
+    ch.sweep()
+    assert np.array_equal(Xg[2], ch.X)
+    alone = hq.Engine(p, 1)
+    alone.set_chain(0, X[3], seed=987654321, chain_id=77, sweep=5)
+    alone.sweep(2)
+    assert np.array_equal(alone.get_fields()[0], Xg[2])
