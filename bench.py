@@ -414,8 +414,7 @@ def run_learned(args):
     eng.close()
     net = hq.Engine(params, 1)
     net.attach_network(64, Xtr.shape[0])
-    from oracle import nn as nn_oracle  # initial weights only (seeded He initialisation)
-    net.set_params(nn_oracle.init_params(args.nn_seed))
+    net.set_params(hq.init_network(args.nn_seed))
     Xd, yd = torch.from_numpy(Xtr).to(dev), torch.from_numpy(ytr).to(dev)
     t0 = time.perf_counter()
     # learning rate halved every third of the epochs (Adam state carries over)
@@ -483,24 +482,35 @@ def run_learned(args):
     return 0
 
 
-SERVING_KINDS = (("4x4 beta=2", dict(nx=4, ny=4, beta=2.0)), ("6x6 beta=2", dict(nx=6, ny=6, beta=2.0)),
-                 ("8x8 beta=4", dict(nx=8, ny=8, beta=4.0)))
+SERVING_SIDES = (4, 6, 8)
+SERVING_BETAS = (1.0, 2.0, 4.0)
+SERVING_LAMBDAS = (0.15, 0.25, 0.35)
+
+
+def serving_params(side, beta, lam, seed):
+    """Holstein parameters of one request: t = M = Omega = 1, g from lambda = g^2/(M Omega^2 8t),
+    half filling mu = -g^2/(M Omega^2)."""
+    g = math.sqrt(8.0 * lam)
+    return workloads.HolsteinParams(nx=side, ny=side, beta=beta, g=g, mu=-g * g, seed=seed)
 
 
 def run_serving(args):
-    """Continuous-batching service under Poisson arrivals (plain sampler).
+    """Continuous-batching service under Poisson arrivals.
 
-    Requests of three lattice shapes (scaled down from the batched workload so that a request
-    finishes in about a second) arrive at args.rate per second for args.duration seconds, each
-    asking for args.req_sweeps sweeps of one chain with its own seed, chain word and initial
-    fields.  Reported: served chain-sweeps/s over the whole run, request latency (arrival to
-    result on the host) percentiles, queueing delay, and, for reference, the latency of a few
-    requests served alone on an idle GPU.
+    Each request asks for args.req_sweeps sweeps (plain) or cumulative steps (learned) of one
+    chain with its own lattice side, beta, lambda, seed, chain word and initial fields; side,
+    beta, lambda and the sampler are drawn uniformly (the sizes are scaled down from 6..16 and
+    beta 4..12 so that a request takes well under a second to a few seconds).  Learned requests
+    carry a small seeded network (the cumulative accept keeps them exact whatever it is).
+    Reported: served chain-sweeps/s, request latency (arrival to result on the host)
+    percentiles, queueing delay, and the latency of the same kinds served alone on an idle GPU.
     """
     import numpy as np
     import torch
+    import paper_1905_07440_gb300 as hq
     from paper_1905_07440_gb300.serving import GpuBackend, Request, Server
 
+    theta = hq.init_network(args.nn_seed, out_scale=0.1)
     rng = np.random.default_rng(args.serve_seed)
     reqs, t = [], 0.0
     while True:
@@ -508,60 +518,75 @@ def run_serving(args):
         if t > args.duration:
             break
         k = len(reqs)
-        kind, shape = SERVING_KINDS[rng.integers(len(SERVING_KINDS))]
-        p = workloads.HolsteinParams(**shape, seed=workloads.BATCHED.seed + 7919 * k)
-        reqs.append(Request(rid=k, params=p, X0=workloads.initial_fields(p, 1, seed=10_000 + k)[0],
-                            sweeps=args.req_sweeps, chain_id=k, arrival=t))
-        reqs[-1].kind = kind
+        side = int(rng.choice(SERVING_SIDES))
+        beta = float(rng.choice(SERVING_BETAS))
+        lam = float(rng.choice(SERVING_LAMBDAS))
+        sampler = "learned" if rng.random() < args.learned_frac else "plain"
+        p = serving_params(side, beta, lam, workloads.BATCHED.seed + 7919 * k)
+        r = Request(rid=k, params=p, X0=workloads.initial_fields(p, 1, seed=10_000 + k)[0], sweeps=args.req_sweeps,
+                    sampler=sampler, theta=theta if sampler == "learned" else None, chain_id=k, arrival=t)
+        r.kind = (side, beta, sampler)
+        reqs.append(r)
     backend = GpuBackend()
-    # warm-up: one request of each kind (kernel loading, allocator)
-    warm = [Request(rid=-1 - j, params=workloads.HolsteinParams(**sh), X0=workloads.initial_fields(
-        workloads.HolsteinParams(**sh), 1)[0], sweeps=1) for j, (_, sh) in enumerate(SERVING_KINDS)]
-    Server(backend, args.hbm_budget, args.slots).run(warm)
+
+    def server():
+        return Server(backend, args.hbm_budget, args.slots, max_pools=args.max_pools)
+
+    # warm-up: one request of each lattice side and sampler (kernel loading, allocator)
+    warm = [Request(rid=-1, params=serving_params(s_, 1.0, 0.25, 1), X0=workloads.initial_fields(
+        serving_params(s_, 1.0, 0.25, 1), 1)[0], sweeps=1, sampler=sm, theta=theta)
+        for s_ in SERVING_SIDES for sm in ("plain", "learned")]
+    server().run(warm)
     torch.cuda.synchronize()
-    peak = [0]
+    peak = {"bytes": 0, "pools": 0}
 
     class Tracking(Server):
         def poll(self):
             super().poll()
-            peak[0] = max(peak[0], self.used)
+            peak["bytes"] = max(peak["bytes"], self.used)
+            peak["pools"] = max(peak["pools"], len(self.pools))
 
-    srv = Tracking(backend, args.hbm_budget, args.slots)
+    srv = Tracking(backend, args.hbm_budget, args.slots, max_pools=args.max_pools)
     sampler = ClockSampler()
     sampler.start()
     t0 = time.perf_counter()
     done = srv.run(reqs)
     wall = time.perf_counter() - t0
     clocks = sampler.stop()
+    pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
     lat = np.array([r.done - r.arrival for r in done]) * 1e3
     wait = np.array([r.admitted - r.arrival for r in done]) * 1e3
-    by_kind = {}
-    for kind, _ in SERVING_KINDS:
-        lk = np.array([r.done - r.arrival for r in done if r.kind == kind]) * 1e3
-        if lk.size:
-            by_kind[kind] = {"n": int(lk.size), "p50": float(np.percentile(lk, 50)), "p99": float(np.percentile(lk, 99))}
-    # the same kinds served alone (one request at a time, idle GPU)
+    by_side = {}
+    for side in SERVING_SIDES:
+        lk = np.array([r.done - r.arrival for r in done if r.kind[0] == side]) * 1e3
+        by_side[f"{side}x{side}"] = {"n": int(lk.size), "p50": pct(lk, 50), "p99": pct(lk, 99)}
+    # the same kinds alone (one request at a time, idle GPU) against the mix
     alone = {}
-    for kind, sh in SERVING_KINDS:
-        ts = []
-        for j in range(3):
-            p = workloads.HolsteinParams(**sh, seed=123 + j)
-            r = Request(rid=j, params=p, X0=workloads.initial_fields(p, 1, seed=j)[0], sweeps=args.req_sweeps)
-            a = time.perf_counter()
-            Server(backend, args.hbm_budget, 1).run([r])
-            ts.append((time.perf_counter() - a) * 1e3)
-        alone[kind] = float(np.median(ts))
+    for side in SERVING_SIDES:
+        for beta in (SERVING_BETAS[0], SERVING_BETAS[-1]):
+            ts = []
+            for j in range(3):
+                p = serving_params(side, beta, 0.25, 123 + j)
+                r = Request(rid=j, params=p, X0=workloads.initial_fields(p, 1, seed=j)[0], sweeps=args.req_sweeps)
+                a = time.perf_counter()
+                server().run([r])
+                ts.append((time.perf_counter() - a) * 1e3)
+            mixed = np.array([r.done - r.arrival for r in done if r.kind == (side, beta, "plain")]) * 1e3
+            alone[f"{side}x{side} beta={beta:g} plain"] = {"alone_ms": float(np.median(ts)), "mix_p50_ms": pct(mixed, 50),
+                                                           "mix_n": int(mixed.size)}
     served = sum(r.sweeps for r in done)
-    pct = lambda a, q: float(np.percentile(a, q))
+    n_learned = sum(1 for r in done if r.sampler == "learned")
     line = {"metric": METRIC, "mode": "serving", "value": served / wall, "unit": "chain-sweeps/s (served)",
-            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "Poisson mix of " + ", ".join(k for k, _ in SERVING_KINDS) + " (L = beta/0.1)",
+            "higher_is_better": True, "dtype": "f64 (learned requests: bf16-weight/fp32 network)", "data": "synthetic",
+            "config": {"workload": "Poisson arrivals; side in %s, beta in %s, lambda in %s, learned fraction %g"
+                                   % (SERVING_SIDES, SERVING_BETAS, SERVING_LAMBDAS, args.learned_frac),
                        "rate_per_s": args.rate, "duration_s": args.duration, "sweeps_per_request": args.req_sweeps,
-                       "slots_per_pool": args.slots, "hbm_budget_bytes": args.hbm_budget},
-            "requests": len(done), "wall_s": wall, "requests_per_s": len(done) / wall,
+                       "slots_per_pool": args.slots, "max_pools": args.max_pools, "hbm_budget_bytes": args.hbm_budget},
+            "requests": len(done), "learned_requests": n_learned, "wall_s": wall, "requests_per_s": len(done) / wall,
             "latency_ms": {"p50": pct(lat, 50), "p90": pct(lat, 90), "p99": pct(lat, 99), "max": float(lat.max())},
-            "queue_ms": {"p50": pct(wait, 50), "p99": pct(wait, 99)}, "latency_by_kind_ms": by_kind,
-            "alone_latency_ms": alone, "peak_pool_bytes": int(peak[0]), "clocks": clocks}
+            "queue_ms": {"p50": pct(wait, 50), "p99": pct(wait, 99)}, "latency_by_side_ms": by_side,
+            "alone_vs_mix": alone, "peak_pool_bytes": int(peak["bytes"]), "peak_pools": peak["pools"],
+            "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -618,10 +643,16 @@ def main():
     ap.add_argument("--rate", type=float, default=40.0, help="serving mode: requests per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serving mode: seconds of arrivals")
     ap.add_argument("--req-sweeps", type=int, default=10, help="serving mode: sweeps per request")
-    ap.add_argument("--slots", type=int, default=32, help="serving mode: chain slots per pool")
+    ap.add_argument("--slots", type=int, default=16, help="serving mode: chain slots per pool")
+    ap.add_argument("--max-pools", type=int, default=32, help="serving mode: live pools (streams)")
+    ap.add_argument("--learned-frac", type=float, default=0.5, help="serving mode: share of learned requests")
     ap.add_argument("--hbm-budget", type=int, default=8 << 30, help="serving mode: bytes for pool state")
     ap.add_argument("--serve-seed", type=int, default=3)
     args = ap.parse_args()
+    if args.workload == "serving":
+        # one hardware queue per pool stream: with fewer, streams share queues and a pool's
+        # launches wait behind another pool's running kernels (read when CUDA initialises)
+        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     if args.workload == "learned":
         sys.exit(run_learned(args))
     if args.workload == "serving":

@@ -151,8 +151,11 @@ int hq_block_move_method(const hq_engine* e);
  * cumulative step of that chain), so a chain's trajectory depends only on its own fields and
  * identity, not on which slot it occupies or what else runs in the engine.
  * hq_set_chain loads one slot (fields X_host [L][N], key `seed`, chain word, counter), clears
- * its counters, totals and series, and makes it active; hq_set_active(e, slot, 0) idles a slot
- * (it takes no work until reactivated or reloaded).  Both synchronise the stream. */
+ * its counters, totals and series, and makes it active; it synchronises the stream, so the
+ * caller may reuse X_host on return.  X_host in page-locked memory keeps the copy from
+ * waiting for kernels of other streams.  hq_set_active(e, slot, 0) idles a slot (it takes no
+ * work until reactivated or reloaded); it is stream-ordered and does not synchronise.
+ * Errors: HQ_EINVAL for a null engine or pointer or a slot outside [0, n_chains). */
 int hq_set_chain(hq_engine* e, int slot, const double* X_host, uint64_t seed, uint32_t chain_id, uint32_t sweep);
 int hq_set_active(hq_engine* e, int slot, int active);
 

@@ -6,6 +6,7 @@ device arena and the stream; there is no CPU fallback -- importing the binding f
 loudly when the library has not been built.
 """
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -260,11 +261,18 @@ class Engine:
         return {PHASES[i]: (float(ms[i]), int(n[i])) for i in range(HQ_N_PHASES)}
 
     def set_chain(self, slot, X, seed, chain_id, sweep=0):
-        """Load one slot: fields X [L][N], Philox key `seed`, chain word, sweep counter."""
-        X = np.ascontiguousarray(X, dtype=np.float64)
-        assert X.shape == self.field_shape[1:]
-        self._check(self.lib.hq_set_chain(self._h, int(slot), _dptr(X), int(seed), int(chain_id), int(sweep)),
-                    "hq_set_chain")
+        """Load one slot: fields X [L][N], Philox key `seed`, chain word, sweep counter.  The
+        fields go through a page-locked staging buffer so that the copy does not wait for
+        kernels that other engines run on other streams."""
+        import torch
+        X = np.asarray(X, dtype=np.float64)
+        if X.shape != self.field_shape[1:]:
+            raise ValueError(f"fields must have shape {self.field_shape[1:]}")
+        if getattr(self, "_stage", None) is None:
+            self._stage = torch.empty(self.field_shape[1:], dtype=torch.float64, pin_memory=True)
+        self._stage.numpy()[...] = X
+        self._check(self.lib.hq_set_chain(self._h, int(slot), ctypes.cast(self._stage.data_ptr(), _dp), int(seed),
+                                          int(chain_id), int(sweep)), "hq_set_chain")
 
     def set_active(self, slot, active):
         self._check(self.lib.hq_set_active(self._h, int(slot), 1 if active else 0), "hq_set_active")
@@ -359,6 +367,19 @@ def proposal_uniforms(seed, chain, sweep, events, tag, stream=None):
     if rc != HQ_OK:
         raise HQError(f"hq_proposal_uniforms failed ({rc})")
     return u1, u2
+
+
+def init_network(seed, out_scale=1.0):
+    """Seeded He initialisation of the patch network in the flat layout of hq_nn_set_params:
+    W1[25][64], b1[64], W2[64][64], b2[64], W3[64], b3 (biases zero, W3 ~ 0.01 N(0,1) scaled
+    by out_scale)."""
+    rng = np.random.default_rng(seed)
+    w1 = rng.standard_normal((25, 64)) * math.sqrt(2.0 / 25)
+    w2 = rng.standard_normal((64, 64)) * math.sqrt(2.0 / 64)
+    w3 = rng.standard_normal(64) * 0.01 * out_scale
+    out = np.concatenate([w1.ravel(), np.zeros(64), w2.ravel(), np.zeros(64), w3, [0.0]]).astype(np.float32)
+    assert out.size == HQ_NN_PARAMS
+    return out
 
 
 def tau_int(series, c=6.0):

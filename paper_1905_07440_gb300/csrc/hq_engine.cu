@@ -11,6 +11,12 @@
 #include "../../include/holstein_dqmc.h"
 
 struct hq_engine {
+  void set_act(int slot, int v) {
+    act[slot] = v;
+    int n = 0;
+    for (int a : act) n += a ? 1 : 0;
+    d.n_active = n;
+  }
   hq_params p;
   hq::Dev d;
   cudaStream_t stream;
@@ -22,6 +28,7 @@ struct hq_engine {
   bool stack_valid;     // left stack, G_0 and log|det M| match the fields
   bool logdet_valid;    // log|det M| matches the fields
   bool green_valid;     // G holds G_0 of the fields
+  std::vector<int> act;  // host mirror of the active flags
   std::string err;
   // optional per-phase timing
   struct Span { cudaEvent_t a, b; int phase, launches; };
@@ -271,18 +278,10 @@ int hq_create(const hq_params* p, int n_chains, int first_chain, int max_series,
   rc = rc ? rc : cuda_check(e, cudaMemcpyAsync((void*)d.kin, kin.data(), kin.size() * sizeof(double),
                                                cudaMemcpyHostToDevice, e->stream), "kinetic upload");
   // per-chain identity: key = seed, chain word = first_chain + c, counter 0; all active
-  std::vector<uint32_t> cid(4 * (size_t)n_chains);
-  std::vector<int> act((size_t)n_chains, 1);
-  for (int c = 0; c < n_chains; ++c) {
-    cid[4 * c] = d.key0;
-    cid[4 * c + 1] = d.key1;
-    cid[4 * c + 2] = (uint32_t)(first_chain + c);
-    cid[4 * c + 3] = 0u;
-  }
-  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(d.cid, cid.data(), cid.size() * 4, cudaMemcpyHostToDevice, e->stream),
-                            "chain ids");
-  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(d.active, act.data(), act.size() * 4, cudaMemcpyHostToDevice,
-                                               e->stream), "active flags");
+  rc = rc ? rc : cuda_check(e, hq::launch_slot_control(d, -1, d.key0, d.key1, (uint32_t)first_chain, 0u, 1, 1,
+                                                       e->stream), "chain ids");
+  e->act.assign((size_t)n_chains, 1);
+  e->d.n_active = n_chains;
   rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "create sync");
   if (rc) {
     std::fprintf(stderr, "hq_create: %s\n", e->err.c_str());
@@ -476,26 +475,13 @@ int hq_set_chain(hq_engine* e, int slot, const double* X_host, uint64_t seed, ui
   if (!e || !X_host || slot < 0 || slot >= e->d.n_chains) return HQ_EINVAL;
   const hq::Dev& d = e->d;
   const size_t NL = (size_t)d.L * d.n;
-  const uint32_t id[4] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), chain_id, sweep};
-  const int one = 1, zero = 0;
   cudaStream_t st = e->stream;
   int rc = cuda_check(e, cudaMemcpyAsync(d.X + slot * NL, X_host, NL * sizeof(double), cudaMemcpyHostToDevice, st),
                       "set_chain fields");
-  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(d.cid + 4 * (size_t)slot, id, sizeof(id), cudaMemcpyHostToDevice, st),
-                            "set_chain id");
-  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(d.active + slot, &one, sizeof(int), cudaMemcpyHostToDevice, st),
-                            "set_chain active");
-  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(d.slen + slot, &zero, sizeof(int), cudaMemcpyHostToDevice, st),
-                            "set_chain series");
-  rc = rc ? rc : cuda_check(e, cudaMemsetAsync(d.acc + (size_t)slot * hq::kAccSlots, 0, sizeof(double) * hq::kAccSlots, st),
-                            "set_chain acc");
-  rc = rc ? rc : cuda_check(e, cudaMemsetAsync(d.tot + (size_t)slot * hq::kTotSlots, 0, sizeof(double) * hq::kTotSlots, st),
-                            "set_chain totals");
-  rc = rc ? rc : cuda_check(e, cudaMemsetAsync(d.counters + (size_t)slot * hq::kCounters, 0,
-                                               sizeof(long long) * hq::kCounters, st), "set_chain counters");
-  rc = rc ? rc : cuda_check(e, cudaMemsetAsync(d.status + slot, 0, sizeof(int), st), "set_chain status");
-  if (d.use_cm) rc = rc ? rc : cuda_check(e, cudaMemsetAsync(d.cbuf + slot, 0, sizeof(int), st), "set_chain cbuf");
-  // the host values above are on the stack: make the copies complete before returning
+  rc = rc ? rc : cuda_check(e, hq::launch_slot_control(d, slot, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32),
+                                                       chain_id, sweep, 1, 1, st), "set_chain slot");
+  if (!rc) e->set_act(slot, 1);
+  // the caller may reuse X_host on return
   rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(st), "set_chain sync");
   e->stack_valid = e->logdet_valid = e->green_valid = false;
   return rc;
@@ -504,9 +490,8 @@ int hq_set_chain(hq_engine* e, int slot, const double* X_host, uint64_t seed, ui
 int hq_set_active(hq_engine* e, int slot, int active) {
   if (!e || slot < 0 || slot >= e->d.n_chains) return HQ_EINVAL;
   const int v = active ? 1 : 0;
-  int rc = cuda_check(e, cudaMemcpyAsync(e->d.active + slot, &v, sizeof(int), cudaMemcpyHostToDevice, e->stream),
-                      "set_active");
-  rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "set_active sync");
+  int rc = cuda_check(e, hq::launch_slot_control(e->d, slot, 0u, 0u, 0u, 0u, v, 0, e->stream), "set_active");
+  if (!rc) e->set_act(slot, v);
   if (v) e->stack_valid = e->logdet_valid = e->green_valid = false;
   return rc;
 }
@@ -599,6 +584,12 @@ int hq_restore(hq_engine* e, const void* buf, size_t len) {
   o += C * 4 * sizeof(uint32_t);
   rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(e->d.active, o, C * sizeof(int), cudaMemcpyHostToDevice, e->stream),
                             "rs active");
+  for (size_t c = 0; c < C; ++c) {
+    int v;
+    std::memcpy(&v, o + c * sizeof(int), sizeof(int));
+    e->act[c] = v ? 1 : 0;
+  }
+  e->set_act(0, e->act[0]);
   o += C * sizeof(int);
   rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(e->d.slen, o, C * sizeof(int), cudaMemcpyHostToDevice, e->stream),
                             "rs series lengths");
@@ -714,6 +705,7 @@ int hq_logdet_noalloc(const hq_params* p, int n_chains, const double* X_device, 
   d.n_wrap = p->n_wrap;
   d.k = p->delay_k;
   d.n_chains = n_chains;
+  d.n_active = n_chains;
   d.t = p->t;
   d.mu = p->mu;
   d.omega = p->omega;

@@ -55,6 +55,7 @@ struct Dev {
   uint32_t* cid;      // [C][4] per chain: Philox key (2 words), chain word, sweep/step counter
   int* active;        // [C] 0: the slot takes no work
   int* slen;          // [C] per-sweep records kept for the chain
+  int n_active;       // host count of active slots (sizes the persistent launch)
   // chunk propagators for block moves (used when use_cm != 0)
   int use_cm, n_chunks;
   double* expV;       // [C][L][N] exp(-dtau V) of the current fields
@@ -102,12 +103,21 @@ struct NNState {
 
 size_t smem_bytes(const Dev& d);
 
+// Raise a kernel's dynamic shared memory limit to the device maximum (once per kernel and
+// device) when it needs more than the default 48 KB.
+cudaError_t opt_in_smem(const void* kernel, size_t bytes);
+
 // Launchers (asynchronous on the stream).  Return cudaGetLastError().
 cudaError_t launch_stack_build(const Dev& d, cudaStream_t s);
 cudaError_t launch_local_chunk(const Dev& d, int s0, int s1, int measure, cudaStream_t s);
 cudaError_t launch_global_phase(const Dev& d, cudaStream_t s);
 cudaError_t launch_sweep_end(const Dev& d, int measured, cudaStream_t s);
 cudaError_t launch_reset_acc(const Dev& d, cudaStream_t s);
+// Slot identity/activity: slot >= 0 sets that slot (reset: key, chain word, sweep counter,
+// series length, accumulators, counters, status); slot < 0 sets every chain c with chain
+// word chain + c.
+cudaError_t launch_slot_control(const Dev& d, int slot, uint32_t key0, uint32_t key1, uint32_t chain, uint32_t sweep,
+                                int active, int reset, cudaStream_t s);
 cudaError_t launch_log_weight(const Dev& d, double* out_logw, cudaStream_t s);
 cudaError_t launch_proposals(uint32_t key0, uint32_t key1, uint32_t chain, uint32_t sweep, uint32_t tag,
                              const uint32_t* events, int n, double* u1, double* u2, cudaStream_t s);

@@ -11,6 +11,8 @@
 //   sweep_end     per-sweep observable records
 #include <cstdio>
 #include <mutex>
+#include <utility>
+#include <vector>
 #include "hq_device.cuh"
 #include "hq_internal.h"
 #include "../../include/holstein_dqmc.h"
@@ -837,6 +839,32 @@ __global__ void __launch_bounds__(HQ_THREADS) measure_g0_kernel(Dev d) {
   measure_green(d, c, sm, d.G + (size_t)c * d.n * d.n);
 }
 
+// Slot control without host memory: a copy from pageable host memory can wait for kernels
+// running on other streams, so identity, activity and the per-slot reset are written by a
+// kernel from its arguments.  slot < 0: every chain c gets chain word first + c (creation).
+__global__ void slot_control_kernel(Dev d, int slot, uint32_t key0, uint32_t key1, uint32_t chain, uint32_t sweep,
+                                    int active, int reset) {
+  const int c = slot < 0 ? blockIdx.x : slot;
+  const uint32_t word = slot < 0 ? chain + (uint32_t)blockIdx.x : chain;
+  if (threadIdx.x == 0) {
+    d.active[c] = active;
+    if (reset) {
+      uint32_t* id = d.cid + 4 * (size_t)c;
+      id[0] = key0;
+      id[1] = key1;
+      id[2] = word;
+      id[3] = sweep;
+      d.slen[c] = 0;
+      d.status[c] = 0;
+      if (d.use_cm) d.cbuf[c] = 0;
+    }
+  }
+  if (!reset) return;
+  for (int o = threadIdx.x; o < kAccSlots; o += blockDim.x) d.acc[(size_t)c * kAccSlots + o] = 0.0;
+  for (int o = threadIdx.x; o < kTotSlots; o += blockDim.x) d.tot[(size_t)c * kTotSlots + o] = 0.0;
+  for (int o = threadIdx.x; o < kCounters; o += blockDim.x) d.counters[(size_t)c * kCounters + o] = 0;
+}
+
 __global__ void reset_acc_kernel(Dev d) {
   const int c = blockIdx.x;
   for (int o = threadIdx.x; o < kAccSlots; o += blockDim.x) d.acc[(size_t)c * kAccSlots + o] = 0.0;
@@ -882,10 +910,30 @@ static inline int lmax_of(int nx, int ny) {
   return m <= 2 ? 2 : m <= 4 ? 4 : m <= 8 ? 8 : 16;
 }
 
-// Dynamic shared memory above the default 48 KB needs an opt-in per kernel.
+// Dynamic shared memory above the default 48 KB needs an opt-in per kernel.  The opt-in is
+// set once per kernel and device, to the device maximum: engines of different shapes share
+// kernel instantiations and run concurrently on their own streams, and changing the
+// attribute between their launches would make a launch wait for the running ones.
+cudaError_t opt_in_smem(const void* kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, int>> done;
+  int dev = 0, cap = 0;
+  cudaError_t st = cudaGetDevice(&dev);
+  if (st == cudaSuccess) st = cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (st != cudaSuccess) return st;
+  if (bytes > (size_t)cap) return cudaErrorInvalidValue;
+  std::lock_guard<std::mutex> lock(mu);
+  for (const auto& kd : done)
+    if (kd.first == kernel && kd.second == dev) return cudaSuccess;
+  st = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  if (st == cudaSuccess) done.emplace_back(kernel, dev);
+  return st;
+}
+
 template <typename K>
 static inline void allow_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  opt_in_smem((const void*)kernel, bytes);
 }
 
 #define HQ_DISPATCH(KERNEL, d, stream, ...)                                                  \
@@ -985,10 +1033,12 @@ static cudaError_t launch_phase(const Dev& d, cudaStream_t s) {
   if (occ < 1) return cudaErrorInvalidConfiguration;
   // One wave at most.  A worker only waits for a task that an earlier, running worker has
   // taken, so progress never depends on a block that is not resident (other streams may hold
-  // SMs).  The steps of one chain are sequential, so at most C tasks run at once: more
-  // workers than chains would only wait, holding SMs that concurrent launches could use.
+  // SMs).  The steps of one chain are sequential, so at most one task per active chain runs
+  // at once: more workers than active chains would only wait, holding SMs that concurrent
+  // launches could use (idle slots' tasks are skipped by whichever worker takes them).
   int workers = sms * (occ < kWorkersPerSm ? occ : kWorkersPerSm);
-  if (workers > d.n_chains) workers = d.n_chains;
+  if (workers > d.n_active) workers = d.n_active;
+  if (workers < 1) workers = 1;
   st = cudaMemsetAsync(d.sched, 0, sizeof(int) * (kSchedHeader + d.n_chains), s);
   if (st != cudaSuccess) return st;
   global_phase_kernel<LMAX><<<workers, HQ_THREADS, sb, s>>>(d);
@@ -1011,6 +1061,12 @@ cudaError_t launch_measure_g0(const Dev& d, cudaStream_t s) {
 
 cudaError_t launch_sweep_end(const Dev& d, int measured, cudaStream_t s) {
   sweep_end_kernel<<<d.n_chains, HQ_THREADS, 0, s>>>(d, measured);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slot_control(const Dev& d, int slot, uint32_t key0, uint32_t key1, uint32_t chain, uint32_t sweep,
+                                int active, int reset, cudaStream_t s) {
+  slot_control_kernel<<<slot < 0 ? d.n_chains : 1, 32, 0, s>>>(d, slot, key0, key1, chain, sweep, active, reset);
   return cudaGetLastError();
 }
 

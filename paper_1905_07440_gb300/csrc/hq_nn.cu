@@ -545,10 +545,7 @@ __global__ void nn_set_kernel(NNState nn, const float* src) {
 }
 
 // ------------------------------------------------------------------------ launchers
-static inline cudaError_t smem_opt_in(const void* k, size_t bytes) {
-  if (bytes > 48 * 1024) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  return cudaSuccess;
-}
+static inline cudaError_t smem_opt_in(const void* k, size_t bytes) { return opt_in_smem(k, bytes); }
 
 cudaError_t nn_launch_eval(const Dev& d, const NNState& nn, const double* X, double* F, int write_cache,
                            cudaStream_t s) {

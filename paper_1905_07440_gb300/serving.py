@@ -9,6 +9,11 @@ all live pools stay inside the HBM budget, and empty pools are released.  Pools 
 concurrently on their streams, so their work overlaps on the device.  Because every chain
 carries its own key, chain word and sweep counter, a request's result is the same alone and
 in any mix.
+
+Each live pool needs a hardware work queue of its own: CUDA maps streams onto
+CUDA_DEVICE_MAX_CONNECTIONS queues (8 unless set before CUDA initialises), and streams that
+share a queue run their launches in submission order, so a pool's short launch would wait
+behind another pool's long block-move phase.  Set it to at least max_pools (32 at most).
 """
 import collections
 import dataclasses
@@ -48,6 +53,7 @@ class Pool:
         self.slots = [None] * slots
         self.left = [0] * slots
         self.busy = False
+        self.idle_since = None    # clock time at which the pool last became empty
 
     def free_slot(self):
         for k, r in enumerate(self.slots):
@@ -62,10 +68,13 @@ class Pool:
 class Server:
     """Admission, continuous batching and completion of requests on one GPU."""
 
-    def __init__(self, backend, hbm_budget, slots_per_pool=32, clock=time.perf_counter):
+    def __init__(self, backend, hbm_budget, slots_per_pool=32, keep_idle_s=2.0, max_pools=32,
+                 clock=time.perf_counter):
         self.backend = backend
         self.budget = hbm_budget
         self.slots_per_pool = slots_per_pool
+        self.max_pools = max_pools      # live pools (one CUDA stream each)
+        self.keep_idle_s = keep_idle_s  # empty pools stay (warm) this long unless memory is needed
         self.clock = clock
         self.queue = collections.deque()
         self.pools = []
@@ -78,10 +87,27 @@ class Server:
     def submit(self, req):
         self.queue.append(req)
 
+    def _release(self, pool):
+        self.backend.release(pool.engine)
+        self.pools.remove(pool)
+
+    def _fits(self, need):
+        return self.used + need <= self.budget and len(self.pools) < self.max_pools
+
+    def _make_room(self, need):
+        """Release empty pools, longest idle first, until a pool of `need` more bytes fits the
+        budget and the pool limit."""
+        for pool in sorted((p for p in self.pools if not p.active() and not p.busy), key=lambda p: p.idle_since):
+            if self._fits(need):
+                break
+            self._release(pool)
+        return self._fits(need)
+
     def _admit(self):
         """Place queued requests, in arrival order, at sweep boundaries: into an idle pool of the
         same key with a free slot; if every pool of that key is full, into a new pool when the
-        HBM budget allows one; otherwise (a matching pool is mid-sweep, or no room) they wait."""
+        HBM budget allows one (after releasing empty pools); otherwise (a matching pool is
+        mid-sweep, or no room) they wait."""
         waiting = collections.deque()
         while self.queue:
             req = self.queue.popleft()
@@ -90,7 +116,7 @@ class Server:
             pool = next((p for p in same if not p.busy), None)
             if pool is None and not same:
                 need = self.backend.engine_bytes(req.params, self.slots_per_pool, req.sampler)
-                if self.used + need <= self.budget:
+                if self._make_room(need):
                     pool = Pool(self.backend, req, self.slots_per_pool)
                     self.pools.append(pool)
             if pool is None:
@@ -100,6 +126,7 @@ class Server:
             self.backend.load(pool.engine, k, req)
             pool.slots[k] = req
             pool.left[k] = req.sweeps
+            pool.idle_since = None
             req.admitted = self.clock()
         self.queue = waiting
 
@@ -127,9 +154,14 @@ class Server:
                         self.backend.idle(pool.engine, k)
                         pool.slots[k] = None
                         self.finished.append(req)
+                    if not pool.active():
+                        pool.idle_since = now
+        now = self.clock()
         for pool in [p for p in self.pools if not p.active() and not p.busy]:
-            self.backend.release(pool.engine)
-            self.pools.remove(pool)
+            if pool.idle_since is None:
+                pool.idle_since = now
+            elif now - pool.idle_since > self.keep_idle_s:
+                self._release(pool)
 
     def poll(self):
         """One scheduling round: collect finished sweeps, admit, launch the next sweeps."""
@@ -138,7 +170,12 @@ class Server:
         self._launch()
 
     def pending(self):
-        return bool(self.queue) or any(p.active() for p in self.pools)
+        return bool(self.queue) or any(p.active() or p.busy for p in self.pools)
+
+    def close(self):
+        """Release every pool (call when no request is pending)."""
+        for pool in list(self.pools):
+            self._release(pool)
 
     def run(self, requests, sleep=1e-4):
         """Serve requests arriving at their `arrival` times (seconds from the start)."""
@@ -154,24 +191,43 @@ class Server:
             self.poll()
             if k < len(todo) and not self.pending():
                 time.sleep(min(sleep, max(0.0, todo[k].arrival - (self.clock() - t0))))
+        self.close()
         return self.finished
 
 
 class GpuBackend:
-    """Engines of the C ABI, one CUDA stream per pool."""
+    """Engines of the C ABI, each pool on a CUDA stream of its own."""
 
     def __init__(self, device=0, nn_batch=4):
         import torch
         import paper_1905_07440_gb300 as hq
         self.torch, self.hq, self.device = torch, hq, torch.device("cuda", device)
         self.nn_batch = nn_batch
+        self._free_streams = []
+        self._in_use = set()
+
+    def _stream(self):
+        """A stream no live pool uses.  PyTorch hands out streams round-robin from a small
+        pool, so a fresh one can be a stream a busy pool still holds; two pools on one stream
+        would run one after the other."""
+        st = self._free_streams.pop() if self._free_streams else None
+        for prio in (0, -1):
+            for _ in range(64 if st is None else 0):
+                cand = self.torch.cuda.Stream(device=self.device, priority=prio)
+                if cand.cuda_stream not in self._in_use:
+                    st = cand
+                    break
+        if st is None:
+            raise RuntimeError("no CUDA stream free for another pool")
+        self._in_use.add(st.cuda_stream)
+        return st
 
     def engine_bytes(self, params, slots, sampler):
         nb = self.hq.arena_bytes(params, slots, 0)
         return nb * (2 if sampler == "learned" else 1)
 
     def new_engine(self, params, slots, sampler, theta):
-        stream = self.torch.cuda.Stream(device=self.device)
+        stream = self._stream()
         eng = self.hq.Engine(params, slots, max_series=0, device=self.device, stream=stream)
         nbytes = eng.arena.numel()
         if sampler == "learned":
@@ -210,4 +266,7 @@ class GpuBackend:
         eng.set_active(slot, False)
 
     def release(self, eng):
+        st = eng.stream
         eng.close()
+        self._in_use.discard(st.cuda_stream)
+        self._free_streams.append(st)

@@ -68,6 +68,7 @@ def test_every_request_gets_exactly_its_sweeps():
         srv.submit(r)
     while srv.pending():
         srv.poll()
+    srv.close()
     assert len(srv.finished) == 20
     for r in srv.finished:
         assert r.obs["sweeps"] == r.sweeps
@@ -88,6 +89,36 @@ def test_budget_limits_live_pools_and_queues_the_rest():
         srv.poll()
         peak = max(peak, srv.used)
     assert peak <= 250 and len(srv.finished) == 6
+
+
+def test_empty_pools_stay_warm_then_release():
+    t = [0.0]
+    be = FakeBackend()
+    srv = Server(be, hbm_budget=1000, slots_per_pool=2, keep_idle_s=5.0, clock=lambda: t[0])
+    srv.submit(make(1, 4, 1))
+    while srv.pending():
+        srv.poll()
+    assert len(srv.pools) == 1 and be.released == 0      # empty but kept
+    t[0] = 1.0
+    srv.submit(make(2, 4, 1))                             # reuses the warm pool
+    while srv.pending():
+        srv.poll()
+    assert be.created == 1
+    t[0] = 10.0
+    srv.poll()
+    assert not srv.pools and be.released == 1             # idle past keep_idle_s
+
+
+def test_idle_pools_are_released_for_budget():
+    be = FakeBackend(bytes_per_engine=100)
+    srv = Server(be, hbm_budget=150, slots_per_pool=2, keep_idle_s=1e9)
+    srv.submit(make(1, 4, 1))
+    while srv.pending():
+        srv.poll()
+    srv.submit(make(2, 6, 1))                             # other shape: needs the idle pool's memory
+    while srv.pending():
+        srv.poll()
+    assert be.created == 2 and be.released == 1 and len(srv.finished) == 2
 
 
 def test_late_arrivals_join_a_running_pool():
