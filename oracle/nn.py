@@ -195,20 +195,32 @@ def loss_and_grad(p, theta, Xs, ys):
 class CumulativeChain:
     """The network-driven sampler with the exact cumulative accept (paper, NNMC section).
 
-    Inner moves are Metropolis moves on exp(-dtau S_ph + 2F) (exact phonon action, learned F);
-    after n_inner inner sweeps the proposal X -> X' is accepted with min(1, p_c),
-    p_c = exp(2 [log|det M(X')| - log|det M(X)|] - 2 [F(X') - F(X)]).  The smallest relative
-    distance |u - p| / p of any decision is kept in min_margin (for parity checks).
+    Inner moves are Metropolis moves, each on its own learned weight: local moves on
+    exp(-dtau S_ph + 2F) (patch network F), block moves on exp(-dtau S_ph + 2F_b) with F_b the
+    convolutional action when `cnn_theta` is given, else F as well.  After n_inner inner
+    sweeps the proposal X -> X' is accepted with min(1, p_c).
+
+    Reading of p_c: reversing the realised sequence of moves has probability ratio
+    prod over accepted moves of pi_j(before) / pi_j(after) (detailed balance of each move), so
+    p_c = [W(X')/W(X)] prod_j pi_j(before)/pi_j(after) = exp(2 dlog|det M| - 2 sum_acc dF_j):
+    the phonon action cancels and the accepted network changes enter as a path sum (for a
+    single network the sum is F(X') - F(X)).  The smallest relative distance |u - p| / p of
+    any decision is kept in min_margin (for parity checks).
     """
 
-    def __init__(self, p, X, theta, chain=0):
+    def __init__(self, p, X, theta, chain=0, cnn_theta=None):
         self.p = p
         self.X = np.array(X, dtype=np.float64, copy=True)
         self.chain = int(chain)
         self.act = EffectiveAction(p, theta)
+        self.cnn = None
+        if cnn_theta is not None:
+            from .cnn import CnnAction
+            self.cnn = CnnAction(p, cnn_theta)
         self.expK, _ = dqmc.kinetic_propagators(p)
         self.logdet = dqmc.log_det_M(p, self.expK, self.X)
         self.min_margin = math.inf
+        self.dF_path = 0.0
 
     def _decide(self, u, prob):
         self.min_margin = min(self.min_margin, abs(u - prob) / max(prob, 1e-300))
@@ -222,7 +234,8 @@ class CumulativeChain:
         p, X = self.p, self.X
         L, N = X.shape
         X0 = X.copy()
-        ld0, F0 = self.logdet, self.act.F(X0)
+        ld0 = self.logdet
+        path = 0.0
         uc, ud = proposal_uniforms(p.seed, self.chain, k, [0], TAG_CUMULATIVE)
         fwd = bool(ud[0] < 0.5)
         order = (lambda m: range(m)) if fwd else (lambda m: range(m - 1, -1, -1))
@@ -239,16 +252,19 @@ class CumulativeChain:
                             dF = self.act.delta_local(X, s, i, xn)
                             if self._decide(u2[i], math.exp(min(2.0 * dF - dS, 709.0))):
                                 X[s, i] = xn
+                                path += dF
                 if part == "block" and block:
                     u1, u2 = proposal_uniforms(p.seed, self.chain, isw, np.arange(N), TAG_NN_BLOCK)
                     for i in order(N):
                         dx = p.dx_global * (2.0 * u1[i] - 1.0)
                         dS = dqmc.global_action_change(p, X, i, dx)
-                        dF = self.act.delta_block(X, i, dx)
+                        dF = self.cnn.delta_block(X, i, dx) if self.cnn is not None else self.act.delta_block(X, i, dx)
                         if self._decide(u2[i], math.exp(min(2.0 * dF - dS, 709.0))):
                             X[:, i] += dx
-        ld1, F1 = dqmc.log_det_M(p, self.expK, X), self.act.F(X)
-        pc = math.exp(min(2.0 * (ld1 - ld0) - 2.0 * (F1 - F0), 709.0))
+                            path += dF
+        ld1 = dqmc.log_det_M(p, self.expK, X)
+        self.dF_path = path
+        pc = math.exp(min(2.0 * (ld1 - ld0) - 2.0 * path, 709.0))
         accepted = self._decide(float(uc[0]), pc)
         if accepted:
             self.logdet = ld1
