@@ -225,8 +225,12 @@ int hq_logdet_noalloc(const hq_params* p, int n_chains, const double* X_device, 
  * so the chain samples the exact weight.  Here E_NN is the scalar
  *   F(X) = sum_{i,l} f(patch_{i,l}(X)),  patch = X on the 5-site cross x 5 slices around
  *   (i, l) minus the mean field -g/(M Omega^2),  f: 25 -> 64 -> 64 -> 1, ReLU, linear out,
- * with bfloat16 weights and FP32 arithmetic; the inner chain samples exp(-dtau S_ph + 2F)
- * with the exact phonon action and p_c = exp(2 [log|det M(X')| - log|det M(X)|] - 2 [F(X') - F(X)]).
+ * with bfloat16 weights and FP32 arithmetic.  Local moves are Metropolis moves on
+ * exp(-dtau S_ph + 2F) with the exact phonon action; block moves on the same weight, or
+ * (HQ_CNN_BLOCK) with the convolutional action F_cnn below in place of F.  Every move is
+ * reversible for its own weight, so the cumulative accept is
+ *   p_c = exp(2 [log|det M(X')| - log|det M(X)|] - 2 sum over accepted inner moves of dF)
+ * (the phonon action cancels; with one network the sum is F(X') - F(X)).
  * Parameters are a flat float vector: W1[25][64] (input k, unit u at k*64+u), b1[64],
  * W2[64][64] (v*64+u), b2[64], W3[64], b3.  Inputs are ordered (slice offset -2..2) x
  * (cross site: centre, +x, -x, +y, -y).  Requires nx, ny >= 4 and L >= 5.
@@ -266,11 +270,44 @@ int hq_nn_train(hq_engine* e, const double* X_device, const double* y_device, in
 int hq_nn_gradient(hq_engine* e, const double* X_device, const double* y_device, int n_samples, float* grad_host,
                    double* loss_host);
 /* n_steps cumulative steps of every chain: n_inner network-driven sweeps (flags HQ_LOCAL:
- * a local move at every (l, i); HQ_GLOBAL: a block move at every site), then the exact
- * accept of the cumulative move; HQ_MEASURE also records electronic observables after each
- * step (one more stabilised G per step).  Asynchronous. */
+ * a local move at every (l, i); HQ_GLOBAL: a block move at every site, with HQ_CNN_BLOCK on
+ * F_cnn), then the exact accept of the cumulative move; HQ_MEASURE also records electronic
+ * observables after each step (one more stabilised G per step).  Asynchronous.
+ * Errors: HQ_EINVAL for bad arguments, HQ_CNN_BLOCK without convolutional parameters, or no
+ * attached network state. */
 int hq_cumulative_sweep(hq_engine* e, int n_steps, int n_inner, unsigned flags);
 int hq_get_learned_stats(hq_engine* e, hq_learned_stats* out);
+
+/* ------------------------------------------------------------------------------------
+ * Convolutional action for block moves (paper, "Global Updates": a convolutional network on
+ * the whole field predicts the weight, so a move of a whole imaginary-time column is cheap
+ * to estimate).  F_cnn(X) = sum over the (x, y, tau) torus of three 3x3x3 cross-correlations
+ * with periodic padding, 1 -> 16 -> 16 -> 1 channels, ReLU after the first two, on
+ * z = X + g/(M Omega^2); tap t = 9 (dl + 1) + 3 (dy + 1) + (dx + 1) reads (l + dl, y + dy,
+ * x + dx).  Parameters, one flat float vector: W1[27][16] (tap, out), b1[16],
+ * W2[27][16][16] (tap, in, out), b2[16], W3[27][16] (tap, in), b3; bfloat16 weights, FP32
+ * arithmetic.  Its state lives in the hq_nn_attach arena (activations of every chain's
+ * current fields, 33 floats per point).  A block move's change of F_cnn is computed from the
+ * cached activations in the window of lattice distance <= 3 around the moved site.
+ * ------------------------------------------------------------------------------------ */
+#define HQ_CNN_PARAMS 7809
+#define HQ_CNN_BLOCK 8u   /* hq_cumulative_sweep flag: block moves use F_cnn */
+
+/* Set the convolutional parameters from HQ_CNN_PARAMS host floats (bfloat16 for use, FP32
+ * master copy kept, optimiser state reset); enables HQ_CNN_BLOCK.  Synchronises.
+ * Errors: HQ_EINVAL without an attached network state or with a null pointer. */
+int hq_cnn_set_params(hq_engine* e, const float* theta_host);
+/* FP32 master parameters, or with bf16 != 0 the bfloat16 values the kernels use. */
+int hq_cnn_get_params(hq_engine* e, float* theta_host, int bf16);
+/* F_cnn of every chain's current fields (host, n_chains doubles); refreshes the cached
+ * activations.  Synchronises. */
+int hq_cnn_eval(hq_engine* e, double* F_host);
+/* Training and gradient of F_cnn, with the arguments and semantics of hq_nn_train and
+ * hq_nn_gradient (targets y, minibatch loss (1/B) sum (F_cnn(X_a) - y_a)^2, Adam). */
+int hq_cnn_train(hq_engine* e, const double* X_device, const double* y_device, int n_samples, int epochs,
+                 int batch, float lr, uint64_t seed, double* loss_host);
+int hq_cnn_gradient(hq_engine* e, const double* X_device, const double* y_device, int n_samples, float* grad_host,
+                    double* loss_host);
 
 /* Per-section device cycle counters (profiling builds compiled with -DHQ_SECTION_TIMING):
  * copies up to n counters (sum over CTAs of thread 0's clock64 spans; ids in

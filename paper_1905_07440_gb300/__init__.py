@@ -61,6 +61,8 @@ class hq_learned_stats(ctypes.Structure):
 
 
 HQ_NN_PARAMS = 5889
+HQ_CNN_PARAMS = 7809
+HQ_CNN_BLOCK = 8
 
 _P = ctypes.POINTER
 _dp = _P(ctypes.c_double)
@@ -100,6 +102,12 @@ _SIGNATURES = {
                                    ctypes.c_uint64, _dp]),
     "hq_nn_gradient": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _P(ctypes.c_float), _dp]),
     "hq_cumulative_sweep": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint]),
+    "hq_cnn_set_params": (ctypes.c_int, [_vp, _P(ctypes.c_float)]),
+    "hq_cnn_get_params": (ctypes.c_int, [_vp, _P(ctypes.c_float), ctypes.c_int]),
+    "hq_cnn_eval": (ctypes.c_int, [_vp, _dp]),
+    "hq_cnn_train": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                    ctypes.c_uint64, _dp]),
+    "hq_cnn_gradient": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _P(ctypes.c_float), _dp]),
     "hq_get_learned_stats": (ctypes.c_int, [_vp, _P(hq_learned_stats)]),
     "hq_get_section_cycles": (ctypes.c_int, [_P(ctypes.c_uint64), ctypes.c_int]),
     "hq_get_timing": (ctypes.c_int, [_vp, _dp, _P(ctypes.c_int64)]),
@@ -321,9 +329,44 @@ class Engine:
                                          _dptr(losses)), "hq_nn_train")
         return losses[: int(epochs)]
 
-    def cumulative(self, n_steps=1, n_inner=1, local=True, global_=True, measure=False):
-        flags = (HQ_LOCAL if local else 0) | (HQ_GLOBAL if global_ else 0) | (HQ_MEASURE if measure else 0)
+    def cumulative(self, n_steps=1, n_inner=1, local=True, global_=True, measure=False, cnn=False):
+        """Cumulative steps; cnn=True drives block moves by the convolutional action."""
+        flags = ((HQ_LOCAL if local else 0) | (HQ_GLOBAL if global_ else 0) | (HQ_MEASURE if measure else 0)
+                 | (HQ_CNN_BLOCK if cnn else 0))
         self._check(self.lib.hq_cumulative_sweep(self._h, int(n_steps), int(n_inner), flags), "hq_cumulative_sweep")
+
+    # convolutional action (block moves)
+    def cnn_set_params(self, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        assert t.size == HQ_CNN_PARAMS
+        self._check(self.lib.hq_cnn_set_params(self._h, t.ctypes.data_as(_P(ctypes.c_float))), "hq_cnn_set_params")
+
+    def cnn_get_params(self, bf16=False):
+        t = np.empty(HQ_CNN_PARAMS, dtype=np.float32)
+        self._check(self.lib.hq_cnn_get_params(self._h, t.ctypes.data_as(_P(ctypes.c_float)), 1 if bf16 else 0),
+                    "hq_cnn_get_params")
+        return t
+
+    def cnn_eval(self):
+        F = np.empty(self.n_chains)
+        self._check(self.lib.hq_cnn_eval(self._h, _dptr(F)), "hq_cnn_eval")
+        return F
+
+    def cnn_gradient(self, X, y):
+        """X: CUDA float64 [n][L][N], y: CUDA float64 [n]; returns (grad, loss)."""
+        g = np.empty(HQ_CNN_PARAMS, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(self.lib.hq_cnn_gradient(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                             int(X.shape[0]), g.ctypes.data_as(_P(ctypes.c_float)),
+                                             ctypes.byref(loss)), "hq_cnn_gradient")
+        return g, loss.value
+
+    def cnn_train(self, X, y, epochs, batch, lr, seed=1):
+        losses = np.empty(max(int(epochs), 1))
+        self._check(self.lib.hq_cnn_train(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                          int(X.shape[0]), int(epochs), int(batch), float(lr), int(seed),
+                                          _dptr(losses)), "hq_cnn_train")
+        return losses[: int(epochs)]
 
     def learned_stats(self):
         arr = (hq_learned_stats * self.n_chains)()
@@ -379,6 +422,19 @@ def init_network(seed, out_scale=1.0):
     w3 = rng.standard_normal(64) * 0.01 * out_scale
     out = np.concatenate([w1.ravel(), np.zeros(64), w2.ravel(), np.zeros(64), w3, [0.0]]).astype(np.float32)
     assert out.size == HQ_NN_PARAMS
+    return out
+
+
+def init_cnn(seed, out_scale=1.0):
+    """Seeded He initialisation of the convolutional action in the flat layout of
+    hq_cnn_set_params: W1[27][16], b1[16], W2[27][16][16], b2[16], W3[27][16], b3 (biases
+    zero, the last layer 0.01 N(0,1) scaled by out_scale)."""
+    rng = np.random.default_rng(seed)
+    w1 = rng.standard_normal((27, 16)) * math.sqrt(2.0 / 27)
+    w2 = rng.standard_normal((27, 16, 16)) * math.sqrt(2.0 / (27 * 16))
+    w3 = rng.standard_normal((27, 16)) * 0.01 * out_scale
+    out = np.concatenate([w1.ravel(), np.zeros(16), w2.ravel(), np.zeros(16), w3.ravel(), [0.0]]).astype(np.float32)
+    assert out.size == HQ_CNN_PARAMS
     return out
 
 

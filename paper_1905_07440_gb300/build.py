@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libholstein_dqmc.so")
-SOURCES = ["hq_kernels.cu", "hq_nn.cu", "hq_engine.cu"]
+SOURCES = ["hq_kernels.cu", "hq_nn.cu", "hq_cnn.cu", "hq_engine.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include")]

@@ -79,6 +79,15 @@ __device__ __forceinline__ double block_max(double v, double* red) {
   return s;
 }
 
+// ---------------------------------------------------------------- bfloat16
+__device__ __forceinline__ float bf16_to_float(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+
+// round to nearest even (finite inputs)
+__device__ __forceinline__ uint16_t float_to_bf16(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+
 // ---------------------------------------------------------------- Philox4x32-10
 // Salmon, Moraes, Dror, Shaw (SC'11): ten rounds of two 32x32->64 multiplies with the
 // round constants, key bumped by the Weyl constants between rounds.

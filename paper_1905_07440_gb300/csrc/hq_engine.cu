@@ -40,7 +40,9 @@ struct hq_engine {
   // learned effective action (optional)
   bool nn_on = false;
   hq::NNState nn{};
+  hq::CnnState cn{};
   int nn_max_batch = 0, nn_max_samples = 0;
+  int cn_t_step = 0;
   long long cum_steps = 0;
   int nn_t_step = 0;
   ~hq_engine() {
@@ -732,8 +734,13 @@ namespace {
 
 constexpr int kNNParamsPad = (HQ_NN_PARAMS + 3) & ~3;
 
+constexpr int kCnnParamsPad = (HQ_CNN_PARAMS + 3) & ~3;
+
 struct NNLayout {
-  size_t wbf, master, grad, am, av, partials, fcache, fnew, X0, ld0, F0, F1, pc, Fb, loss, idx, counters, total;
+  size_t wbf, master, grad, am, av, partials, fcache, fnew, X0, ld0, F0, F1, pc, Fb, loss, idx, counters, dFpath;
+  size_t cwbf, cmaster, cgrad, cam, cav, cpartials, h1c, h2c, o3c, h1p, h2p, o3p, tr, cFb, cF;
+  int train_ctas;
+  size_t total;
 };
 
 NNLayout nn_layout(const hq::Dev& d, int max_batch, int max_samples) {
@@ -758,6 +765,25 @@ NNLayout nn_layout(const hq::Dev& d, int max_batch, int max_samples) {
   l.loss = take(8);
   l.idx = take(4 * (size_t)max_samples);
   l.counters = take(8 * C * hq::kNNCounters);
+  l.dFpath = take(8 * C);
+  // convolutional action
+  const size_t PC = kCnnParamsPad, CH = hq::kCnnC;
+  l.train_ctas = max_batch < hq::kCnnTrainCtas ? max_batch : hq::kCnnTrainCtas;
+  l.cwbf = take(2 * PC);
+  l.cmaster = take(4 * PC);
+  l.cgrad = take(4 * PC);
+  l.cam = take(4 * PC);
+  l.cav = take(4 * PC);
+  l.cpartials = take(4 * PC * l.train_ctas);
+  l.h1c = take(4 * C * NL * CH);
+  l.h2c = take(4 * C * NL * CH);
+  l.o3c = take(4 * C * NL);
+  l.h1p = take(4 * C * 9 * d.L * CH);
+  l.h2p = take(4 * C * 25 * d.L * CH);
+  l.o3p = take(4 * C * 49 * d.L);
+  l.tr = take(4 * (size_t)l.train_ctas * 3 * NL * CH);
+  l.cFb = take(8 * (size_t)max_batch);
+  l.cF = take(8 * C);
   l.total = off;
   return l;
 }
@@ -808,7 +834,27 @@ int hq_nn_attach(hq_engine* e, void* arena, size_t bytes, int max_batch, int max
   nn.loss = (double*)(a + l.loss);
   nn.idx = (int*)(a + l.idx);
   nn.counters = (long long*)(a + l.counters);
+  nn.dFpath = (double*)(a + l.dFpath);
   nn.x0 = -e->p.g / (e->p.mass * e->p.omega * e->p.omega);
+  hq::CnnState& cn = e->cn;
+  cn.on = 0;
+  cn.wbf = (uint16_t*)(a + l.cwbf);
+  cn.master = (float*)(a + l.cmaster);
+  cn.grad = (float*)(a + l.cgrad);
+  cn.adam_m = (float*)(a + l.cam);
+  cn.adam_v = (float*)(a + l.cav);
+  cn.partials = (float*)(a + l.cpartials);
+  cn.train_ctas = l.train_ctas;
+  cn.h1c = (float*)(a + l.h1c);
+  cn.h2c = (float*)(a + l.h2c);
+  cn.o3c = (float*)(a + l.o3c);
+  cn.h1p = (float*)(a + l.h1p);
+  cn.h2p = (float*)(a + l.h2p);
+  cn.o3p = (float*)(a + l.o3p);
+  cn.tr = (float*)(a + l.tr);
+  cn.Fb = (double*)(a + l.cFb);
+  cn.F = (double*)(a + l.cF);
+  e->cn_t_step = 0;
   int rc = cuda_check(e, cudaMemsetAsync(a, 0, l.total, e->stream), "nn arena clear");
   if (rc) return rc;
   e->nn_on = true;
@@ -924,7 +970,9 @@ int hq_nn_train(hq_engine* e, const double* X_device, const double* y_device, in
 int hq_cumulative_sweep(hq_engine* e, int n_steps, int n_inner, unsigned flags) {
   int rc = nn_ready(e);
   if (rc) return rc;
-  if (n_steps < 0 || n_inner < 1 || (flags & ~(HQ_LOCAL | HQ_GLOBAL | HQ_MEASURE))) return HQ_EINVAL;
+  if (n_steps < 0 || n_inner < 1 || (flags & ~(HQ_LOCAL | HQ_GLOBAL | HQ_MEASURE | HQ_CNN_BLOCK))) return HQ_EINVAL;
+  const int use_cnn = (flags & HQ_CNN_BLOCK) ? 1 : 0;
+  if (use_cnn && !e->cn.on) return set_err(e, HQ_EINVAL, "HQ_CNN_BLOCK needs convolutional parameters (hq_cnn_set_params)");
   const hq::Dev& d = e->d;
   const size_t fbytes = sizeof(double) * (size_t)d.n_chains * d.L * d.n;
   for (int k = 0; k < n_steps; ++k) {
@@ -935,10 +983,11 @@ int hq_cumulative_sweep(hq_engine* e, int n_steps, int n_inner, unsigned flags) 
     rc = cuda_check(e, cudaMemcpyAsync(e->nn.X0, d.X, fbytes, cudaMemcpyDeviceToDevice, e->stream), "X0 copy");
     rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(e->nn.ld0, d.logdet, sizeof(double) * d.n_chains,
                                                  cudaMemcpyDeviceToDevice, e->stream), "ld0 copy");
+    // caches of the current fields (the previous step may have restored X)
     rc = rc ? rc : cuda_check(e, hq::nn_launch_eval(d, e->nn, d.X, e->nn.F0, 1, e->stream), "nn eval F0");
-    rc = rc ? rc : cuda_check(e, hq::nn_launch_inner(d, e->nn, n_inner, (flags & HQ_LOCAL) ? 1 : 0,
-                                                     (flags & HQ_GLOBAL) ? 1 : 0, e->stream), "nn inner");
-    rc = rc ? rc : cuda_check(e, hq::nn_launch_eval(d, e->nn, d.X, e->nn.F1, 0, e->stream), "nn eval F1");
+    if (use_cnn) rc = rc ? rc : cuda_check(e, hq::cnn_launch_eval(d, e->cn, d.X, e->cn.F, 1, e->stream), "cnn eval");
+    rc = rc ? rc : cuda_check(e, hq::nn_launch_inner(d, e->nn, e->cn, n_inner, (flags & HQ_LOCAL) ? 1 : 0,
+                                                     (flags & HQ_GLOBAL) ? 1 : 0, use_cnn, e->stream), "nn inner");
     e->stack_valid = false;
     rc = rc ? rc : ensure_state(e);  // log|det M(X')| (and G, stack of X')
     rc = rc ? rc : cuda_check(e, hq::nn_launch_decide(d, e->nn, e->stream), "nn decide");
@@ -956,6 +1005,116 @@ int hq_cumulative_sweep(hq_engine* e, int n_steps, int n_inner, unsigned flags) 
     e->cum_steps++;
   }
   return HQ_OK;
+}
+
+int hq_cnn_set_params(hq_engine* e, const float* theta_host) {
+  int rc = nn_ready(e);
+  if (rc) return rc;
+  if (!theta_host) return HQ_EINVAL;
+  rc = cuda_check(e, cudaMemcpyAsync(e->cn.partials, theta_host, sizeof(float) * HQ_CNN_PARAMS,
+                                     cudaMemcpyHostToDevice, e->stream), "cnn params upload");
+  rc = rc ? rc : cuda_check(e, hq::cnn_launch_set(e->cn, e->cn.partials, e->stream), "cnn set");
+  rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "cnn set sync");
+  if (!rc) e->cn.on = 1;
+  e->cn_t_step = 0;
+  return rc;
+}
+
+int hq_cnn_get_params(hq_engine* e, float* theta_host, int bf16) {
+  int rc = nn_ready(e);
+  if (rc) return rc;
+  if (!theta_host) return HQ_EINVAL;
+  if (bf16) {
+    std::vector<uint16_t> h(HQ_CNN_PARAMS);
+    rc = cuda_check(e, cudaMemcpyAsync(h.data(), e->cn.wbf, 2 * HQ_CNN_PARAMS, cudaMemcpyDeviceToHost, e->stream),
+                    "cnn params copy");
+    rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "cnn params sync");
+    if (rc) return rc;
+    for (int k = 0; k < HQ_CNN_PARAMS; ++k) {
+      const uint32_t u = (uint32_t)h[k] << 16;
+      std::memcpy(&theta_host[k], &u, 4);
+    }
+    return HQ_OK;
+  }
+  rc = cuda_check(e, cudaMemcpyAsync(theta_host, e->cn.master, 4 * HQ_CNN_PARAMS, cudaMemcpyDeviceToHost,
+                                     e->stream), "cnn params copy");
+  return rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "cnn params sync");
+}
+
+int hq_cnn_eval(hq_engine* e, double* F_host) {
+  int rc = nn_ready(e);
+  if (rc) return rc;
+  if (!F_host) return HQ_EINVAL;
+  if (!e->cn.on) return set_err(e, HQ_EINVAL, "no convolutional parameters (hq_cnn_set_params)");
+  rc = cuda_check(e, hq::cnn_launch_eval(e->d, e->cn, e->d.X, e->cn.F, 1, e->stream), "cnn eval");
+  rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(F_host, e->cn.F, sizeof(double) * e->d.n_chains,
+                                               cudaMemcpyDeviceToHost, e->stream), "cnn eval copy");
+  return rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "cnn eval sync");
+}
+
+int hq_cnn_gradient(hq_engine* e, const double* X_device, const double* y_device, int n_samples, float* grad_host,
+                    double* loss_host) {
+  int rc = nn_ready(e);
+  if (rc) return rc;
+  if (!X_device || !y_device || n_samples < 1 || n_samples > e->nn_max_batch) return HQ_EINVAL;
+  if (!e->cn.on) return set_err(e, HQ_EINVAL, "no convolutional parameters (hq_cnn_set_params)");
+  std::vector<int> idx(n_samples);
+  for (int a = 0; a < n_samples; ++a) idx[a] = a;
+  rc = cuda_check(e, cudaMemcpyAsync(e->nn.idx, idx.data(), sizeof(int) * n_samples, cudaMemcpyHostToDevice,
+                                     e->stream), "cnn idx");
+  rc = rc ? rc : cuda_check(e, cudaMemsetAsync(e->nn.loss, 0, sizeof(double), e->stream), "cnn loss clear");
+  rc = rc ? rc : cuda_check(e, hq::cnn_launch_batch(e->d, e->cn, X_device, y_device, e->nn.idx, n_samples, 0.f, 1,
+                                                     e->stream), "cnn batch");
+  rc = rc ? rc : cuda_check(e, hq::cnn_launch_loss(e->cn, y_device, e->nn.idx, n_samples, 1.0 / n_samples,
+                                                    e->nn.loss, e->stream), "cnn loss");
+  if (!rc && grad_host)
+    rc = cuda_check(e, cudaMemcpyAsync(grad_host, e->cn.grad, 4 * HQ_CNN_PARAMS, cudaMemcpyDeviceToHost, e->stream),
+                    "cnn grad copy");
+  if (!rc && loss_host)
+    rc = cuda_check(e, cudaMemcpyAsync(loss_host, e->nn.loss, sizeof(double), cudaMemcpyDeviceToHost, e->stream),
+                    "cnn loss copy");
+  return rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "cnn grad sync");
+}
+
+int hq_cnn_train(hq_engine* e, const double* X_device, const double* y_device, int n_samples, int epochs, int batch,
+                 float lr, uint64_t seed, double* loss_host) {
+  int rc = nn_ready(e);
+  if (rc) return rc;
+  if (!X_device || !y_device || n_samples < 1 || n_samples > e->nn_max_samples || epochs < 0 || batch < 1 ||
+      batch > e->nn_max_batch || !(lr > 0.f))
+    return HQ_EINVAL;
+  if (!e->cn.on) return set_err(e, HQ_EINVAL, "no convolutional parameters (hq_cnn_set_params)");
+  std::vector<int> order(n_samples);
+  uint64_t st = seed;
+  for (int ep = 0; ep < epochs; ++ep) {
+    for (int a = 0; a < n_samples; ++a) order[a] = a;
+    for (int a = n_samples - 1; a > 0; --a) {  // Fisher-Yates with splitmix64
+      const int b = (int)(splitmix64(st) % (uint64_t)(a + 1));
+      std::swap(order[a], order[b]);
+    }
+    rc = cuda_check(e, cudaMemcpyAsync(e->nn.idx, order.data(), sizeof(int) * n_samples, cudaMemcpyHostToDevice,
+                                       e->stream), "cnn order");
+    rc = rc ? rc : cuda_check(e, cudaMemsetAsync(e->nn.loss, 0, sizeof(double), e->stream), "cnn loss clear");
+    if (rc) return rc;
+    for (int a0 = 0; a0 + batch <= n_samples; a0 += batch) {
+      rc = cuda_check(e, hq::cnn_launch_batch(e->d, e->cn, X_device, y_device, e->nn.idx + a0, batch, lr,
+                                              ++e->cn_t_step, e->stream), "cnn batch");
+      rc = rc ? rc : cuda_check(e, hq::cnn_launch_loss(e->cn, y_device, e->nn.idx + a0, batch,
+                                                       1.0 / (double)(n_samples / batch * batch), e->nn.loss,
+                                                       e->stream), "cnn loss");
+      if (rc) return rc;
+    }
+    // the host order vector is reused by the next epoch: its copy must have completed
+    rc = cuda_check(e, cudaStreamSynchronize(e->stream), "cnn epoch sync");
+    if (rc) return rc;
+    if (loss_host) {
+      rc = cuda_check(e, cudaMemcpyAsync(&loss_host[ep], e->nn.loss, sizeof(double), cudaMemcpyDeviceToHost,
+                                         e->stream), "cnn loss copy");
+      rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "cnn epoch sync");
+      if (rc) return rc;
+    }
+  }
+  return cuda_check(e, cudaStreamSynchronize(e->stream), "cnn train sync");
 }
 
 int hq_get_learned_stats(hq_engine* e, hq_learned_stats* out) {

@@ -98,7 +98,34 @@ struct NNState {
   double* loss;         // [1] epoch loss accumulator
   int* idx;             // [max samples] minibatch order
   long long* counters;  // [C][kNNCounters]
+  double* dFpath;       // [C] sum of the accepted inner moves' network changes (cumulative step)
   double x0;            // input shift -g/(M Omega^2)
+};
+
+// Periodic 3D convolutional action for block moves: three 3x3x3 layers 1 -> 16 -> 16 -> 1
+// on the (x, y, tau) torus, summed over every point.  Activations are stored after the ReLU,
+// 16 floats per point (point-major).  Window buffers hold the block-move proposal around the
+// moved site: radius 1 (layer 1), 2 (layer 2), 3 (layer 3) in the lattice, every slice.
+constexpr int kCnnC = 16;
+constexpr int kCnnTrainCtas = 152;
+struct CnnState {
+  int on;               // parameters have been set
+  uint16_t* wbf;        // bfloat16 weights used by every kernel
+  float* master;        // FP32 master weights (training)
+  float* grad;
+  float* adam_m;
+  float* adam_v;
+  float* partials;      // [train_ctas][padded params]
+  int train_ctas;
+  float* h1c;           // [C][L N][16] layer-1 activations of the current fields
+  float* h2c;           // [C][L N][16]
+  float* o3c;           // [C][L N] layer-3 outputs
+  float* h1p;           // [C][9 L][16] proposal, window radius 1
+  float* h2p;           // [C][25 L][16] radius 2
+  float* o3p;           // [C][49 L] radius 3
+  float* tr;            // [train_ctas][3][L N][16] training activations and gradients
+  double* Fb;           // [max batch] minibatch F
+  double* F;            // [C]
 };
 
 size_t smem_bytes(const Dev& d);
@@ -125,13 +152,21 @@ double fp64_probe_tflops(int kind, int reps, cudaStream_t s);
 cudaError_t launch_measure_g0(const Dev& d, cudaStream_t s);
 cudaError_t nn_launch_eval(const Dev& d, const NNState& nn, const double* X, double* F, int write_cache,
                            cudaStream_t s);
-cudaError_t nn_launch_inner(const Dev& d, const NNState& nn, int n_inner, int do_local,
-                            int do_block, cudaStream_t s);
+
 cudaError_t nn_launch_decide(const Dev& d, const NNState& nn, cudaStream_t s);
 cudaError_t nn_launch_set(const NNState& nn, const float* src_device, cudaStream_t s);
 cudaError_t nn_launch_batch(const Dev& d, const NNState& nn, const double* Xs, const double* ys, const int* idx,
                             int B, float lr, int t_step, cudaStream_t s);
 cudaError_t nn_launch_loss(const NNState& nn, const double* ys, const int* idx, int B, double scale, cudaStream_t s);
+cudaError_t nn_launch_inner(const Dev& d, const NNState& nn, const CnnState& cn, int n_inner, int do_local,
+                            int do_block, int use_cnn, cudaStream_t s);
+cudaError_t cnn_launch_eval(const Dev& d, const CnnState& cn, const double* X, double* F, int write_cache,
+                            cudaStream_t s);
+cudaError_t cnn_launch_set(const CnnState& cn, const float* src_device, cudaStream_t s);
+cudaError_t cnn_launch_batch(const Dev& d, const CnnState& cn, const double* Xs, const double* ys, const int* idx,
+                             int B, float lr, int t_step, cudaStream_t s);
+cudaError_t cnn_launch_loss(const CnnState& cn, const double* ys, const int* idx, int B, double scale,
+                            double* loss, cudaStream_t s);
 int section_cycles(unsigned long long* out, int n);
 size_t noalloc_scratch_needed(int nx, int ny, int n_chains);
 // log|det M| per chain with all scratch in the library's static device array (no allocation).

@@ -7,11 +7,15 @@
 //
 // Here E_NN is one scalar function: F(X) = sum_{i,l} f(patch_{i,l}(X)), patch = X on the
 // 5-site cross x 5 slices around (i, l) minus the mean field -g/(M Omega^2), f a 25-64-64-1
-// ReLU network with bfloat16 weights and FP32 arithmetic.  The inner chain samples
-// exp(-dtau S_ph + 2F) (exact phonon action), and p_c = exp(2 dlog|det M| - 2 dF).
+// ReLU network with bfloat16 weights and FP32 arithmetic.  Local moves are Metropolis moves on
+// exp(-dtau S_ph + 2F) (exact phonon action); block moves on the same weight, or with the
+// periodic convolutional action F_cnn in place of F (hq_cnn.cuh).  Each move is reversible for
+// its own weight, so p_c = exp(2 dlog|det M| - 2 sum of the accepted moves' network changes)
+// (the phonon action cancels; for one network the sum telescopes to F(X') - F(X)).
 // Every kernel evaluates f through nn_patch_eval (one 8-lane group per patch, fixed order),
 // so the inner chain and the acceptance see bit-identical values of f.
 #include <cstdio>
+#include "hq_cnn.cuh"
 #include "hq_device.cuh"
 #include "hq_internal.h"
 #include "../../include/holstein_dqmc.h"
@@ -26,13 +30,6 @@ static_assert(NN_NP == HQ_NN_PARAMS, "parameter count");
 constexpr int NN_WPAD = (NN_NP + 3) & ~3;
 constexpr int NN_GROUPS = HQ_THREADS / 8;
 
-__device__ __forceinline__ float bf16_to_float(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
-
-// round to nearest even (finite inputs)
-__device__ __forceinline__ uint16_t float_to_bf16(float f) {
-  const uint32_t u = __float_as_uint(f);
-  return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
-}
 
 __device__ inline void load_weights(const uint16_t* wb, float* w) {
   for (int k = threadIdx.x; k < NN_WPAD; k += HQ_THREADS) w[k] = (k < NN_NP) ? bf16_to_float(wb[k]) : 0.f;
@@ -108,27 +105,65 @@ struct NNSmem {
   double* pds;   // [n] dtau dS_ph
   double* gacc;  // [NN_GROUPS] per-group sums
   double* scal;  // [8]
+  float* cw;     // [CN_WPAD] convolutional weights (with_cnn)
+  CnWindow win;  // block-move window (with_cnn)
 };
 
-__host__ __device__ inline size_t nn_smem_bytes(int n) {
-  return sizeof(float) * (NN_WPAD + NN_GROUPS * (NN_IN + 3) + NN_GROUPS * NN_H) +
-         sizeof(double) * (HQ_WARPS + 3 * (size_t)n + NN_GROUPS + 8);
+__host__ __device__ inline size_t nn_smem_bytes(int n, bool with_cnn = false) {
+  size_t b = sizeof(double) * (HQ_WARPS + 3 * (size_t)n + NN_GROUPS + 8) +
+             sizeof(float) * (NN_WPAD + NN_GROUPS * (NN_IN + 3) + NN_GROUPS * NN_H);
+  if (with_cnn) b += sizeof(float) * CN_WPAD + sizeof(int) * (4 + 3 * CN_WIN + 2 * (size_t)n);
+  return b;
 }
 
-__device__ inline NNSmem nn_carve(int n, char* base) {
+__device__ inline NNSmem nn_carve(int n, char* base, bool with_cnn = false) {
   NNSmem s;
-  float* f = (float*)base;
-  s.w = f; f += NN_WPAD;
-  s.z = f; f += NN_GROUPS * (NN_IN + 3);
-  s.h1 = f; f += NN_GROUPS * NN_H;
-  double* p = (double*)f;
+  double* p = (double*)base;
   s.red = p; p += HQ_WARPS;
   s.pu2 = p; p += n;
   s.pxn = p; p += n;
   s.pds = p; p += n;
   s.gacc = p; p += NN_GROUPS;
-  s.scal = p;
+  s.scal = p; p += 8;
+  float* f = (float*)p;
+  s.w = f; f += NN_WPAD;
+  s.z = f; f += NN_GROUPS * (NN_IN + 3);
+  s.h1 = f; f += NN_GROUPS * NN_H;
+  s.cw = nullptr;
+  if (with_cnn) {
+    s.cw = f; f += CN_WPAD;
+    int* q = (int*)f;
+    s.win.cnt = q; q += 4;
+    s.win.lst = q; q += 3 * CN_WIN;
+    s.win.pos = q;
+  }
   return s;
+}
+
+// F of one configuration by the whole CTA (groups of 8 lanes per patch, fixed order); the
+// patch values go to fc when fc != nullptr.  Returns F in every thread.
+__device__ inline double fc_eval_all(const Dev& d, const NNSmem& s, const double* X, double x0, float* fc) {
+  const int n = d.n, NL = d.n * d.L;
+  const int g = threadIdx.x / 8, sub = threadIdx.x % 8;
+  float* z = s.z + g * (NN_IN + 3);
+  float* h1 = s.h1 + g * NN_H;
+  double part = 0.0;
+  for (int base = 0; base < NL; base += NN_GROUPS) {
+    const int row = base + g;
+    const bool on = row < NL;
+    fill_patch(d, X, on ? row / n : 0, on ? row % n : 0, x0, z, sub, -1, -1, 0.0, 0.0);
+    const float f = nn_patch_eval(s.w, z, h1, sub);
+    if (on && sub == 0) {
+      if (fc) fc[row] = f;
+      part += (double)f;
+    }
+  }
+  if (sub == 0) s.gacc[g] = part;
+  __syncthreads();
+  double F = 0.0;
+  for (int k = 0; k < NN_GROUPS; ++k) F += s.gacc[k];
+  __syncthreads();
+  return F;
 }
 
 // F(X) of every chain (grid = chains); also refreshes the patch cache fc.
@@ -138,53 +173,49 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_eval_kernel(Dev d, NNState nn, 
   const int c = blockIdx.x, n = d.n, NL = d.n * d.L;
   const NNSmem s = nn_carve(n, nraw);
   load_weights(nn.wbf, s.w);
-  const double* X = Xall + (size_t)c * NL;
-  float* fc = nn.fcache + (size_t)c * NL;
-  const int g = threadIdx.x / 8, sub = threadIdx.x % 8;
-  float* z = s.z + g * (NN_IN + 3);
-  float* h1 = s.h1 + g * NN_H;
-  double part = 0.0;
-  for (int base = 0; base < NL; base += NN_GROUPS) {
-    const int row = base + g;
-    const bool on = row < NL;
-    fill_patch(d, X, on ? row / n : 0, on ? row % n : 0, nn.x0, z, sub, -1, -1, 0.0, 0.0);
-    const float f = nn_patch_eval(s.w, z, h1, sub);
-    if (on && sub == 0) {
-      if (write_cache) fc[row] = f;
-      part += (double)f;
-    }
-  }
-  if (sub == 0) s.gacc[g] = part;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double F = 0.0;
-    for (int k = 0; k < NN_GROUPS; ++k) F += s.gacc[k];
-    Fout[c] = F;
-  }
+  const double F = fc_eval_all(d, s, Xall + (size_t)c * NL, nn.x0, write_cache ? nn.fcache + (size_t)c * NL : nullptr);
+  if (threadIdx.x == 0) Fout[c] = F;
 }
 
 // n_inner network-driven sweeps of every chain: local moves at every (l, i), then block
-// moves at every site, each accepted on exp(2 dF - dtau dS_ph) with the exact phonon action.
+// moves at every site, each accepted on exp(2 dF - dtau dS_ph) with the exact phonon action
+// (dF from the patch network, or for block moves with use_cnn from the convolutional action).
 // A fixed visiting order of reversible moves is not reversible as a whole, and the
 // cumulative accept needs a reversible proposal; so each step draws a direction (second
 // uniform of the step's Philox block, tag 4): forward (l, i ascending, then block moves i
-// ascending) or the exact reverse of that sequence, with probability 1/2 each.
-__global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn, int n_inner, int do_local,
-                                                              int do_block) {
+// ascending) or the exact reverse of that sequence, with probability 1/2 each.  The accepted
+// moves' dF are summed (thread 0, fixed order) into nn.dFpath for the cumulative accept.
+// The caches of the current fields (fc; with use_cnn also the convolutional activations) are
+// valid on entry; with use_cnn each network's cache is rebuilt before its part when the other
+// part has changed the fields.
+__global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn, CnnState cn, int n_inner,
+                                                              int do_local, int do_block, int use_cnn) {
   extern __shared__ __align__(16) char nraw[];
   const int c = blockIdx.x, n = d.n, L = d.L, NL = n * L;
   if (!d.active[c]) return;
-  const NNSmem s = nn_carve(n, nraw);
+  const NNSmem s = nn_carve(n, nraw, use_cnn != 0);
   load_weights(nn.wbf, s.w);
+  if (use_cnn) cn_load_weights(cn.wbf, s.cw);
   double* X = d.X + (size_t)c * NL;
   float* fc = nn.fcache + (size_t)c * NL;
   float* fnew = nn.fnew + (size_t)c * 5 * L;
+  float *h1c = nullptr, *h2c = nullptr, *o3c = nullptr, *h1p = nullptr, *h2p = nullptr, *o3p = nullptr;
+  if (use_cnn) {
+    h1c = cn.h1c + (size_t)c * NL * CN_C;
+    h2c = cn.h2c + (size_t)c * NL * CN_C;
+    o3c = cn.o3c + (size_t)c * NL;
+    h1p = cn.h1p + (size_t)c * 9 * L * CN_C;
+    h2p = cn.h2p + (size_t)c * 25 * L * CN_C;
+    o3p = cn.o3p + (size_t)c * CN_WIN * L;
+  }
   const int g = threadIdx.x / 8, sub = threadIdx.x % 8;
   float* z = s.z + g * (NN_IN + 3);
   float* h1 = s.h1 + g * NN_H;
   const uint32_t* id = d.cid + 4 * (size_t)c;
   const uint32_t key0 = id[0], key1 = id[1], chain = id[2], step = id[3];
   long long nl_acc = 0, nb_acc = 0;
+  double path = 0.0;                   // thread 0
+  bool fc_stale = false, cn_stale = false;  // uniform over the CTA
   const double kfac = d.mass / (2.0 * d.dtau), pfac = 0.5 * d.dtau * d.mass * (d.omega * d.omega);
   double du1, du2;
   proposal_uniforms(key0, key1, 0u, step, chain, 4u, du1, du2);
@@ -194,6 +225,10 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
     for (int part = 0; part < 2; ++part) {
     const bool local_part = (part == 0) == fwd;
     if (local_part && do_local) {
+      if (fc_stale) {
+        fc_eval_all(d, s, X, nn.x0, fc);
+        fc_stale = false;
+      }
       for (int sl0 = 0; sl0 < L; ++sl0) {
         const int sl = fwd ? sl0 : L - 1 - sl0;
         for (int i = threadIdx.x; i < n; i += HQ_THREADS) {
@@ -230,16 +265,26 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
             const double prob = exp(fmin(2.0 * dF - s.pds[i], 709.0));
             const int acc = s.pu2[i] < prob;
             s.scal[0] = acc;
-            if (acc) X[(size_t)sl * n + i] = s.pxn[i];
+            if (acc) {
+              X[(size_t)sl * n + i] = s.pxn[i];
+              path += dF;
+            }
             nl_acc += acc;
           }
           __syncthreads();
-          if (s.scal[0] != 0.0 && row >= 0 && sub == 0) fc[row] = f;
+          if (s.scal[0] != 0.0) {
+            if (row >= 0 && sub == 0) fc[row] = f;
+            cn_stale = true;
+          }
           __syncthreads();
         }
       }
     }
     if (!local_part && do_block) {
+      if (use_cnn && cn_stale) {
+        cn_forward_all(d, s.cw, X, nn.x0, h1c, h2c, o3c, s.red);
+        cn_stale = false;
+      }
       for (int i0 = 0; i0 < n; ++i0) {
         const int i = fwd ? i0 : n - 1 - i0;
         if (threadIdx.x == 0) {
@@ -257,44 +302,56 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
         }
         a = block_sum(a, s.red);
         const double dS = pfac * a;
-        // the 5 L patches containing site i: centres (l, i - c)
-        double part = 0.0;
         const int x = i % d.nx, y = i / d.nx;
-        for (int base = 0; base < 5 * L; base += NN_GROUPS) {
-          const int q = base + g;
-          const bool on = q < 5 * L;
-          int row = 0;
-          if (on) {
-            const int cidx = q % 5, sl = q / 5;
-            const int cx_ = (cidx == 1) - (cidx == 2), cy_ = (cidx == 3) - (cidx == 4);
-            const int j = (x - cx_ + d.nx) % d.nx + d.nx * ((y - cy_ + d.ny) % d.ny);
-            row = sl * n + j;
+        double dF;
+        if (use_cnn) {
+          cn_build_window(d, i, s.win);
+          dF = cn_block_delta(d, s.cw, s.win, X, nn.x0, i, dx, h1c, h2c, o3c, h1p, h2p, o3p, s.red);
+        } else {
+          // the 5 L patches containing site i: centres (l, i - c)
+          double pt = 0.0;
+          for (int base = 0; base < 5 * L; base += NN_GROUPS) {
+            const int q = base + g;
+            const bool on = q < 5 * L;
+            int row = 0;
+            if (on) {
+              const int cidx = q % 5, sl = q / 5;
+              const int cx_ = (cidx == 1) - (cidx == 2), cy_ = (cidx == 3) - (cidx == 4);
+              const int j = (x - cx_ + d.nx) % d.nx + d.nx * ((y - cy_ + d.ny) % d.ny);
+              row = sl * n + j;
+            }
+            fill_patch(d, X, row / n, row % n, nn.x0, z, sub, i, -1, 0.0, dx);
+            const float f = nn_patch_eval(s.w, z, h1, sub);
+            if (on && sub == 0) {
+              fnew[q] = f;
+              pt += (double)f - (double)fc[row];
+            }
           }
-          fill_patch(d, X, row / n, row % n, nn.x0, z, sub, i, -1, 0.0, dx);
-          const float f = nn_patch_eval(s.w, z, h1, sub);
-          if (on && sub == 0) {
-            fnew[q] = f;
-            part += (double)f - (double)fc[row];
-          }
-        }
-        if (sub == 0) s.gacc[g] = part;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          double dF = 0.0;
+          if (sub == 0) s.gacc[g] = pt;
+          __syncthreads();
+          dF = 0.0;
           for (int k = 0; k < NN_GROUPS; ++k) dF += s.gacc[k];
+        }
+        if (threadIdx.x == 0) {
           const double prob = exp(fmin(2.0 * dF - dS, 709.0));
           const int acc = s.scal[2] < prob;
           s.scal[0] = acc;
+          if (acc) path += dF;
           nb_acc += acc;
         }
         __syncthreads();
         if (s.scal[0] != 0.0) {
           for (int sl = threadIdx.x; sl < L; sl += HQ_THREADS) X[(size_t)sl * n + i] = X[(size_t)sl * n + i] + dx;
-          for (int q = threadIdx.x; q < 5 * L; q += HQ_THREADS) {
-            const int cidx = q % 5, sl = q / 5;
-            const int cx_ = (cidx == 1) - (cidx == 2), cy_ = (cidx == 3) - (cidx == 4);
-            const int j = (x - cx_ + d.nx) % d.nx + d.nx * ((y - cy_ + d.ny) % d.ny);
-            fc[(size_t)sl * n + j] = fnew[q];
+          if (use_cnn) {
+            cn_block_commit(d, s.win, h1c, h2c, o3c, h1p, h2p, o3p);
+            fc_stale = true;
+          } else {
+            for (int q = threadIdx.x; q < 5 * L; q += HQ_THREADS) {
+              const int cidx = q % 5, sl = q / 5;
+              const int cx_ = (cidx == 1) - (cidx == 2), cy_ = (cidx == 3) - (cidx == 4);
+              const int j = (x - cx_ + d.nx) % d.nx + d.nx * ((y - cy_ + d.ny) % d.ny);
+              fc[(size_t)sl * n + j] = fnew[q];
+            }
           }
         }
         __syncthreads();
@@ -308,11 +365,12 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
     cnt[1] += nl_acc;
     cnt[2] += (long long)n_inner * (do_block ? n : 0);
     cnt[3] += nb_acc;
+    nn.dFpath[c] = path;
   }
 }
 
 // Cumulative accept of X' (fields now in d.X, log|det M(X')| in d.logdet after the stack
-// build) against X (saved in nn.X0 with nn.ld0, nn.F0): p_c = exp(2 dlog|det M| - 2 dF).
+// build) against X (saved in nn.X0 with nn.ld0): p_c = exp(2 dlog|det M| - 2 nn.dFpath).
 __global__ void __launch_bounds__(HQ_THREADS) nn_decide_kernel(Dev d, NNState nn) {
   const int c = blockIdx.x, NL = d.n * d.L;
   if (!d.active[c]) return;
@@ -322,7 +380,7 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_decide_kernel(Dev d, NNState nn
     const uint32_t* id = d.cid + 4 * (size_t)c;
     proposal_uniforms(id[0], id[1], 0u, id[3], id[2], 4u, u1, u2);
     const double ld1 = d.logdet[c], ld0 = nn.ld0[c];
-    const double arg = 2.0 * (ld1 - ld0) - 2.0 * (nn.F1[c] - nn.F0[c]);
+    const double arg = 2.0 * (ld1 - ld0) - 2.0 * nn.dFpath[c];
     const double pc = exp(fmin(arg, 709.0));
     acc = u1 < pc;
     nn.last_pc[c] = pc;
@@ -555,11 +613,11 @@ cudaError_t nn_launch_eval(const Dev& d, const NNState& nn, const double* X, dou
   return cudaGetLastError();
 }
 
-cudaError_t nn_launch_inner(const Dev& d, const NNState& nn, int n_inner, int do_local, int do_block,
-                            cudaStream_t s) {
-  const size_t sb = nn_smem_bytes(d.n);
+cudaError_t nn_launch_inner(const Dev& d, const NNState& nn, const CnnState& cn, int n_inner, int do_local,
+                            int do_block, int use_cnn, cudaStream_t s) {
+  const size_t sb = nn_smem_bytes(d.n, use_cnn != 0);
   smem_opt_in((const void*)nn_inner_kernel, sb);
-  nn_inner_kernel<<<d.n_chains, HQ_THREADS, sb, s>>>(d, nn, n_inner, do_local, do_block);
+  nn_inner_kernel<<<d.n_chains, HQ_THREADS, sb, s>>>(d, nn, cn, n_inner, do_local, do_block, use_cnn);
   return cudaGetLastError();
 }
 
