@@ -384,6 +384,9 @@ def run_tau(args):
 def run_learned(args):
     """Learned vs plain sampler on the batched workload (8x8, beta = 8, 256 chains).
 
+    With --cnn the block moves of the inner chain use the convolutional action, trained on the
+    same samples; local moves always use the patch network.
+
     1. Plain sampler: warm-up, then training samples (fields and exact log|det M|).
     2. Network training on those samples (the library's kernels).
     3. Learned sampler (cumulative steps of args.n_inner network sweeps, exact accept) from the
@@ -424,6 +427,18 @@ def run_learned(args):
         losses.extend(net.nn_train(Xd, yd, epochs=ep, batch=64, lr=args.lr * 0.5 ** k, seed=args.nn_seed + k))
     t_train = time.perf_counter() - t0
     theta = net.get_params()
+    theta_cnn, closs = None, None
+    if args.cnn:
+        # convolutional action for block moves, fitted to the same targets
+        net.cnn_set_params(hq.init_cnn(args.nn_seed))
+        t1 = time.perf_counter()
+        closs = []
+        for k in range(3):
+            ep = args.epochs // 3 + (args.epochs % 3 if k == 2 else 0)
+            closs.extend(net.cnn_train(Xd, yd, epochs=ep, batch=64, lr=args.cnn_lr * 0.5 ** k,
+                                       seed=args.nn_seed + 10 + k))
+        t_train_cnn = time.perf_counter() - t1
+        theta_cnn = net.cnn_get_params()
     del Xd, yd
     net.close()
     # learned sampler
@@ -431,16 +446,19 @@ def run_learned(args):
     lrn = hq.Engine(params, C, max_series=steps + args.warmup + args.steps + 4)
     lrn.attach_network(4, 8)
     lrn.set_params(theta)
+    if theta_cnn is not None:
+        lrn.cnn_set_params(theta_cnn)
+    use_cnn = theta_cnn is not None
     lrn.set_fields(X_eq)
-    lrn.cumulative(args.warmup, args.n_inner, measure=True)
+    lrn.cumulative(args.warmup, args.n_inner, measure=True, cnn=use_cnn)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
-    lrn.cumulative(args.steps, args.n_inner, measure=True)
+    lrn.cumulative(args.steps, args.n_inner, measure=True, cnn=use_cnn)
     b.record()
     torch.cuda.synchronize()
     step_rate = C * args.steps / (a.elapsed_time(b) / 1e3)
-    lrn.cumulative(steps, args.n_inner, measure=True)
+    lrn.cumulative(steps, args.n_inner, measure=True, cnn=use_cnn)
     st = lrn.learned_stats()
     acc = sum(x["cumulative_accepted"] for x in st) / max(1, sum(x["cumulative_proposed"] for x in st))
     inner_l = sum(x["inner_local_accepted"] for x in st) / max(1, sum(x["inner_local_proposed"] for x in st))
@@ -477,6 +495,9 @@ def run_learned(args):
             "gain": {k: indep_l[k] / indep_p[k] for k in indep_l},
             "training": {"seconds": t_train, "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
                          "target_variance": float(np.var(ytr))},
+            "block_moves": "convolutional action" if use_cnn else "patch network",
+            "cnn_training": None if not use_cnn else {"seconds": t_train_cnn, "loss_first": float(closs[0]),
+                                                      "loss_last": float(closs[-1]), "lr": args.cnn_lr},
             "wall_s": time.perf_counter() - t_all}
     print(json.dumps(line), flush=True)
     return 0
@@ -640,6 +661,8 @@ def main():
     ap.add_argument("--train-warmup", type=int, default=30)
     ap.add_argument("--train-snapshots", type=int, default=32)
     ap.add_argument("--tau-steps", type=int, default=150)
+    ap.add_argument("--cnn", action="store_true", help="learned mode: convolutional action for block moves")
+    ap.add_argument("--cnn-lr", type=float, default=3e-3)
     ap.add_argument("--rate", type=float, default=40.0, help="serving mode: requests per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serving mode: seconds of arrivals")
     ap.add_argument("--req-sweeps", type=int, default=10, help="serving mode: sweeps per request")
