@@ -612,6 +612,29 @@ def run_serving(args):
     return 0
 
 
+def run_autotune(args):
+    """Autotuner table (ms per sweep for every delay rank and block-move method) on the
+    batched workload (full sweeps) and on the largest lattice (local sweeps only: a full sweep
+    there is minutes of block moves)."""
+    import torch
+    import paper_1905_07440_gb300 as hq
+    out = {"mode": "autotune", "metric": "ms per sweep", "tables": {}}
+    for name, prm, C, glob in (("batched 8x8 beta=8 L=80", workloads.BATCHED, workloads.BATCHED_RUN["n_chains"], True),
+                               ("largest 16x16 beta=16 L=160, local sweeps", workloads.LARGEST, 64, False)):
+        X = torch.from_numpy(workloads.initial_fields(prm, C)).cuda()
+        ks = (4, 8, 16, 32)
+        methods = (1, 2) if glob else (1,)
+        t0 = time.perf_counter()
+        table, bk, bm = hq.autotune(prm, X, ks=ks, methods=methods, global_=glob, warmup=1, reps=args.steps)
+        out["tables"][name] = {"chains": C, "ms_per_sweep": {f"k={k},method={m}": v for (k, m), v in table.items()},
+                               "best_k": bk, "best_method": ["", "per-slice", "chunk propagators"][bm],
+                               "default_ms": table.get((prm.delay_k, 2 if glob else 1)),
+                               "seconds": time.perf_counter() - t0}
+        del X
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_peaks():
     """FP64 pipe evidence: DFMA and DMMA probes of the library, cuBLAS DGEMM/SGEMM via torch."""
     import torch
@@ -682,6 +705,8 @@ def main():
         sys.exit(run_serving(args))
     if args.peaks:
         sys.exit(run_peaks())
+    if args.workload == "autotune":
+        sys.exit(run_autotune(args))
     if args.tau_sweeps:
         sys.exit(run_tau(args))
     if args.warmup < 3 and args.impl == "ours":

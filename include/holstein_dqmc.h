@@ -77,6 +77,10 @@ typedef struct hq_params {
   double dx_local;  /* local proposal dX ~ U[-dx_local, dx_local) */
   double dx_global; /* block proposal dX ~ U[-dx_global, dx_global) */
   uint64_t seed;    /* Philox key */
+  int block_method; /* block-move algorithm: 0 chosen by the FP64 flop model, 1 every slice
+                       through the separable exp(-dtau K), 2 chunk propagators (same results
+                       up to rounding; hq_autotune measures them) */
+  int reserved;     /* must be 0 */
 } hq_params;
 
 typedef struct hq_obs {   /* per chain, accumulated since hq_create / hq_restore */
@@ -140,11 +144,28 @@ int hq_checkpoint(hq_engine* e, void* buf, size_t* len);
 /* Restore a state written by hq_checkpoint for the same parameters and chain count. */
 int hq_restore(hq_engine* e, const void* buf, size_t len);
 
-/* Block-move algorithm chosen for this parameter set by an FP64 flop model: 0 = every
- * slice applied through the separable exp(-dtau K) per move, 1 = chunk propagators (the
- * n_wrap-slice products kept per chain, updated by a rank-n_wrap correction per move and
- * applied with one GEMM per chunk).  Both give the same determinants up to rounding. */
+/* Block-move algorithm in use: 0 = every slice applied through the separable exp(-dtau K)
+ * per move, 1 = chunk propagators (the n_wrap-slice products kept per chain, updated by a
+ * rank-n_wrap correction per move and applied with one GEMM per chunk).  Chosen by
+ * hq_params.block_method, or when that is 0 by an FP64 flop model.  Both give the same
+ * determinants up to rounding. */
 int hq_block_move_method(const hq_engine* e);
+
+/* Autotuner for the runtime choices that change speed but not results (beyond rounding): the
+ * delayed-update rank k and the block-move algorithm.  For every pair (ks[a], methods[b])
+ * (methods: 1 per-slice, 2 chunk propagators) it builds an engine of n_chains chains with
+ * parameters p in the caller's device arena (at least hq_autotune_arena_bytes bytes, 256-byte
+ * aligned; the engine is destroyed before the next pair), copies the fields X_device
+ * [n_chains][L][N] in, runs `warmup` sweeps with `flags`, then times `reps` sweeps with CUDA
+ * events on the stream.  ms_out[a * n_methods + b] receives milliseconds per sweep; best_k
+ * and best_method the fastest pair.  Synchronises.  The paper has no counterpart: it fixes
+ * neither k nor the block-move algorithm.
+ * Errors: HQ_EINVAL for bad arguments or a candidate outside 1..32 / 1..2; HQ_ENOMEM if the
+ * arena is too small; CUDA errors as HQ_ECUDA. */
+size_t hq_autotune_arena_bytes(const hq_params* p, int n_chains, const int* ks, int n_k);
+int hq_autotune(const hq_params* p, int n_chains, const double* X_device, void* device_arena, size_t arena_bytes,
+                void* stream, const int* ks, int n_k, const int* methods, int n_methods, unsigned flags, int warmup,
+                int reps, double* ms_out, int* best_k, int* best_method);
 
 /* Slots.  Every chain slot carries its own Philox key, chain word and sweep counter (set by
  * hq_create to seed, first_chain + slot, 0; the counter advances by one per sweep or

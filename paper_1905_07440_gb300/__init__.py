@@ -41,7 +41,7 @@ class hq_params(ctypes.Structure):
                 ("omega", ctypes.c_double), ("mass", ctypes.c_double), ("g", ctypes.c_double),
                 ("beta", ctypes.c_double), ("dtau", ctypes.c_double), ("n_wrap", ctypes.c_int),
                 ("delay_k", ctypes.c_int), ("dx_local", ctypes.c_double), ("dx_global", ctypes.c_double),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("block_method", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class hq_obs(ctypes.Structure):
@@ -110,6 +110,10 @@ _SIGNATURES = {
     "hq_cnn_gradient": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _P(ctypes.c_float), _dp]),
     "hq_get_learned_stats": (ctypes.c_int, [_vp, _P(hq_learned_stats)]),
     "hq_get_section_cycles": (ctypes.c_int, [_P(ctypes.c_uint64), ctypes.c_int]),
+    "hq_autotune_arena_bytes": (ctypes.c_size_t, [_P(hq_params), ctypes.c_int, _P(ctypes.c_int), ctypes.c_int]),
+    "hq_autotune": (ctypes.c_int, [_P(hq_params), ctypes.c_int, _vp, _vp, ctypes.c_size_t, _vp, _P(ctypes.c_int),
+                                   ctypes.c_int, _P(ctypes.c_int), ctypes.c_int, ctypes.c_uint, ctypes.c_int,
+                                   ctypes.c_int, _dp, _P(ctypes.c_int), _P(ctypes.c_int)]),
     "hq_get_timing": (ctypes.c_int, [_vp, _dp, _P(ctypes.c_int64)]),
 }
 HQ_N_PHASES = 4
@@ -147,7 +151,7 @@ class HQError(RuntimeError):
 def make_params(p):
     """hq_params from any object with the workloads.HolsteinParams attributes."""
     return hq_params(p.nx, p.ny, p.t, p.mu, p.omega, p.mass, p.g, p.beta, p.dtau, p.n_wrap, p.delay_k,
-                     p.dx_local, p.dx_global, p.seed)
+                     p.dx_local, p.dx_global, p.seed, int(getattr(p, "block_method", 0)), 0)
 
 
 def arena_bytes(params, n_chains, max_series=0):
@@ -410,6 +414,34 @@ def proposal_uniforms(seed, chain, sweep, events, tag, stream=None):
     if rc != HQ_OK:
         raise HQError(f"hq_proposal_uniforms failed ({rc})")
     return u1, u2
+
+
+def autotune(params, X, ks=(4, 8, 16, 32), methods=(1, 2), local=True, global_=True, warmup=1, reps=2,
+             stream=None):
+    """Time every (delay rank, block-move method) pair on the fields X (CUDA float64
+    [chains][L][N]); returns ({(k, method): ms per sweep}, best_k, best_method)."""
+    import torch
+    lib = load_library()
+    prm = make_params(params)
+    C = int(X.shape[0])
+    karr = (ctypes.c_int * len(ks))(*ks)
+    marr = (ctypes.c_int * len(methods))(*methods)
+    nb = int(lib.hq_autotune_arena_bytes(ctypes.byref(prm), C, karr, len(ks)))
+    if nb == 0:
+        raise HQError("invalid autotune parameters")
+    arena = torch.empty(nb + 256, dtype=torch.uint8, device=X.device)
+    base = (arena.data_ptr() + 255) // 256 * 256
+    st = stream if stream is not None else torch.cuda.current_stream(X.device)
+    ms = np.zeros(len(ks) * len(methods))
+    bk, bm = ctypes.c_int(), ctypes.c_int()
+    flags = (HQ_LOCAL if local else 0) | (HQ_GLOBAL if global_ else 0)
+    rc = lib.hq_autotune(ctypes.byref(prm), C, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(base), nb,
+                         ctypes.c_void_p(st.cuda_stream), karr, len(ks), marr, len(methods), flags, int(warmup),
+                         int(reps), _dptr(ms), ctypes.byref(bk), ctypes.byref(bm))
+    if rc != HQ_OK:
+        raise HQError(f"hq_autotune failed ({rc})")
+    table = {(k, m): float(ms[a * len(methods) + b]) for a, k in enumerate(ks) for b, m in enumerate(methods)}
+    return table, bk.value, bm.value
 
 
 def init_network(seed, out_scale=1.0):

@@ -82,7 +82,16 @@ const char* validate(const hq_params* p, int n_chains, int max_series) {
   if (!(p->dx_local >= 0.0) || !(p->dx_global >= 0.0)) return "proposal widths must be >= 0";
   if (n_chains < 1) return "n_chains must be >= 1";
   if (max_series < 0) return "max_series must be >= 0";
+  if (p->block_method < 0 || p->block_method > 2) return "block_method must be 0, 1 or 2";
+  if (p->reserved != 0) return "reserved must be 0";
   return nullptr;
+}
+
+// chunk propagators for block moves: forced by block_method, else by the flop model
+bool use_chunks(const hq_params& p) {
+  if (p.block_method == 1) return false;
+  if (p.block_method == 2) return true;
+  return hq::chunk_propagators_pay(p.nx, p.ny, (int)n_slices(p), p.n_wrap);
 }
 
 Layout layout(const hq_params& p, int C, int max_series) {
@@ -115,7 +124,7 @@ Layout layout(const hq_params& p, int C, int max_series) {
   l.cid = take(sizeof(uint32_t) * 4 * C);
   l.active = take(sizeof(int) * C);
   l.slen = take(sizeof(int) * C);
-  if (hq::chunk_propagators_pay(p.nx, p.ny, (int)L, p.n_wrap)) {
+  if (use_chunks(p)) {
     const size_t nch = (L + p.n_wrap - 1) / p.n_wrap;
     l.expV = take(sizeof(double) * C * L * n);
     l.cmat = take(sizeof(double) * C * 2 * nch * nn);
@@ -258,7 +267,7 @@ int hq_create(const hq_params* p, int n_chains, int first_chain, int max_series,
   d.cid = (uint32_t*)(a + l.cid);
   d.active = (int*)(a + l.active);
   d.slen = (int*)(a + l.slen);
-  d.use_cm = hq::chunk_propagators_pay(d.nx, d.ny, d.L, d.n_wrap) ? 1 : 0;
+  d.use_cm = use_chunks(*p) ? 1 : 0;
   d.n_chunks = (d.L + d.n_wrap - 1) / d.n_wrap;
   if (d.use_cm) {
     d.expV = (double*)(a + l.expV);
@@ -1135,6 +1144,71 @@ int hq_get_learned_stats(hq_engine* e, hq_learned_stats* out) {
     out[c] = hq_learned_stats{k[0], k[1], k[2], k[3], k[4], k[5], pc[c]};
   }
   return HQ_OK;
+}
+
+size_t hq_autotune_arena_bytes(const hq_params* p, int n_chains, const int* ks, int n_k) {
+  if (!p || !ks || n_k < 1) return 0;
+  size_t need = 0;
+  for (int a = 0; a < n_k; ++a)
+    for (int m = 1; m <= 2; ++m) {
+      hq_params q = *p;
+      q.delay_k = ks[a];
+      q.block_method = m;
+      if (validate(&q, n_chains, 0)) return 0;
+      const size_t b = layout(q, n_chains, 0).total;
+      need = b > need ? b : need;
+    }
+  return need;
+}
+
+int hq_autotune(const hq_params* p, int n_chains, const double* X_device, void* device_arena, size_t arena_bytes,
+                void* stream, const int* ks, int n_k, const int* methods, int n_methods, unsigned flags, int warmup,
+                int reps, double* ms_out, int* best_k, int* best_method) {
+  if (!p || !X_device || !ks || !methods || n_k < 1 || n_methods < 1 || warmup < 0 || reps < 1 || !ms_out ||
+      (flags & ~(HQ_LOCAL | HQ_GLOBAL | HQ_MEASURE)))
+    return HQ_EINVAL;
+  for (int b = 0; b < n_methods; ++b)
+    if (methods[b] < 1 || methods[b] > 2) return HQ_EINVAL;
+  const size_t need = hq_autotune_arena_bytes(p, n_chains, ks, n_k);
+  if (need == 0) return HQ_EINVAL;
+  if (!device_arena || arena_bytes < need) return HQ_ENOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) {
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    return HQ_ECUDA;
+  }
+  int rc = HQ_OK;
+  double best = -1.0;
+  for (int a = 0; a < n_k && rc == HQ_OK; ++a)
+    for (int b = 0; b < n_methods && rc == HQ_OK; ++b) {
+      hq_params q = *p;
+      q.delay_k = ks[a];
+      q.block_method = methods[b];
+      hq_engine* e = nullptr;
+      rc = hq_create(&q, n_chains, 0, 0, device_arena, arena_bytes, stream, &e);
+      if (rc) break;
+      rc = hq_set_fields_device(e, X_device);
+      rc = rc ? rc : hq_sweep(e, warmup, flags);
+      rc = rc ? rc : cuda_check(e, cudaEventRecord(ev[0], st), "autotune event");
+      rc = rc ? rc : hq_sweep(e, reps, flags);
+      rc = rc ? rc : cuda_check(e, cudaEventRecord(ev[1], st), "autotune event");
+      rc = rc ? rc : cuda_check(e, cudaEventSynchronize(ev[1]), "autotune sync");
+      float ms = 0.f;
+      rc = rc ? rc : cuda_check(e, cudaEventElapsedTime(&ms, ev[0], ev[1]), "autotune elapsed");
+      hq_destroy(e);
+      if (rc) break;
+      const double per = (double)ms / reps;
+      ms_out[a * n_methods + b] = per;
+      if (best < 0.0 || per < best) {
+        best = per;
+        if (best_k) *best_k = ks[a];
+        if (best_method) *best_method = methods[b];
+      }
+    }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  return rc;
 }
 
 int hq_get_section_cycles(uint64_t* out, int n) {

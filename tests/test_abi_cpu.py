@@ -9,6 +9,8 @@ import subprocess
 import numpy as np
 import pytest
 
+from workloads import HolsteinParams
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "holstein_dqmc.h")
 
@@ -77,3 +79,21 @@ def test_tau_int_matches_oracle():
     assert w_c == w_o
     assert abs(t_c - t_o) < 1e-10 * t_o
     assert hq.tau_int(np.ones(10))[0] == 0.5
+
+
+def test_autotune_arena_is_the_largest_candidate():
+    import paper_1905_07440_gb300 as hq
+    lib = hq.load_library()
+    p = HolsteinParams(nx=8, ny=8, beta=2.0)
+
+    def need(ks):
+        arr = (ctypes.c_int * len(ks))(*ks)
+        return int(lib.hq_autotune_arena_bytes(ctypes.byref(hq.make_params(p)), 16, arr, len(ks)))
+
+    one = {k: need([k]) for k in (1, 8, 32)}
+    assert 0 < one[1] <= one[8] <= one[32]
+    assert need([8, 1, 32]) == one[32]
+    # the chunk-propagator layout is the larger one and is always included
+    for m in (1, 2):
+        assert hq.arena_bytes(p.with_(delay_k=32, block_method=m), 16) <= one[32]
+    assert need([0]) == 0 and need([33]) == 0

@@ -159,6 +159,31 @@ def test_block_move_methods_against_oracle(hq, nx, beta, n_wrap, method):
     check_against_oracle(hq, p, X0, 2, local=True, global_=True)
 
 
+@pytest.mark.parametrize("nx,beta,n_wrap", [(4, 1.0, 3), (8, 1.0, 10), (6, 2.0, 7)])
+@pytest.mark.parametrize("forced", [1, 2])
+def test_forced_block_move_method_against_oracle(hq, nx, beta, n_wrap, forced):
+    """block_method forces either algorithm whatever the flop model says; both agree with the
+    oracle (fields bit for bit, log-determinants and G to rounding)."""
+    p = HolsteinParams(nx=nx, ny=nx, beta=beta, n_wrap=n_wrap, delay_k=8, seed=13, block_method=forced)
+    eng = hq.Engine(p, 1)
+    assert eng.block_move_method == forced - 1
+    eng.close()
+    X0 = initial_fields(p, 2, seed=23)
+    check_against_oracle(hq, p, X0, 1, local=False, global_=True)
+
+
+def test_autotune_times_every_pair(hq):
+    import torch
+    p = HolsteinParams(nx=6, ny=6, beta=1.0, seed=3)
+    X = torch.from_numpy(initial_fields(p, 8, seed=1)).cuda()
+    table, bk, bm = hq.autotune(p, X, ks=(4, 16), methods=(1, 2), warmup=1, reps=1)
+    assert set(table) == {(4, 1), (4, 2), (16, 1), (16, 2)}
+    assert all(v > 0 for v in table.values())
+    assert table[(bk, bm)] == min(table.values())
+    # the fields given to the autotuner are not modified
+    assert np.array_equal(X.cpu().numpy(), initial_fields(p, 8, seed=1))
+
+
 def test_local_only_and_global_only(hq):
     p = HolsteinParams(nx=4, ny=4, beta=2.0, delay_k=5)
     X0 = initial_fields(p, 2, seed=9)

@@ -33,6 +33,7 @@ class HolsteinParams:
     dx_local: float = 0.5
     dx_global: float = 1.0
     seed: int = DEFAULT_SEED
+    block_method: int = 0  # engine's block-move algorithm (0 flop model, 1 per slice, 2 chunks)
 
     @property
     def n_sites(self) -> int:
