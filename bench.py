@@ -612,6 +612,62 @@ def run_serving(args):
     return 0
 
 
+HETERO_MIX = ((dict(nx=4, ny=4, beta=4.0), 64), (dict(nx=6, ny=6, beta=4.0), 64), (dict(nx=8, ny=8, beta=4.0), 48),
+              (dict(nx=10, ny=10, beta=2.0), 32), (dict(nx=12, ny=12, beta=2.0), 16))
+
+
+def run_hetero(args):
+    """Heterogeneous batching: engines of five lattice shapes (224 chains) swept (a) one
+    engine after another on one stream, (b) each engine on its own stream, (c) as one group
+    (one persistent launch per sweep).  Value: chain-sweeps/s of (c)."""
+    import torch
+    import paper_1905_07440_gb300 as hq
+
+    def engines(streams):
+        out = []
+        for k, (shape, C) in enumerate(HETERO_MIX):
+            p = workloads.HolsteinParams(**shape, seed=workloads.BATCHED.seed + k)
+            e = hq.Engine(p, C, stream=torch.cuda.Stream() if streams else torch.cuda.current_stream())
+            e.set_fields(workloads.initial_fields(p, C, seed=k))
+            out.append(e)
+        return out
+
+    total = sum(C for _, C in HETERO_MIX)
+    res = {}
+    for mode in ("sequential", "streams", "group"):
+        engs = engines(mode == "streams")
+        grp = hq.Group(engs) if mode == "group" else None
+
+        def step():
+            if grp is not None:
+                grp.sweep(1)
+            else:
+                for e in engs:
+                    e.sweep(1)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+        torch.cuda.synchronize()
+        res[mode] = total * args.steps / (time.perf_counter() - t0)
+        if grp is not None:
+            grp.close()
+        for e in engs:
+            e.close()
+    line = {"metric": METRIC, "mode": "heterogeneous batching", "value": res["group"], "unit": "chain-sweeps/s",
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "; ".join(f"{s['nx']}x{s['ny']} beta={s['beta']:g} x{C}" for s, C in HETERO_MIX),
+                       "chains": total, "steps": args.steps, "warmup": args.warmup,
+                       "timing": "host wall clock, synchronised"},
+            "chain_sweeps_per_s": res, "group_vs_sequential": res["group"] / res["sequential"],
+            "group_vs_streams": res["group"] / res["streams"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_autotune(args):
     """Autotuner table (ms per sweep for every delay rank and block-move method) on the
     batched workload (full sweeps) and on the largest lattice (local sweeps only: a full sweep
@@ -707,6 +763,8 @@ def main():
         sys.exit(run_peaks())
     if args.workload == "autotune":
         sys.exit(run_autotune(args))
+    if args.workload == "hetero":
+        sys.exit(run_hetero(args))
     if args.tau_sweeps:
         sys.exit(run_tau(args))
     if args.warmup < 3 and args.impl == "ours":

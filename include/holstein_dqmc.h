@@ -151,6 +151,27 @@ int hq_restore(hq_engine* e, const void* buf, size_t len);
  * determinants up to rounding. */
 int hq_block_move_method(const hq_engine* e);
 
+/* Heterogeneous groups.  Engines of different lattices, temperatures and couplings (each
+ * with its own chains, fields and arena) swept together by one persistent launch per sweep:
+ * a chain's sweep (stack build, local chunks, block moves, records) is sequential, so workers
+ * take whole chain-sweeps from the group's table, longest estimated first, and short chains
+ * fill in around long ones; small engines fill the GPU together instead of one after another.
+ * Each chain computes exactly what its own engine's hq_sweep computes.  The group borrows the
+ * engines: do not destroy them while the group exists (hq_group_sweep orders itself after the
+ * engines' streams, and the engines' later calls after itself).  The group's device arena
+ * (hq_group_arena_bytes, 256-byte aligned) holds the engine descriptors and the task table,
+ * uploaded once, so an engine's chain count must not change afterwards (slots may be idled
+ * and reloaded).
+ * Errors: HQ_EINVAL for 0 or more than 64 engines, a repeated or null engine, an engine with
+ * more than 65535 chains; HQ_ENOMEM for a missing or small arena. */
+typedef struct hq_group hq_group;
+size_t hq_group_arena_bytes(hq_engine* const* engines, int n_engines);
+int hq_group_create(hq_engine* const* engines, int n_engines, void* device_arena, size_t arena_bytes,
+                    void* cuda_stream, hq_group** out);
+/* n_sweeps sweeps of every chain of every engine (flags as hq_sweep).  Asynchronous. */
+int hq_group_sweep(hq_group* g, int n_sweeps, unsigned flags);
+void hq_group_destroy(hq_group* g);
+
 /* Autotuner for the runtime choices that change speed but not results (beyond rounding): the
  * delayed-update rank k and the block-move algorithm.  For every pair (ks[a], methods[b])
  * (methods: 1 per-slice, 2 chunk propagators) it builds an engine of n_chains chains with

@@ -110,6 +110,10 @@ _SIGNATURES = {
     "hq_cnn_gradient": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _P(ctypes.c_float), _dp]),
     "hq_get_learned_stats": (ctypes.c_int, [_vp, _P(hq_learned_stats)]),
     "hq_get_section_cycles": (ctypes.c_int, [_P(ctypes.c_uint64), ctypes.c_int]),
+    "hq_group_arena_bytes": (ctypes.c_size_t, [_P(_vp), ctypes.c_int]),
+    "hq_group_create": (ctypes.c_int, [_P(_vp), ctypes.c_int, _vp, ctypes.c_size_t, _vp, _P(_vp)]),
+    "hq_group_sweep": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_uint]),
+    "hq_group_destroy": (None, [_vp]),
     "hq_autotune_arena_bytes": (ctypes.c_size_t, [_P(hq_params), ctypes.c_int, _P(ctypes.c_int), ctypes.c_int]),
     "hq_autotune": (ctypes.c_int, [_P(hq_params), ctypes.c_int, _vp, _vp, ctypes.c_size_t, _vp, _P(ctypes.c_int),
                                    ctypes.c_int, _P(ctypes.c_int), ctypes.c_int, ctypes.c_uint, ctypes.c_int,
@@ -387,6 +391,46 @@ class Engine:
         s = ctypes.c_int64()
         self.lib.hq_shape(self._h, None, None, None, ctypes.byref(s))
         return s.value
+
+
+class Group:
+    """Engines of different shapes swept together by one persistent launch per sweep; thin
+    wrapper of hq_group_*."""
+
+    def __init__(self, engines, stream=None):
+        import torch
+        self.lib = load_library()
+        self.engines = list(engines)
+        self._arr = (_vp * len(self.engines))(*[e._h.value for e in self.engines])
+        nb = int(self.lib.hq_group_arena_bytes(self._arr, len(self.engines)))
+        if nb == 0:
+            raise HQError("invalid engine group")
+        dev = self.engines[0].arena.device
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        self.arena = torch.empty(nb + 256, dtype=torch.uint8, device=dev)
+        base = (self.arena.data_ptr() + 255) // 256 * 256
+        self._h = ctypes.c_void_p()
+        rc = self.lib.hq_group_create(self._arr, len(self.engines), ctypes.c_void_p(base), nb,
+                                      ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._h))
+        if rc != HQ_OK:
+            raise HQError(f"hq_group_create failed ({rc})")
+
+    def sweep(self, n=1, local=True, global_=True, measure=True):
+        flags = (HQ_LOCAL if local else 0) | (HQ_GLOBAL if global_ else 0) | (HQ_MEASURE if measure else 0)
+        rc = self.lib.hq_group_sweep(self._h, int(n), flags)
+        if rc != HQ_OK:
+            raise HQError(f"hq_group_sweep failed ({rc})")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self.lib.hq_group_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 NOALLOC_SCRATCH_BYTES = 64 << 20

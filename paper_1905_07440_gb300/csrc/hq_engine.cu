@@ -2,6 +2,7 @@
 // kinetic propagators, the sweep schedule, copies in and out, checkpoints, tau_int.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -1144,6 +1145,164 @@ int hq_get_learned_stats(hq_engine* e, hq_learned_stats* out) {
     out[c] = hq_learned_stats{k[0], k[1], k[2], k[3], k[4], k[5], pc[c]};
   }
   return HQ_OK;
+}
+
+// ----------------------------------------------------------------- engine groups
+struct hq_group {
+  std::vector<hq_engine*> eng;
+  hq::GroupDev g{};
+  cudaStream_t stream = nullptr;
+  int lmax = 2;
+  size_t sb = 0;
+  std::vector<cudaEvent_t> ev;  // [n_eng + 1]: engine streams -> group, group -> engines
+  ~hq_group() {
+    for (auto x : ev)
+      if (x) cudaEventDestroy(x);
+  }
+};
+
+namespace {
+struct GroupLayout {
+  size_t devs, tasks, sched, total;
+  int n_tasks;
+};
+
+// FP64 flop estimate of one chain-sweep (orders the task table; only ratios matter): stack
+// build, local chunks (wraps, flushes, restabilisations), block moves (a stabilised
+// determinant per site)
+double group_chain_cost(const hq_engine* e) {
+  const double n = e->d.n, n3 = n * n * n, L = e->d.L;
+  const double Q = (e->d.L + e->d.n_wrap - 1) / e->d.n_wrap;
+  return Q * 6.0 * n3 + L * 8.0 * n3 + n * Q * 6.0 * n3;
+}
+
+const char* group_check(hq_engine* const* engines, int n_engines) {
+  if (!engines || n_engines < 1 || n_engines > hq::kGroupMaxEngines) return "1..64 engines";
+  for (int a = 0; a < n_engines; ++a) {
+    if (!engines[a]) return "null engine";
+    if (engines[a]->d.n_chains > 65535) return "engine too large for a group";
+    for (int b = 0; b < a; ++b)
+      if (engines[a] == engines[b]) return "an engine appears twice";
+  }
+  return nullptr;
+}
+
+GroupLayout group_layout(hq_engine* const* engines, int n_engines) {
+  GroupLayout l{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes); return o; };
+  for (int a = 0; a < n_engines; ++a) l.n_tasks += engines[a]->d.n_chains;
+  l.devs = take(sizeof(hq::Dev) * n_engines);
+  l.tasks = take(sizeof(uint32_t) * (size_t)l.n_tasks);
+  l.sched = take(sizeof(int) * hq::kSchedHeader);
+  l.total = off;
+  return l;
+}
+}  // namespace
+
+size_t hq_group_arena_bytes(hq_engine* const* engines, int n_engines) {
+  if (group_check(engines, n_engines)) return 0;
+  return group_layout(engines, n_engines).total;
+}
+
+int hq_group_create(hq_engine* const* engines, int n_engines, void* device_arena, size_t arena_bytes, void* stream,
+                    hq_group** out) {
+  if (!out) return HQ_EINVAL;
+  *out = nullptr;
+  if (const char* why = group_check(engines, n_engines)) {
+    std::fprintf(stderr, "hq_group_create: %s\n", why);
+    return HQ_EINVAL;
+  }
+  const GroupLayout l = group_layout(engines, n_engines);
+  if (!device_arena || arena_bytes < l.total || ((uintptr_t)device_arena % kAlign) != 0) return HQ_ENOMEM;
+  hq_group* g = new (std::nothrow) hq_group();
+  if (!g) return HQ_ENOMEM;
+  g->eng.assign(engines, engines + n_engines);
+  g->stream = (cudaStream_t)stream;
+  char* a = (char*)device_arena;
+  std::vector<hq::Dev> devs(n_engines);
+  for (int e = 0; e < n_engines; ++e) {
+    const hq::Dev& d = engines[e]->d;
+    devs[e] = d;
+    const int lm = hq::lmax_class(d.nx, d.ny);
+    g->lmax = lm > g->lmax ? lm : g->lmax;
+    const size_t sb = hq::smem_bytes(d);
+    g->sb = sb > g->sb ? sb : g->sb;
+  }
+  // task table: every chain, longest estimated sweep first (longest-processing-time order)
+  struct Item { double cost; uint32_t w; };
+  std::vector<Item> items;
+  items.reserve(l.n_tasks);
+  for (int e = 0; e < n_engines; ++e)
+    for (int c = 0; c < engines[e]->d.n_chains; ++c)
+      items.push_back({group_chain_cost(engines[e]), ((uint32_t)e << 26) | (uint32_t)c});
+  std::stable_sort(items.begin(), items.end(), [](const Item& x, const Item& y) { return x.cost > y.cost; });
+  std::vector<uint32_t> tasks(items.size());
+  for (size_t k = 0; k < items.size(); ++k) tasks[k] = items[k].w;
+  g->g.devs = (const hq::Dev*)(a + l.devs);
+  g->g.tasks = (const uint32_t*)(a + l.tasks);
+  g->g.sched = (int*)(a + l.sched);
+  g->g.n_eng = n_engines;
+  g->g.n_tasks = l.n_tasks;
+  cudaError_t st = cudaMemcpyAsync(a + l.devs, devs.data(), sizeof(hq::Dev) * n_engines, cudaMemcpyHostToDevice,
+                                   g->stream);
+  if (st == cudaSuccess)
+    st = cudaMemcpyAsync(a + l.tasks, tasks.data(), sizeof(uint32_t) * tasks.size(), cudaMemcpyHostToDevice,
+                         g->stream);
+  if (st == cudaSuccess) st = cudaStreamSynchronize(g->stream);
+  g->ev.assign(n_engines + 1, nullptr);
+  for (int k = 0; k <= n_engines && st == cudaSuccess; ++k)
+    st = cudaEventCreateWithFlags(&g->ev[k], cudaEventDisableTiming);
+  if (st != cudaSuccess) {
+    std::fprintf(stderr, "hq_group_create: %s\n", cudaGetErrorString(st));
+    delete g;
+    return HQ_ECUDA;
+  }
+  *out = g;
+  return HQ_OK;
+}
+
+void hq_group_destroy(hq_group* g) { delete g; }
+
+int hq_group_sweep(hq_group* g, int n_sweeps, unsigned flags) {
+  if (!g || n_sweeps < 0 || (flags & ~(HQ_LOCAL | HQ_GLOBAL | HQ_MEASURE))) return HQ_EINVAL;
+  const bool do_local = flags & HQ_LOCAL, do_global = flags & HQ_GLOBAL;
+  const int E = (int)g->eng.size();
+  hq_engine* e0 = g->eng[0];
+  // order after the engines' own streams
+  for (int e = 0; e < E; ++e) {
+    int rc = cuda_check(e0, cudaEventRecord(g->ev[e], g->eng[e]->stream), "group event");
+    rc = rc ? rc : cuda_check(e0, cudaStreamWaitEvent(g->stream, g->ev[e], 0), "group wait");
+    if (rc) return rc;
+  }
+  int rc = HQ_OK;
+  for (int it = 0; it < n_sweeps && rc == HQ_OK; ++it) {
+    bool need_stack = false;
+    int n_active = 0;
+    for (hq_engine* e : g->eng) {
+      if ((do_local || !e->logdet_valid) && !e->stack_valid) need_stack = true;
+      n_active += e->d.n_active;
+    }
+    // a stack build of an engine whose state is current recomputes the same values
+    rc = cuda_check(e0, cudaMemsetAsync(g->g.sched, 0, sizeof(int) * hq::kSchedHeader, g->stream), "group sched");
+    rc = rc ? rc : cuda_check(e0, hq::launch_group_sweep(g->g, g->lmax, g->sb, n_active, (int)flags,
+                                                         need_stack ? 1 : 0, g->stream), "group sweep");
+    if (rc) break;
+    for (hq_engine* e : g->eng) {
+      if (need_stack) e->stack_valid = e->logdet_valid = e->green_valid = true;
+      if (do_local) {
+        e->stack_valid = false;
+        e->logdet_valid = e->green_valid = true;
+      }
+      if (do_global) e->stack_valid = e->green_valid = false;
+      e->sweeps++;
+    }
+  }
+  // the engines' later calls on their own streams follow the group's work
+  int rc2 = cuda_check(e0, cudaEventRecord(g->ev[E], g->stream), "group event");
+  for (int e = 0; e < E && rc2 == HQ_OK; ++e)
+    rc2 = cuda_check(e0, cudaStreamWaitEvent(g->eng[e]->stream, g->ev[E], 0), "engine wait");
+  return rc ? rc : rc2;
 }
 
 size_t hq_autotune_arena_bytes(const hq_params* p, int n_chains, const int* ks, int n_k) {

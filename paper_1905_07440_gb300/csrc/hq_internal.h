@@ -64,6 +64,16 @@ struct Dev {
   double* corr;       // [C][2 N L + L] correction vectors of every chunk, shifted diagonal
 };
 
+// A heterogeneous group of engines swept together (device copy of each engine's
+// descriptor; task table of chain-sweeps, entry = engine << 26 | chain, longest first).
+constexpr int kGroupMaxEngines = 64;
+struct GroupDev {
+  const Dev* devs;        // [n_eng]
+  const uint32_t* tasks;  // [n_tasks]
+  int* sched;             // [kSchedHeader] task counter
+  int n_eng, n_tasks;
+};
+
 // FP64 flop model of one chunk of a block move: n_wrap separable slice applications versus
 // the chunk-propagator update (rank-m correction vectors, rank-m update, one GEMM).
 inline bool chunk_propagators_pay(int nx, int ny, int L, int n_wrap) {
@@ -168,6 +178,11 @@ cudaError_t cnn_launch_batch(const Dev& d, const CnnState& cn, const double* Xs,
 cudaError_t cnn_launch_loss(const CnnState& cn, const double* ys, const int* idx, int B, double scale,
                             double* loss, cudaStream_t s);
 int section_cycles(unsigned long long* out, int n);
+int lmax_class(int nx, int ny);
+// One persistent launch sweeping every chain of a group (flags as hq_sweep; stack != 0 runs
+// the stack build first).
+cudaError_t launch_group_sweep(const GroupDev& g, int lmax, size_t sb, int n_active, int flags, int stack,
+                               cudaStream_t s);
 size_t noalloc_scratch_needed(int nx, int ny, int n_chains);
 // log|det M| per chain with all scratch in the library's static device array (no allocation).
 cudaError_t launch_logdet_noalloc(Dev d, const double* kin_host, double* out, cudaStream_t s);

@@ -187,9 +187,7 @@ __device__ double udv_top_down(const Dev& d, int c, const Smem& sm, const double
 }
 
 template <int LMAX>
-__global__ void __launch_bounds__(HQ_THREADS) stack_build_kernel(Dev d) {
-  extern __shared__ double smraw[];
-  const int c = blockIdx.x;
+__device__ void stack_build_body(const Dev& d, int c, double* smraw) {
   if (!d.active[c]) return;
   const Smem sm = carve(d, smraw);
   load_kinetic(d, sm);
@@ -200,6 +198,12 @@ __global__ void __launch_bounds__(HQ_THREADS) stack_build_kernel(Dev d) {
     d.logdet[c] = ld;
     flag_nonfinite(d, c, ld);
   }
+}
+
+template <int LMAX>
+__global__ void __launch_bounds__(HQ_THREADS) stack_build_kernel(Dev d) {
+  extern __shared__ double smraw[];
+  stack_build_body<LMAX>(d, blockIdx.x, smraw);
 }
 
 // Fresh G_l at boundary l from the right factors (B_l..B_1 = UR DR TR) and, if l < L,
@@ -293,10 +297,7 @@ __device__ void measure_green(const Dev& d, int c, const Smem& sm, const double*
 }
 
 template <int LMAX>
-__global__ void __launch_bounds__(HQ_THREADS)
-local_chunk_kernel(Dev d, int s0, int s1, int measure) {
-  extern __shared__ double smraw[];
-  const int c = blockIdx.x;
+__device__ void local_chunk_body(const Dev& d, int c, int s0, int s1, int measure, double* smraw) {
   if (!d.active[c]) return;
   const int n = d.n, L = d.L, k = d.k;
   const Smem sm = carve(d, smraw);
@@ -470,6 +471,12 @@ local_chunk_kernel(Dev d, int s0, int s1, int measure) {
   HQ_TIC(ms);
   if (measure) measure_green(d, c, sm, G);
   HQ_TOC(ms, SEC_MEASURE);
+}
+
+template <int LMAX>
+__global__ void __launch_bounds__(HQ_THREADS) local_chunk_kernel(Dev d, int s0, int s1, int measure) {
+  extern __shared__ double smraw[];
+  local_chunk_body<LMAX>(d, blockIdx.x, s0, s1, measure, smraw);
 }
 
 // -------------------------------------------- block moves with chunk propagators
@@ -782,9 +789,7 @@ __global__ void __launch_bounds__(HQ_THREADS) global_phase_kernel(Dev d) {
   }
 }
 
-__global__ void __launch_bounds__(HQ_THREADS) sweep_end_kernel(Dev d, int measured) {
-  __shared__ double red[HQ_WARPS];
-  const int c = blockIdx.x;
+__device__ void sweep_end_body(const Dev& d, int c, int measured, double* red) {
   if (!d.active[c]) return;
   const int n = d.n, L = d.L;
   const double* X = d.X + (size_t)c * L * n;
@@ -826,6 +831,58 @@ __global__ void __launch_bounds__(HQ_THREADS) sweep_end_kernel(Dev d, int measur
     tot[TOT_SWEEPS] += 1.0;
     tot[TOT_WRAP] = fmax(tot[TOT_WRAP], acc[ACC_WRAP]);
     for (int o = 0; o < kAccSlots; ++o) acc[o] = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(HQ_THREADS) sweep_end_kernel(Dev d, int measured) {
+  __shared__ double red[HQ_WARPS];
+  sweep_end_body(d, blockIdx.x, measured, red);
+}
+
+// ------------------------------------------------ heterogeneous groups of engines
+// Engines of different lattices, temperatures and couplings swept together by ONE persistent
+// launch.  A chain's sweep is sequential (stack build, local chunks, block moves, records),
+// so the unit of work is a whole chain-sweep: workers take chains from the group's table --
+// sorted by estimated cost, longest first, so the long chains start at once and the short
+// ones fill in around them -- and run every step of the chain.  No worker ever waits for
+// another.  Kernels are instantiated for the largest lattice side of the group (the separable
+// propagator's arithmetic does not depend on it) and take the largest shared-memory carve.
+template <int LMAX>
+__global__ void __launch_bounds__(HQ_THREADS) group_sweep_kernel(GroupDev g, int flags, int stack) {
+  extern __shared__ double smraw[];
+  __shared__ int s_task;
+  __shared__ Dev sd;
+  const bool do_local = flags & HQ_LOCAL, do_global = flags & HQ_GLOBAL, meas = flags & HQ_MEASURE;
+  int cur = -1;
+  Smem sm{};
+  for (;;) {
+    if (threadIdx.x == 0) s_task = atomicAdd(g.sched, 1);
+    __syncthreads();
+    const int t = s_task;
+    __syncthreads();  // every thread has read s_task before the next iteration overwrites it
+    if (t >= g.n_tasks) break;
+    const uint32_t w = g.tasks[t];
+    const int e = (int)(w >> 26), c = (int)(w & 0xffffu);
+    if (e != cur) {
+      if (threadIdx.x == 0) sd = g.devs[e];
+      __syncthreads();
+      sm = carve(sd, smraw);
+      load_kinetic(sd, sm);
+      cur = e;
+    }
+    if (!sd.active[c]) continue;
+    if (stack) stack_build_body<LMAX>(sd, c, smraw);
+    if (do_local)
+      for (int s0 = 0; s0 < sd.L; s0 += sd.n_wrap) {
+        const int s1 = s0 + sd.n_wrap < sd.L ? s0 + sd.n_wrap : sd.L;
+        local_chunk_body<LMAX>(sd, c, s0, s1, meas ? 1 : 0, smraw);
+      }
+    if (do_global) {
+      if (sd.use_cm) build_chunks<LMAX>(sd, sm, c);
+      for (int site = 0; site < sd.n; ++site) block_move<LMAX>(sd, sm, c, site);
+    }
+    sweep_end_body(sd, c, (meas && do_local) ? 1 : 0, sm.red);
+    __syncthreads();
   }
 }
 
@@ -1051,6 +1108,37 @@ cudaError_t launch_global_phase(const Dev& d, cudaStream_t s) {
     case 4: return launch_phase<4>(d, s);
     case 8: return launch_phase<8>(d, s);
     default: return launch_phase<16>(d, s);
+  }
+}
+
+// ---- group launcher (lmax: largest lattice side class of the group; sb: largest carve).
+// The caller zeroes the group's task counter first.
+int lmax_class(int nx, int ny) { return lmax_of(nx, ny); }
+
+template <int LMAX>
+static cudaError_t launch_group_t(const GroupDev& g, size_t sb, int n_active, int flags, int stack, cudaStream_t s) {
+  allow_smem(group_sweep_kernel<LMAX>, sb);
+  int dev = 0, sms = 0, occ = 0;
+  cudaError_t st = cudaGetDevice(&dev);
+  if (st == cudaSuccess) st = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (st == cudaSuccess)
+    st = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, group_sweep_kernel<LMAX>, HQ_THREADS, sb);
+  if (st != cudaSuccess) return st;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  int workers = sms * (occ < kWorkersPerSm ? occ : kWorkersPerSm);
+  if (workers > n_active) workers = n_active;
+  if (workers < 1) workers = 1;
+  group_sweep_kernel<LMAX><<<workers, HQ_THREADS, sb, s>>>(g, flags, stack);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_sweep(const GroupDev& g, int lmax, size_t sb, int n_active, int flags, int stack,
+                               cudaStream_t s) {
+  switch (lmax) {
+    case 2: return launch_group_t<2>(g, sb, n_active, flags, stack, s);
+    case 4: return launch_group_t<4>(g, sb, n_active, flags, stack, s);
+    case 8: return launch_group_t<8>(g, sb, n_active, flags, stack, s);
+    default: return launch_group_t<16>(g, sb, n_active, flags, stack, s);
   }
 }
 
