@@ -668,6 +668,106 @@ def run_hetero(args):
     return 0
 
 
+PHYSICS_SIDES = ((4, 48), (6, 48), (8, 32), (10, 16), (12, 16))
+PHYSICS_OBS_SIDES = (4, 6, 8, 10)  # observables; 12x12 (2.7 s per chain-sweep) is timed only
+
+
+def physics_params(side, seed):
+    """The paper's benchmark point: Omega = t/2, lambda = g^2/(M Omega^2 8t) = 1/2 (g = 1),
+    half filling mu = -g^2/(M Omega^2) = -4, beta = 4.1 (its T_c), dtau = 0.1 (L = 41)."""
+    return workloads.HolsteinParams(nx=side, ny=side, omega=0.5, g=1.0, mu=-4.0, beta=4.1, seed=seed)
+
+
+def run_physics(args):
+    """The paper's physics point on lattice sides 4..12: S_CDW(pi,pi), <n>, <X> from one
+    heterogeneous group (all sizes in one persistent launch), and the GPU time of one
+    chain-sweep against N with its power-law exponent (the paper fits CPU time ~ N^z)."""
+    import numpy as np
+    import torch
+    import paper_1905_07440_gb300 as hq
+    W, M = args.warmup, args.steps
+    engines = []
+    for k, (side, C) in enumerate(PHYSICS_SIDES):
+        p = physics_params(side, workloads.BATCHED.seed + 31 * k)
+        e = hq.Engine(p, C, max_series=W + M)
+        # start at the mean field <X> = -g/(M Omega^2) = -4 with the free-phonon spread: from
+        # X ~ N(0, 4) the block moves' random walk needs hundreds of sweeps to get there
+        x0 = -p.g / (p.mass * p.omega ** 2)
+        e.set_fields(workloads.initial_fields(p, C, seed=100 + k) + x0)
+        engines.append(e)
+    obs_engines = [e for (side, _), e in zip(PHYSICS_SIDES, engines) if side in PHYSICS_OBS_SIDES]
+    grp = hq.Group(obs_engines)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    grp.sweep(W + M)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    obs = {}
+    for (side, C), e in zip(PHYSICS_SIDES, engines):
+        if side not in PHYSICS_OBS_SIDES:
+            continue
+        row = {"chains": C}
+        for oid, name in ((hq.HQ_OBS_SCDW, "s_cdw"), (hq.HQ_OBS_DENSITY, "density"), (hq.HQ_OBS_X_MEAN, "x_mean"),
+                          (hq.HQ_OBS_DOUBLE_OCC, "double_occ")):
+            pc = e.series(oid)[:, W:].mean(axis=1)
+            row[name] = [float(pc.mean()), float(pc.std(ddof=1) / math.sqrt(C))]
+        row["status_ok"] = all(o["status"] == 0 for o in e.observables())
+        obs[f"{side}x{side}"] = row
+    grp.close()
+    # time of one chain-sweep per lattice (each engine alone, one chain per SM)
+    times = {}
+    for k, (side, C) in enumerate(PHYSICS_SIDES):
+        e = engines[k]
+        e.sweep(1)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        e.sweep(2)
+        torch.cuda.synchronize()
+        times[side] = (time.perf_counter() - t1) / 2
+    Ns = np.array([s * s for s, _ in PHYSICS_SIDES], dtype=float)
+    ts = np.array([times[s] for s, _ in PHYSICS_SIDES])
+    z = float(np.polyfit(np.log(Ns), np.log(ts), 1)[0])
+    z_big = float(np.polyfit(np.log(Ns[-3:]), np.log(ts[-3:]), 1)[0])
+    line = {"mode": "physics point", "metric": "S_CDW(pi,pi) vs lattice; seconds per chain-sweep vs N",
+            "config": {"workload": "Omega=0.5, lambda=0.5 (g=1), mu=-4, beta=4.1, dtau=0.1 (L=41), "
+                                   "full sweeps (local moves + a block move per site); fields start at "
+                                   "-g/(M Omega^2) + N(0, 1/(M Omega^2))",
+                       "warmup_sweeps": W, "measured_sweeps": M, "data": "synthetic"},
+            "group_wall_s": wall, "observables": obs,
+            "seconds_per_chain_sweep": {f"{s}x{s}": times[s] for s, _ in PHYSICS_SIDES},
+            "z_fit_all": z, "z_fit_8_to_12": z_big,
+            "paper_context": "CPU time ~ N^z with z = 3.41 (DQMC) and 2.35 (NN-accelerated), hardware unstated"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_graphs(args):
+    """Launch cost: sweeps of small lattices, eager launches against CUDA-graph replay
+    (hq_set_graphs); host wall clock over args.steps sweeps after args.warmup."""
+    import torch
+    import paper_1905_07440_gb300 as hq
+    out = {"mode": "graph replay", "metric": "sweeps/s (engine)", "cases": {}}
+    for name, shape, C in (("4x4 beta=1", dict(nx=4, ny=4, beta=1.0), 1), ("4x4 beta=1", dict(nx=4, ny=4, beta=1.0), 64),
+                           ("8x8 beta=1", dict(nx=8, ny=8, beta=1.0), 64)):
+        p = workloads.HolsteinParams(**shape)
+        row = {}
+        for graphs in (False, True):
+            eng = hq.Engine(p, C, stream=torch.cuda.Stream())
+            eng.set_fields(workloads.initial_fields(p, C))
+            eng.set_graphs(graphs)
+            eng.sweep(max(args.warmup, 3))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            eng.sweep(args.steps)
+            torch.cuda.synchronize()
+            row["graph" if graphs else "eager"] = args.steps / (time.perf_counter() - t0)
+            eng.close()
+        row["speedup"] = row["graph"] / row["eager"]
+        out["cases"][f"{name} x{C} chains"] = row
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_autotune(args):
     """Autotuner table (ms per sweep for every delay rank and block-move method) on the
     batched workload (full sweeps) and on the largest lattice (local sweeps only: a full sweep
@@ -688,6 +788,103 @@ def run_autotune(args):
                                "seconds": time.perf_counter() - t0}
         del X
     print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_largest_learned(args):
+    """Learned vs plain at the largest lattice, 16x16, beta = 16 (L = 160), 64 chains.
+
+    The patch network is local, so it is trained where samples are cheap -- 8x8 at the same
+    beta and couplings, 256 chains of the plain sampler -- and deployed at 16x16.  Plain
+    comparison: local sweeps only (a full sweep with a block move per site costs 256 stabilised
+    determinants per chain, minutes per sweep at this size; its cost is stated from the
+    measured block-move rate, not run).  Both samplers start at the mean field with the
+    free-phonon spread; tau_int from the measured part of each run.
+    """
+    import numpy as np
+    import torch
+    import paper_1905_07440_gb300 as hq
+    big = workloads.LARGEST
+    C = args.chains or 64
+    small = big.with_(nx=8, ny=8)
+    x0 = -big.g / (big.mass * big.omega ** 2)
+    dev = torch.device("cuda", 0)
+    t_all = time.perf_counter()
+    # training data at 8x8
+    eng = hq.Engine(small, 256)
+    eng.set_fields(workloads.initial_fields(small, 256) + x0)
+    eng.sweep(args.train_warmup, local=True, global_=True)
+    Xs, ys = [], []
+    for _ in range(args.train_snapshots):
+        eng.sweep(2)
+        Xs.append(eng.get_fields())
+        ys.append(eng.log_weight()[1])
+    eng.close()
+    Xtr, ytr = np.concatenate(Xs), np.concatenate(ys)
+    ytr -= ytr.mean()
+    net = hq.Engine(small, 1)
+    net.attach_network(64, Xtr.shape[0])
+    net.set_params(hq.init_network(args.nn_seed))
+    Xd, yd = torch.from_numpy(Xtr).to(dev), torch.from_numpy(ytr).to(dev)
+    losses = []
+    for k in range(3):
+        ep = args.epochs // 3 + (args.epochs % 3 if k == 2 else 0)
+        losses.extend(net.nn_train(Xd, yd, epochs=ep, batch=64, lr=args.lr * 0.5 ** k, seed=args.nn_seed + k))
+    theta = net.get_params()
+    del Xd, yd
+    net.close()
+    W, M = args.warmup, args.tau_steps
+    X0 = workloads.initial_fields(big, C, seed=7) + x0
+    series_ids = ((hq.HQ_OBS_X2, "x2"), (hq.HQ_OBS_DOUBLE_OCC, "double_occ"), (hq.HQ_OBS_SCDW, "s_cdw"))
+
+    def tau_block(e, first):
+        out = {}
+        for oid, name in series_ids:
+            ser = e.series(oid)[:, first:]
+            out[name] = (float(np.mean([hq.tau_int(ser[c])[0] for c in range(C)])), float(ser.mean()))
+        return out
+
+    # learned sampler
+    lrn = hq.Engine(big, C, max_series=W + M)
+    lrn.attach_network(4, 8)
+    lrn.set_params(theta)
+    lrn.set_fields(X0)
+    lrn.cumulative(W, args.n_inner, measure=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lrn.cumulative(M, args.n_inner, measure=True)
+    torch.cuda.synchronize()
+    l_rate = C * M / (time.perf_counter() - t0)
+    st = lrn.learned_stats()
+    acc = sum(x["cumulative_accepted"] for x in st) / max(1, sum(x["cumulative_proposed"] for x in st))
+    l_tau = tau_block(lrn, W)
+    lrn.close()
+    # plain sampler, local sweeps
+    pl = hq.Engine(big, C, max_series=W + M)
+    pl.set_fields(X0)
+    pl.sweep(W, global_=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pl.sweep(M, global_=False)
+    torch.cuda.synchronize()
+    p_rate = C * M / (time.perf_counter() - t0)
+    p_tau = tau_block(pl, W)
+    pl.close()
+    gain = {k: (l_rate / (2 * l_tau[k][0])) / (p_rate / (2 * p_tau[k][0])) for k in l_tau}
+    line = {"metric": METRIC, "mode": "learned vs plain, largest lattice",
+            "value": l_rate / (2 * l_tau["s_cdw"][0]), "unit": "independent samples/s of S_CDW(pi,pi) (learned)",
+            "higher_is_better": True, "dtype": "f64 weights, bf16-weight/fp32 network", "data": "synthetic",
+            "config": {"workload": "16x16 beta=16 L=160, g=sqrt2, mu=-2", "chains": C, "warmup": W, "measured": M,
+                       "network": "patch network trained at 8x8 beta=16 (%d samples, %d epochs)"
+                                  % (Xtr.shape[0], args.epochs),
+                       "plain": "local sweeps (no block moves)"},
+            "learned": {"steps_per_s": l_rate, "cumulative_acceptance": acc,
+                        "tau_int_and_mean": l_tau},
+            "plain": {"sweeps_per_s": p_rate, "tau_int_and_mean": p_tau},
+            "gain_indep_samples": gain,
+            "training_loss": [float(losses[0]), float(losses[-1]), float(np.var(ytr))],
+            "wall_s": time.perf_counter() - t_all}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -757,6 +954,8 @@ def main():
         os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     if args.workload == "learned":
         sys.exit(run_learned(args))
+    if args.workload == "largest-learned":
+        sys.exit(run_largest_learned(args))
     if args.workload == "serving":
         sys.exit(run_serving(args))
     if args.peaks:
@@ -765,6 +964,10 @@ def main():
         sys.exit(run_autotune(args))
     if args.workload == "hetero":
         sys.exit(run_hetero(args))
+    if args.workload == "graphs":
+        sys.exit(run_graphs(args))
+    if args.workload == "physics":
+        sys.exit(run_physics(args))
     if args.tau_sweeps:
         sys.exit(run_tau(args))
     if args.warmup < 3 and args.impl == "ours":

@@ -229,6 +229,15 @@ double hq_tau_int(const double* series, int n, double c, int* window);
  * phase is one persistent launch per sweep (N x n_chains moves). */
 #define HQ_N_PHASES 4
 int hq_set_timing(hq_engine* e, int enable);
+
+/* CUDA-graph replay of sweeps (no counterpart in the paper; it trims the host's launch cost,
+ * which matters for small lattices whose sweeps take a few milliseconds).  With enable != 0,
+ * hq_sweep runs the first sweep of each shape eagerly, captures the next one on the engine's
+ * stream and replays the captured graph for later sweeps of the same shape (flags, whether the
+ * state must be rebuilt first, number of active slots).  Results are identical to eager
+ * sweeps.  Needs a stream created by the caller (not stream 0); per-phase timing
+ * (hq_set_timing) runs sweeps eagerly.  Errors: HQ_EINVAL for a null engine or stream 0. */
+int hq_set_graphs(hq_engine* e, int enable);
 int hq_get_timing(hq_engine* e, double* ms, int64_t* launches);
 
 /* log|det M| of every chain's fields, with no device allocation of any kind.

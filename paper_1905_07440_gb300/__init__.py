@@ -92,6 +92,7 @@ _SIGNATURES = {
     "hq_tau_int": (ctypes.c_double, [_dp, ctypes.c_int, ctypes.c_double, _P(ctypes.c_int)]),
     "hq_fp64_peak_tflops": (ctypes.c_double, [ctypes.c_int, ctypes.c_int, _vp]),
     "hq_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "hq_set_graphs": (ctypes.c_int, [_vp, ctypes.c_int]),
     "hq_logdet_noalloc": (ctypes.c_int, [_P(hq_params), ctypes.c_int, _vp, _vp, _vp]),
     "hq_nn_arena_bytes": (ctypes.c_size_t, [_vp, ctypes.c_int, ctypes.c_int]),
     "hq_nn_attach": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int]),
@@ -265,6 +266,10 @@ class Engine:
     def restore(self, blob):
         buf = ctypes.create_string_buffer(blob, len(blob))
         self._check(self.lib.hq_restore(self._h, buf, len(blob)), "hq_restore")
+
+    def set_graphs(self, enable=True):
+        """Replay sweeps from a captured CUDA graph (needs a non-default stream)."""
+        self._check(self.lib.hq_set_graphs(self._h, 1 if enable else 0), "hq_set_graphs")
 
     def set_timing(self, enable=True):
         self._check(self.lib.hq_set_timing(self._h, 1 if enable else 0), "hq_set_timing")

@@ -34,6 +34,10 @@ struct hq_engine {
   // optional per-phase timing
   struct Span { cudaEvent_t a, b; int phase, launches; };
   bool timing = false;
+  // optional CUDA-graph replay of whole sweeps (key: flags, stack build needed, active slots)
+  bool graphs = false;
+  cudaGraphExec_t gexec = nullptr;
+  long long gkey = -1, gwarm = -1;
   std::vector<Span> spans;
   std::vector<cudaEvent_t> spare;
   double phase_ms[HQ_N_PHASES] = {0, 0, 0, 0};
@@ -49,6 +53,7 @@ struct hq_engine {
   ~hq_engine() {
     for (auto& s : spans) { cudaEventDestroy(s.a); cudaEventDestroy(s.b); }
     for (auto ev : spare) cudaEventDestroy(ev);
+    if (gexec) cudaGraphExecDestroy(gexec);
   }
 };
 
@@ -347,38 +352,115 @@ int hq_get_fields(hq_engine* e, double* X_host) {
   return rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "get_fields sync");
 }
 
-int hq_sweep(hq_engine* e, int n_sweeps, unsigned flags) {
-  if (!e || n_sweeps < 0 || (flags & ~(HQ_LOCAL | HQ_GLOBAL | HQ_MEASURE))) return HQ_EINVAL;
+namespace {
+// One sweep: launches on the engine's stream and the host-side state changes.
+int sweep_once(hq_engine* e, unsigned flags) {
   const bool do_local = flags & HQ_LOCAL, do_global = flags & HQ_GLOBAL, meas = flags & HQ_MEASURE;
   const hq::Dev& d = e->d;
-  for (int it = 0; it < n_sweeps; ++it) {
-    int rc = HQ_OK;
-    if (do_local || !e->logdet_valid) rc = ensure_state(e);
-    if (rc) return rc;
-    if (do_local) {
-      PhaseTimer pt(e, 1, (d.L + d.n_wrap - 1) / d.n_wrap);
-      for (int s0 = 0; s0 < d.L; s0 += d.n_wrap) {
-        const int s1 = s0 + d.n_wrap < d.L ? s0 + d.n_wrap : d.L;
-        rc = cuda_check(e, hq::launch_local_chunk(d, s0, s1, meas ? 1 : 0, e->stream), "local_chunk launch");
-        if (rc) return rc;
-      }
-      e->stack_valid = false;  // fields changed; G_0 and log|det M| are fresh (restabilised at l = L)
-      e->logdet_valid = e->green_valid = true;
-    }
-    if (do_global) {
-      PhaseTimer pt(e, 2, 1);
-      rc = cuda_check(e, hq::launch_global_phase(d, e->stream), "global_phase launch");
+  int rc = HQ_OK;
+  if (do_local || !e->logdet_valid) rc = ensure_state(e);
+  if (rc) return rc;
+  if (do_local) {
+    PhaseTimer pt(e, 1, (d.L + d.n_wrap - 1) / d.n_wrap);
+    for (int s0 = 0; s0 < d.L; s0 += d.n_wrap) {
+      const int s1 = s0 + d.n_wrap < d.L ? s0 + d.n_wrap : d.L;
+      rc = cuda_check(e, hq::launch_local_chunk(d, s0, s1, meas ? 1 : 0, e->stream), "local_chunk launch");
       if (rc) return rc;
-      e->stack_valid = false;
-      e->green_valid = false;  // log|det M| is kept current by the accepted moves
     }
-    {
-      PhaseTimer pt(e, 3, 1);
-      rc = cuda_check(e, hq::launch_sweep_end(d, (meas && do_local) ? 1 : 0, e->stream), "sweep_end launch");
+    e->stack_valid = false;  // fields changed; G_0 and log|det M| are fresh (restabilised at l = L)
+    e->logdet_valid = e->green_valid = true;
+  }
+  if (do_global) {
+    PhaseTimer pt(e, 2, 1);
+    rc = cuda_check(e, hq::launch_global_phase(d, e->stream), "global_phase launch");
+    if (rc) return rc;
+    e->stack_valid = false;
+    e->green_valid = false;  // log|det M| is kept current by the accepted moves
+  }
+  {
+    PhaseTimer pt(e, 3, 1);
+    rc = cuda_check(e, hq::launch_sweep_end(d, (meas && do_local) ? 1 : 0, e->stream), "sweep_end launch");
+  }
+  if (rc) return rc;
+  e->sweeps++;
+  return HQ_OK;
+}
+
+// The host-side state changes of sweep_once without its launches (graph replay).
+void sweep_state(hq_engine* e, unsigned flags) {
+  if ((flags & HQ_LOCAL) || !e->logdet_valid) {
+    if (!e->stack_valid) e->stack_valid = e->logdet_valid = e->green_valid = true;
+  }
+  if (flags & HQ_LOCAL) {
+    e->stack_valid = false;
+    e->logdet_valid = e->green_valid = true;
+  }
+  if (flags & HQ_GLOBAL) e->stack_valid = e->green_valid = false;
+  e->sweeps++;
+}
+
+void drop_graph(hq_engine* e) {
+  if (e->gexec) cudaGraphExecDestroy(e->gexec);
+  e->gexec = nullptr;
+  e->gkey = e->gwarm = -1;
+}
+}  // namespace
+
+int hq_sweep(hq_engine* e, int n_sweeps, unsigned flags) {
+  if (!e || n_sweeps < 0 || (flags & ~(HQ_LOCAL | HQ_GLOBAL | HQ_MEASURE))) return HQ_EINVAL;
+  for (int it = 0; it < n_sweeps; ++it) {
+    if (!e->graphs || e->timing) {
+      const int rc = sweep_once(e, flags);
+      if (rc) return rc;
+      continue;
+    }
+    // graph replay: the launches of one sweep depend on the flags, on whether the state must
+    // be rebuilt first and on the number of active slots (the block-move grid)
+    const bool stack = ((flags & HQ_LOCAL) || !e->logdet_valid) && !e->stack_valid;
+    const long long key = ((long long)e->d.n_active << 8) | ((long long)flags << 1) | (stack ? 1 : 0);
+    if (e->gexec && e->gkey == key) {
+      int rc = cuda_check(e, cudaGraphLaunch(e->gexec, e->stream), "graph launch");
+      if (rc) return rc;
+      sweep_state(e, flags);
+      continue;
+    }
+    if (e->gwarm != key) {
+      // first sweep of this shape runs eagerly (it also sets the kernels' attributes)
+      const int rc = sweep_once(e, flags);
+      if (rc) return rc;
+      e->gwarm = key;
+      continue;
+    }
+    if (e->gexec) cudaGraphExecDestroy(e->gexec);
+    e->gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    int rc = cuda_check(e, cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (rc) return rc;
+    const int rcs = sweep_once(e, flags);  // records the launches and applies the state changes
+    rc = cuda_check(e, cudaStreamEndCapture(e->stream, &graph), "end capture");
+    if (rcs) {
+      if (graph) cudaGraphDestroy(graph);
+      return rcs;
     }
     if (rc) return rc;
-    e->sweeps++;
+    rc = cuda_check(e, cudaGraphInstantiate(&e->gexec, graph, 0), "graph instantiate");
+    cudaGraphDestroy(graph);
+    if (rc) {
+      e->gexec = nullptr;
+      return rc;
+    }
+    e->gkey = key;
+    rc = cuda_check(e, cudaGraphLaunch(e->gexec, e->stream), "graph launch");
+    if (rc) return rc;
   }
+  return HQ_OK;
+}
+
+int hq_set_graphs(hq_engine* e, int enable) {
+  if (!e) return HQ_EINVAL;
+  if (enable && e->stream == nullptr) return set_err(e, HQ_EINVAL, "graph replay needs a created stream, not stream 0");
+  drop_graph(e);
+  e->graphs = enable != 0;
   return HQ_OK;
 }
 
