@@ -61,6 +61,22 @@ def flops_chunk_build(p):
     return p.n_slices * (2.0 * n * n * (p.nx + p.ny) + n * n)
 
 
+def flops_local_phase(p, acc_rate):
+    """FP64 flops of one chain's local phase (L slices, restabilised every n_wrap), for a local
+    acceptance rate acc_rate.  Per slice: the wrap G <- B G B^-1 through the separable
+    propagator on both sides, 2 x 2 N^2 (nx + ny), plus the two diagonal scalings 2 N^2; the
+    delayed-update flushes, 2 N^2 per accepted move (N acc_rate moves).  Per chunk of
+    m <= n_wrap slices: m slice applications to the right factors, m (2 N^2 (nx + ny) + N^2),
+    pre-pivoted QR 4/3 N^3, explicit Q 4/3 N^3, T update N^3, and the two-sided fresh G
+    (products and an LU solve), about 4 N^3.  Proposal arithmetic (O(k) per site) is left out.
+    """
+    n, L, nw = p.n_sites, p.n_slices, p.n_wrap
+    chunks = [min(nw, L - q * nw) for q in range(math.ceil(L / nw))]
+    per_slice = 4.0 * n * n * (p.nx + p.ny) + 2.0 * n * n + 2.0 * n * n * n * acc_rate
+    restab = sum(m * (2.0 * n * n * (p.nx + p.ny) + n * n) + (8.0 / 3.0 + 1.0 + 4.0) * n ** 3 for m in chunks)
+    return L * per_slice + restab
+
+
 # -------------------------------------------------------------- CPU baseline
 def _oracle_worker(args):
     params, chain, n_sweeps = args
@@ -293,6 +309,17 @@ def run_ours(args):
     else:
         fl = None
     achieved = fl / per_launch_s / 1e12 if fl else None
+    # the local phase (wraps, delayed-update flushes, restabilisation) as a second roofline
+    acc_l0 = sum(o["local_accepted"] for o in obs) / max(1, sum(o["local_proposed"] for o in obs))
+    ms_l, n_l = phases.get("local_chunk", (0.0, 0))
+    roof_local = None
+    if n_l:
+        fl_l = chains * flops_local_phase(params, acc_l0)
+        per_sweep_s = ms_l / 1e3 / args.steps
+        roof_local = {"bound": "alu", "kernel": "local_chunk_kernel", "achieved": fl_l / per_sweep_s / 1e12,
+                      "peak": peak, "unit": "TFLOP/s", "frac": fl_l / per_sweep_s / 1e12 / peak,
+                      "flops_per_sweep": fl_l, "launches_per_sweep": n_l / args.steps,
+                      "ms_per_sweep": ms_l / args.steps}
     gpu_launches = sum(n for _, n in phases.values())
     total_ms = sum(m for m, _ in phases.values())
     xbytes = 8 * chains * params.n_slices * params.n_sites
@@ -334,6 +361,7 @@ def run_ours(args):
                      "peak_source": "FP64 DFMA probe measured in this run (hq_fp64_peak_tflops)",
                      "flops_per_launch": fl, "ms_per_launch": per_launch_s * 1e3,
                      "share": ms / total_ms if total_ms else None},
+        "roofline_local": roof_local,
         "phases_ms": {k: v[0] for k, v in phases.items()},
         "indep_samples_per_s": indep,
         "cpu_baseline": cpu,
@@ -796,10 +824,10 @@ def run_largest_learned(args):
 
     The patch network is local, so it is trained where samples are cheap -- 8x8 at the same
     beta and couplings, 256 chains of the plain sampler -- and deployed at 16x16.  Plain
-    comparison: local sweeps only (a full sweep with a block move per site costs 256 stabilised
-    determinants per chain, minutes per sweep at this size; its cost is stated from the
-    measured block-move rate, not run).  Both samplers start at the mean field with the
-    free-phonon spread; tau_int from the measured part of each run.
+    comparison: local sweeps (a full sweep with a block move per site costs 256 stabilised
+    determinants per chain, minutes per sweep at this size; with --plain-full one such sweep is
+    timed and turned into an upper bound on its independent samples/s).  Both samplers start
+    at the mean field with the free-phonon spread; tau_int from the measured part of each run.
     """
     import numpy as np
     import torch
@@ -871,6 +899,23 @@ def run_largest_learned(args):
     p_tau = tau_block(pl, W)
     pl.close()
     gain = {k: (l_rate / (2 * l_tau[k][0])) / (p_rate / (2 * p_tau[k][0])) for k in l_tau}
+    full = None
+    if args.plain_full:
+        # one full sweep (local moves + a block move per site) of 8 chains: per-chain latency
+        fe = hq.Engine(big, 8)
+        fe.set_fields(X0[:8])
+        fe.sweep(1, global_=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fe.sweep(1)
+        torch.cuda.synchronize()
+        t_full = time.perf_counter() - t0
+        fe.close()
+        # even if one full sweep gave an independent sample (tau_int = 1/2 sweep), 64 chains
+        # would give at most this many per second
+        full = {"seconds_per_sweep": t_full, "chains_timed": 8,
+                "indep_samples_per_s_upper_bound": C / t_full,
+                "learned_gain_lower_bound": {k: (l_rate / (2 * l_tau[k][0])) / (C / t_full) for k in l_tau}}
     line = {"metric": METRIC, "mode": "learned vs plain, largest lattice",
             "value": l_rate / (2 * l_tau["s_cdw"][0]), "unit": "independent samples/s of S_CDW(pi,pi) (learned)",
             "higher_is_better": True, "dtype": "f64 weights, bf16-weight/fp32 network", "data": "synthetic",
@@ -881,7 +926,7 @@ def run_largest_learned(args):
             "learned": {"steps_per_s": l_rate, "cumulative_acceptance": acc,
                         "tau_int_and_mean": l_tau},
             "plain": {"sweeps_per_s": p_rate, "tau_int_and_mean": p_tau},
-            "gain_indep_samples": gain,
+            "gain_indep_samples": gain, "plain_full_sweep": full,
             "training_loss": [float(losses[0]), float(losses[-1]), float(np.var(ytr))],
             "wall_s": time.perf_counter() - t_all}
     print(json.dumps(line), flush=True)
@@ -938,6 +983,8 @@ def main():
     ap.add_argument("--train-snapshots", type=int, default=32)
     ap.add_argument("--tau-steps", type=int, default=150)
     ap.add_argument("--cnn", action="store_true", help="learned mode: convolutional action for block moves")
+    ap.add_argument("--plain-full", action="store_true",
+                    help="largest-learned mode: also time one full plain sweep (minutes at 16x16)")
     ap.add_argument("--cnn-lr", type=float, default=3e-3)
     ap.add_argument("--rate", type=float, default=40.0, help="serving mode: requests per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serving mode: seconds of arrivals")

@@ -360,6 +360,15 @@ int hq_cnn_train(hq_engine* e, const double* X_device, const double* y_device, i
 int hq_cnn_gradient(hq_engine* e, const double* X_device, const double* y_device, int n_samples, float* grad_host,
                     double* loss_host);
 
+/* Failure-detection probe (no counterpart in the paper).  Every device-side wait of the
+ * library (a block-move task waiting for its chain's previous step) is bounded: after its
+ * limit it gives up, marks the chains HQ_ETIMEOUT and the kernel returns, so a stuck phase
+ * leaves a usable context.  This entry point runs that same wait on a device flag that nothing
+ * sets, with a limit of limit_seconds (0 < limit <= 2), on the stream, synchronises, and writes
+ * the kernel's verdict to *status_out: HQ_ETIMEOUT when the wait ran out (the expected
+ * result).  Returns HQ_OK, HQ_EINVAL for a bad limit or pointer, HQ_ECUDA on a CUDA error. */
+int hq_wait_probe(double limit_seconds, void* stream, int* status_out);
+
 /* Per-section device cycle counters (profiling builds compiled with -DHQ_SECTION_TIMING):
  * copies up to n counters (sum over CTAs of thread 0's clock64 spans; ids in
  * csrc/hq_device.cuh) to out and clears them.  Returns the number copied; 0 in normal

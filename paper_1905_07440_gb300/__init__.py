@@ -93,6 +93,7 @@ _SIGNATURES = {
     "hq_fp64_peak_tflops": (ctypes.c_double, [ctypes.c_int, ctypes.c_int, _vp]),
     "hq_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "hq_set_graphs": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "hq_wait_probe": (ctypes.c_int, [ctypes.c_double, _vp, _P(ctypes.c_int)]),
     "hq_logdet_noalloc": (ctypes.c_int, [_P(hq_params), ctypes.c_int, _vp, _vp, _vp]),
     "hq_nn_arena_bytes": (ctypes.c_size_t, [_vp, ctypes.c_int, ctypes.c_int]),
     "hq_nn_attach": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int]),
@@ -529,6 +530,17 @@ def tau_int(series, c=6.0):
 
 SECTIONS = ("dl", "kin", "prepivot", "qr", "form_q", "t_update", "logdet", "move", "wait", "prop_prep",
             "prop_seq", "wrap", "restab_prod", "restab_qr", "restab_green", "measure")
+
+
+def wait_probe(limit_seconds=0.05, stream=None):
+    """Run the library's bounded device wait on a flag nothing sets; returns the kernel's
+    status (HQ_ETIMEOUT when the wait ran out)."""
+    lib = load_library()
+    st = ctypes.c_int()
+    rc = lib.hq_wait_probe(float(limit_seconds), ctypes.c_void_p(stream), ctypes.byref(st))
+    if rc != HQ_OK:
+        raise HQError(f"hq_wait_probe failed ({rc})")
+    return st.value
 
 
 def section_cycles():

@@ -79,6 +79,28 @@ __device__ __forceinline__ double block_max(double v, double* red) {
   return s;
 }
 
+// ---------------------------------------------------------------- bounded waits
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Spin (with growing sleeps) until *v >= target.  Gives up -- returns false -- when *abort_flag
+// becomes non-zero or after limit_ns of global time, so a wait never hangs the GPU.
+__device__ inline bool bounded_wait_geq(volatile int* v, int target, volatile int* abort_flag,
+                                        unsigned long long limit_ns) {
+  if (*v >= target) return true;
+  const unsigned long long t0 = global_timer_ns();
+  unsigned ns = 32;
+  while (*v < target) {
+    if (*abort_flag != 0 || global_timer_ns() - t0 > limit_ns) return false;
+    __nanosleep(ns);
+    if (ns < 2048) ns *= 2;
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------- bfloat16
 __device__ __forceinline__ float bf16_to_float(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
 

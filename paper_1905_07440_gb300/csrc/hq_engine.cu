@@ -1452,6 +1452,13 @@ int hq_autotune(const hq_params* p, int n_chains, const double* X_device, void* 
   return rc;
 }
 
+int hq_wait_probe(double limit_seconds, void* stream, int* status_out) {
+  if (!status_out || !(limit_seconds > 0.0) || limit_seconds > 2.0) return HQ_EINVAL;
+  *status_out = HQ_OK;
+  const cudaError_t st = hq::wait_probe(limit_seconds, (cudaStream_t)stream, status_out);
+  return st == cudaSuccess ? HQ_OK : HQ_ECUDA;
+}
+
 int hq_get_section_cycles(uint64_t* out, int n) {
   if (!out || n < 0) return HQ_EINVAL;
   return hq::section_cycles((unsigned long long*)out, n);

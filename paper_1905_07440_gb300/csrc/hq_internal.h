@@ -178,6 +178,8 @@ cudaError_t cnn_launch_batch(const Dev& d, const CnnState& cn, const double* Xs,
 cudaError_t cnn_launch_loss(const CnnState& cn, const double* ys, const int* idx, int B, double scale,
                             double* loss, cudaStream_t s);
 int section_cycles(unsigned long long* out, int n);
+// Bounded-wait probe (limit_s of waiting on a flag nothing sets); writes the kernel's status.
+cudaError_t wait_probe(double limit_s, cudaStream_t s, int* status);
 int lmax_class(int nx, int ny);
 // One persistent launch sweeping every chain of a group (flags as hq_sweep; stack != 0 runs
 // the stack build first).

@@ -715,11 +715,6 @@ __device__ void block_move(const Dev& d, const Smem& sm, int c, int site) {
   }
 }
 
-__device__ __forceinline__ unsigned long long global_timer_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
 
 // The block-move phase of a sweep as one persistent launch.  Task t = step * C + chain;
 // a chain's steps are its N moves in site order, preceded (with chunk propagators) by the
@@ -748,20 +743,11 @@ __global__ void __launch_bounds__(HQ_THREADS) global_phase_kernel(Dev d) {
         t = atomicAdd(counter, 1);
         if (t < ntask) {
           const int site = t / C, c = t % C;
-          if (progress[c] < site) {
-            const unsigned long long t0 = global_timer_ns();
-            unsigned ns = 32;
-            while (progress[c] < site) {
-              if (*abort_flag != 0 || global_timer_ns() - t0 > kWaitLimitNs) {
-                // the phase did not complete: every chain's state is suspect
-                if (atomicExch((int*)abort_flag, 1) == 0)
-                  for (int q = 0; q < C; ++q) d.status[q] = HQ_ETIMEOUT;
-                t = -1;
-                break;
-              }
-              __nanosleep(ns);
-              if (ns < 2048) ns *= 2;
-            }
+          if (!bounded_wait_geq(&progress[c], site, abort_flag, kWaitLimitNs)) {
+            // the phase did not complete: every chain's state is suspect
+            if (atomicExch((int*)abort_flag, 1) == 0)
+              for (int q = 0; q < C; ++q) d.status[q] = HQ_ETIMEOUT;
+            t = -1;
           }
         }
       }
@@ -1177,6 +1163,28 @@ cudaError_t launch_proposals(uint32_t key0, uint32_t key1, uint32_t chain, uint3
 
 // ------------------------------------------------------------ FP64 pipe probe
 #define HQ_PROBE_ITERS 4096
+// Wait probe: the bounded wait of the block-move phase on a flag that nothing sets, so the
+// wait runs out after limit_ns and the kernel reports HQ_ETIMEOUT instead of hanging.
+static __device__ int g_wait_probe_flag;   // nothing sets it
+static __device__ int g_wait_probe_abort;  // nothing sets it
+static __device__ int g_wait_probe_status;
+
+__global__ void wait_probe_kernel(unsigned long long limit_ns) {
+  if (threadIdx.x == 0)
+    g_wait_probe_status =
+        bounded_wait_geq(&g_wait_probe_flag, 1, &g_wait_probe_abort, limit_ns) ? HQ_OK : HQ_ETIMEOUT;
+}
+
+cudaError_t wait_probe(double limit_s, cudaStream_t s, int* status) {
+  const unsigned long long ns = (unsigned long long)(limit_s * 1e9);
+  wait_probe_kernel<<<1, 32, 0, s>>>(ns);
+  cudaError_t st = cudaGetLastError();
+  if (st == cudaSuccess) st = cudaMemcpyFromSymbolAsync(status, g_wait_probe_status, sizeof(int), 0,
+                                                        cudaMemcpyDeviceToHost, s);
+  if (st == cudaSuccess) st = cudaStreamSynchronize(s);
+  return st;
+}
+
 __global__ void fp64_probe_kernel(double* out, double b, double c) {
   double a0 = threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
   for (int it = 0; it < HQ_PROBE_ITERS; ++it) {

@@ -97,3 +97,12 @@ def test_autotune_arena_is_the_largest_candidate():
     for m in (1, 2):
         assert hq.arena_bytes(p.with_(delay_k=32, block_method=m), 16) <= one[32]
     assert need([0]) == 0 and need([33]) == 0
+
+
+def test_wait_probe_rejects_bad_limits():
+    import paper_1905_07440_gb300 as hq
+    lib = hq.load_library()
+    st = ctypes.c_int()
+    for bad in (0.0, -1.0, 3.0):
+        assert lib.hq_wait_probe(bad, None, ctypes.byref(st)) == hq.HQ_EINVAL
+    assert lib.hq_wait_probe(0.1, None, None) == hq.HQ_EINVAL

@@ -348,3 +348,15 @@ def test_graph_replay_equals_eager_sweeps(hq):
     if eng.stream.cuda_stream == 0:
         with pytest.raises(hq.HQError):
             eng.set_graphs(True)
+
+
+def test_bounded_wait_runs_out_and_context_stays_usable(hq):
+    """The library's device wait on a flag that nothing sets gives up after its limit and
+    reports HQ_ETIMEOUT; the context is still usable: a sweep afterwards matches the oracle."""
+    import time
+    t0 = time.perf_counter()
+    assert hq.wait_probe(0.05) == hq.HQ_ETIMEOUT
+    assert hq.wait_probe(0.02) == hq.HQ_ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    p = HolsteinParams(nx=4, ny=4, beta=1.0, seed=5)
+    check_against_oracle(hq, p, initial_fields(p, 2, seed=4), 1)
