@@ -474,6 +474,7 @@ def run_learned(args):
     lrn = hq.Engine(params, C, max_series=steps + args.warmup + args.steps + 4)
     lrn.attach_network(4, 8)
     lrn.set_params(theta)
+    lrn.set_inner_window(args.window)
     if theta_cnn is not None:
         lrn.cnn_set_params(theta_cnn)
     use_cnn = theta_cnn is not None
@@ -876,6 +877,7 @@ def run_largest_learned(args):
     lrn = hq.Engine(big, C, max_series=W + M)
     lrn.attach_network(4, 8)
     lrn.set_params(theta)
+    lrn.set_inner_window(args.window)
     lrn.set_fields(X0)
     lrn.cumulative(W, args.n_inner, measure=True)
     torch.cuda.synchronize()
@@ -888,17 +890,19 @@ def run_largest_learned(args):
     l_tau = tau_block(lrn, W)
     lrn.close()
     # plain sampler, local sweeps
-    pl = hq.Engine(big, C, max_series=W + M)
-    pl.set_fields(X0)
-    pl.sweep(W, global_=False)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    pl.sweep(M, global_=False)
-    torch.cuda.synchronize()
-    p_rate = C * M / (time.perf_counter() - t0)
-    p_tau = tau_block(pl, W)
-    pl.close()
-    gain = {k: (l_rate / (2 * l_tau[k][0])) / (p_rate / (2 * p_tau[k][0])) for k in l_tau}
+    p_rate, p_tau, gain = None, None, None
+    if not args.skip_plain:
+        pl = hq.Engine(big, C, max_series=W + M)
+        pl.set_fields(X0)
+        pl.sweep(W, global_=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pl.sweep(M, global_=False)
+        torch.cuda.synchronize()
+        p_rate = C * M / (time.perf_counter() - t0)
+        p_tau = tau_block(pl, W)
+        pl.close()
+        gain = {k: (l_rate / (2 * l_tau[k][0])) / (p_rate / (2 * p_tau[k][0])) for k in l_tau}
     full = None
     if args.plain_full:
         # one full sweep (local moves + a block move per site) of 8 chains: per-chain latency
@@ -922,7 +926,8 @@ def run_largest_learned(args):
             "config": {"workload": "16x16 beta=16 L=160, g=sqrt2, mu=-2", "chains": C, "warmup": W, "measured": M,
                        "network": "patch network trained at 8x8 beta=16 (%d samples, %d epochs)"
                                   % (Xtr.shape[0], args.epochs),
-                       "plain": "local sweeps (no block moves)"},
+                       "plain": "local sweeps (no block moves)",
+                       "inner_window_slices": args.window or big.n_slices, "skip_plain": args.skip_plain},
             "learned": {"steps_per_s": l_rate, "cumulative_acceptance": acc,
                         "tau_int_and_mean": l_tau},
             "plain": {"sweeps_per_s": p_rate, "tau_int_and_mean": p_tau},
@@ -983,6 +988,8 @@ def main():
     ap.add_argument("--train-snapshots", type=int, default=32)
     ap.add_argument("--tau-steps", type=int, default=150)
     ap.add_argument("--cnn", action="store_true", help="learned mode: convolutional action for block moves")
+    ap.add_argument("--window", type=int, default=0, help="learned modes: local moves per step on this many slices")
+    ap.add_argument("--skip-plain", action="store_true", help="largest-learned mode: learned sampler only")
     ap.add_argument("--plain-full", action="store_true",
                     help="largest-learned mode: also time one full plain sweep (minutes at 16x16)")
     ap.add_argument("--cnn-lr", type=float, default=3e-3)

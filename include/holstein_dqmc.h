@@ -328,6 +328,13 @@ int hq_nn_gradient(hq_engine* e, const double* X_device, const double* y_device,
  * attached network state. */
 int hq_cumulative_sweep(hq_engine* e, int n_steps, int n_inner, unsigned flags);
 int hq_get_learned_stats(hq_engine* e, hq_learned_stats* out);
+/* Size of a cumulative proposal: with slices > 0 (and < L) the local moves of each inner sweep
+ * visit only `slices` consecutive slices, l0, l0 + 1, ... (mod L), with l0 = floor(u L) from
+ * event 1 of the step's tag-4 Philox block (first uniform); block moves are unchanged (turn
+ * them off with the flags).  Fewer moves per proposal mean a smaller accumulated network error
+ * and a higher cumulative acceptance at the same exact-weight cost per step.  0 (default) or
+ * slices >= L: every slice.  Errors: HQ_EINVAL for a null engine or slices < 0. */
+int hq_set_inner_window(hq_engine* e, int slices);
 
 /* ------------------------------------------------------------------------------------
  * Convolutional action for block moves (paper, "Global Updates": a convolutional network on

@@ -226,13 +226,23 @@ class CumulativeChain:
         self.min_margin = min(self.min_margin, abs(u - prob) / max(prob, 1e-300))
         return bool(u < prob)
 
-    def step(self, k, n_inner, local=True, block=True):
+    def step(self, k, n_inner, local=True, block=True, window=0):
         """One cumulative step.  The inner moves run forward (local moves l, i ascending, then
         block moves i ascending) or as the exact reverse of that sequence, each with
         probability 1/2 (second uniform of the step's tag-4 Philox block): a fixed order of
-        reversible moves is not reversible, and p_c relies on a reversible proposal."""
+        reversible moves is not reversible, and p_c relies on a reversible proposal.
+
+        window > 0 (and < L): the local moves visit only `window` consecutive slices starting at
+        l0 = floor(u L), u the first uniform of event 1 of the step's tag-4 block (chosen
+        independently of the fields, so each window's sequence is reversible on its own)."""
         p, X = self.p, self.X
         L, N = X.shape
+        W = window if 0 < window < L else L
+        l0 = 0
+        if W < L:
+            wu, _ = proposal_uniforms(p.seed, self.chain, k, [1], TAG_CUMULATIVE)
+            l0 = min(int(float(wu[0]) * L), L - 1)
+        slices = [(l0 + j) % L for j in range(W)]
         X0 = X.copy()
         ld0 = self.logdet
         path = 0.0
@@ -244,7 +254,8 @@ class CumulativeChain:
             parts = ("local", "block") if fwd else ("block", "local")
             for part in parts:
                 if part == "local" and local:
-                    for s in order(L):
+                    for j in order(W):
+                        s = slices[j]
                         u1, u2 = proposal_uniforms(p.seed, self.chain, isw, s * N + np.arange(N), TAG_NN_LOCAL)
                         for i in order(N):
                             xn = X[s, i] + p.dx_local * (2.0 * u1[i] - 1.0)

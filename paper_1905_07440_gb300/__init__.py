@@ -104,6 +104,7 @@ _SIGNATURES = {
                                    ctypes.c_uint64, _dp]),
     "hq_nn_gradient": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _P(ctypes.c_float), _dp]),
     "hq_cumulative_sweep": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint]),
+    "hq_set_inner_window": (ctypes.c_int, [_vp, ctypes.c_int]),
     "hq_cnn_set_params": (ctypes.c_int, [_vp, _P(ctypes.c_float)]),
     "hq_cnn_get_params": (ctypes.c_int, [_vp, _P(ctypes.c_float), ctypes.c_int]),
     "hq_cnn_eval": (ctypes.c_int, [_vp, _dp]),
@@ -348,6 +349,10 @@ class Engine:
         flags = ((HQ_LOCAL if local else 0) | (HQ_GLOBAL if global_ else 0) | (HQ_MEASURE if measure else 0)
                  | (HQ_CNN_BLOCK if cnn else 0))
         self._check(self.lib.hq_cumulative_sweep(self._h, int(n_steps), int(n_inner), flags), "hq_cumulative_sweep")
+
+    def set_inner_window(self, slices):
+        """Local moves of each cumulative step on `slices` consecutive slices (0: all)."""
+        self._check(self.lib.hq_set_inner_window(self._h, int(slices)), "hq_set_inner_window")
 
     # convolutional action (block moves)
     def cnn_set_params(self, theta):

@@ -48,6 +48,7 @@ struct hq_engine {
   hq::CnnState cn{};
   int nn_max_batch = 0, nn_max_samples = 0;
   int cn_t_step = 0;
+  int nn_window = 0;  // local moves of a cumulative step on this many slices (0: all)
   long long cum_steps = 0;
   int nn_t_step = 0;
   ~hq_engine() {
@@ -1079,7 +1080,8 @@ int hq_cumulative_sweep(hq_engine* e, int n_steps, int n_inner, unsigned flags) 
     rc = rc ? rc : cuda_check(e, hq::nn_launch_eval(d, e->nn, d.X, e->nn.F0, 1, e->stream), "nn eval F0");
     if (use_cnn) rc = rc ? rc : cuda_check(e, hq::cnn_launch_eval(d, e->cn, d.X, e->cn.F, 1, e->stream), "cnn eval");
     rc = rc ? rc : cuda_check(e, hq::nn_launch_inner(d, e->nn, e->cn, n_inner, (flags & HQ_LOCAL) ? 1 : 0,
-                                                     (flags & HQ_GLOBAL) ? 1 : 0, use_cnn, e->stream), "nn inner");
+                                                     (flags & HQ_GLOBAL) ? 1 : 0, use_cnn, e->nn_window,
+                                                     e->stream), "nn inner");
     e->stack_valid = false;
     rc = rc ? rc : ensure_state(e);  // log|det M(X')| (and G, stack of X')
     rc = rc ? rc : cuda_check(e, hq::nn_launch_decide(d, e->nn, e->stream), "nn decide");
@@ -1096,6 +1098,12 @@ int hq_cumulative_sweep(hq_engine* e, int n_steps, int n_inner, unsigned flags) 
     if (rc) return rc;
     e->cum_steps++;
   }
+  return HQ_OK;
+}
+
+int hq_set_inner_window(hq_engine* e, int slices) {
+  if (!e || slices < 0) return HQ_EINVAL;
+  e->nn_window = slices >= e->d.L ? 0 : slices;
   return HQ_OK;
 }
 

@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_eval_kernel(Dev d, NNState nn, 
 // valid on entry; with use_cnn each network's cache is rebuilt before its part when the other
 // part has changed the fields.
 __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn, CnnState cn, int n_inner,
-                                                              int do_local, int do_block, int use_cnn) {
+                                                              int do_local, int do_block, int use_cnn, int window) {
   extern __shared__ __align__(16) char nraw[];
   const int c = blockIdx.x, n = d.n, L = d.L, NL = n * L;
   if (!d.active[c]) return;
@@ -220,6 +220,16 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
   double du1, du2;
   proposal_uniforms(key0, key1, 0u, step, chain, 4u, du1, du2);
   const bool fwd = du2 < 0.5;
+  // local moves on W consecutive slices from a random start l0 (event 1 of the step's tag-4
+  // stream; independent of the fields, so each window's move sequence stays reversible)
+  const int W = (window > 0 && window < L) ? window : L;
+  int l0 = 0;
+  if (W < L) {
+    double wu1, wu2;
+    proposal_uniforms(key0, key1, 1u, step, chain, 4u, wu1, wu2);
+    l0 = (int)(wu1 * (double)L);
+    if (l0 > L - 1) l0 = L - 1;
+  }
   for (int u = 0; u < n_inner; ++u) {
     const uint32_t isw = step * (uint32_t)n_inner + (uint32_t)u;
     for (int part = 0; part < 2; ++part) {
@@ -229,8 +239,8 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
         fc_eval_all(d, s, X, nn.x0, fc);
         fc_stale = false;
       }
-      for (int sl0 = 0; sl0 < L; ++sl0) {
-        const int sl = fwd ? sl0 : L - 1 - sl0;
+      for (int sl0 = 0; sl0 < W; ++sl0) {
+        const int sl = (l0 + (fwd ? sl0 : W - 1 - sl0)) % L;
         for (int i = threadIdx.x; i < n; i += HQ_THREADS) {
           double u1, u2;
           proposal_uniforms(key0, key1, (uint32_t)(sl * n + i), isw, chain, 2u, u1, u2);
@@ -361,7 +371,7 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
   }
   if (threadIdx.x == 0) {
     long long* cnt = nn.counters + (size_t)c * kNNCounters;
-    cnt[0] += (long long)n_inner * (do_local ? NL : 0);
+    cnt[0] += (long long)n_inner * (do_local ? W * n : 0);
     cnt[1] += nl_acc;
     cnt[2] += (long long)n_inner * (do_block ? n : 0);
     cnt[3] += nb_acc;
@@ -614,10 +624,10 @@ cudaError_t nn_launch_eval(const Dev& d, const NNState& nn, const double* X, dou
 }
 
 cudaError_t nn_launch_inner(const Dev& d, const NNState& nn, const CnnState& cn, int n_inner, int do_local,
-                            int do_block, int use_cnn, cudaStream_t s) {
+                            int do_block, int use_cnn, int window, cudaStream_t s) {
   const size_t sb = nn_smem_bytes(d.n, use_cnn != 0);
   smem_opt_in((const void*)nn_inner_kernel, sb);
-  nn_inner_kernel<<<d.n_chains, HQ_THREADS, sb, s>>>(d, nn, cn, n_inner, do_local, do_block, use_cnn);
+  nn_inner_kernel<<<d.n_chains, HQ_THREADS, sb, s>>>(d, nn, cn, n_inner, do_local, do_block, use_cnn, window);
   return cudaGetLastError();
 }
 
