@@ -299,7 +299,7 @@ def run_ours(args):
     dom = max(phases, key=lambda k: phases[k][0])
     ms, launches = phases[dom]
     per_launch_s = ms / 1e3 / max(launches, 1)
-    kernel_names = {"block_moves": "global_phase_kernel", "local_chunk": "local_chunk_kernel",
+    kernel_names = {"block_moves": "global_phase_kernel", "local_chunk": "local_phase_kernel",
                     "stack_build": "stack_build_kernel", "sweep_end": "sweep_end_kernel"}
     method = eng.block_move_method
     if dom == "block_moves":
@@ -316,7 +316,7 @@ def run_ours(args):
     if n_l:
         fl_l = chains * flops_local_phase(params, acc_l0)
         per_sweep_s = ms_l / 1e3 / args.steps
-        roof_local = {"bound": "alu", "kernel": "local_chunk_kernel", "achieved": fl_l / per_sweep_s / 1e12,
+        roof_local = {"bound": "alu", "kernel": "local_phase_kernel", "achieved": fl_l / per_sweep_s / 1e12,
                       "peak": peak, "unit": "TFLOP/s", "frac": fl_l / per_sweep_s / 1e12 / peak,
                       "flops_per_sweep": fl_l, "launches_per_sweep": n_l / args.steps,
                       "ms_per_sweep": ms_l / args.steps}

@@ -362,12 +362,9 @@ int sweep_once(hq_engine* e, unsigned flags) {
   if (do_local || !e->logdet_valid) rc = ensure_state(e);
   if (rc) return rc;
   if (do_local) {
-    PhaseTimer pt(e, 1, (d.L + d.n_wrap - 1) / d.n_wrap);
-    for (int s0 = 0; s0 < d.L; s0 += d.n_wrap) {
-      const int s1 = s0 + d.n_wrap < d.L ? s0 + d.n_wrap : d.L;
-      rc = cuda_check(e, hq::launch_local_chunk(d, s0, s1, meas ? 1 : 0, e->stream), "local_chunk launch");
-      if (rc) return rc;
-    }
+    PhaseTimer pt(e, 1, 1);
+    rc = cuda_check(e, hq::launch_local_phase(d, meas ? 1 : 0, e->stream), "local_phase launch");
+    if (rc) return rc;
     e->stack_valid = false;  // fields changed; G_0 and log|det M| are fresh (restabilised at l = L)
     e->logdet_valid = e->green_valid = true;
   }

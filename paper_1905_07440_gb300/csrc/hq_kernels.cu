@@ -479,6 +479,47 @@ __global__ void __launch_bounds__(HQ_THREADS) local_chunk_kernel(Dev d, int s0, 
   local_chunk_body<LMAX>(d, blockIdx.x, s0, s1, measure, smraw);
 }
 
+// The local phase of a sweep as one persistent launch, like the block-move phase: task
+// t = q * C + chain is chunk q (slices [q n_wrap, min((q + 1) n_wrap, L))) of that chain;
+// workers take tasks from an atomic counter and a task waits (bounded) until its chain
+// finished chunk q - 1, so an SM that runs one chain alone takes more chunks than an SM
+// shared by two.  sched = [counter, abort, ..., progress[C] at kSchedHeader], zeroed first.
+template <int LMAX>
+__global__ void __launch_bounds__(HQ_THREADS) local_phase_kernel(Dev d, int measure) {
+  extern __shared__ double smraw[];
+  __shared__ int s_task;
+  const int C = d.n_chains, Q = (d.L + d.n_wrap - 1) / d.n_wrap, ntask = Q * C;
+  int* counter = d.sched;
+  volatile int* abort_flag = d.sched + 1;
+  volatile int* progress = d.sched + kSchedHeader;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      int t = -1;
+      if (*abort_flag == 0) {
+        t = atomicAdd(counter, 1);
+        if (t < ntask && !bounded_wait_geq(&progress[t % C], t / C, abort_flag, kWaitLimitNs)) {
+          if (atomicExch((int*)abort_flag, 1) == 0)
+            for (int q = 0; q < C; ++q) d.status[q] = HQ_ETIMEOUT;
+          t = -1;
+        }
+      }
+      s_task = t;
+    }
+    __syncthreads();
+    const int t = s_task;
+    if (t < 0 || t >= ntask) break;
+    __threadfence();  // acquire: the previous chunk of this chain (possibly on another SM)
+    const int q = t / C, c = t % C;
+    const int s0 = q * d.n_wrap, s1 = s0 + d.n_wrap < d.L ? s0 + d.n_wrap : d.L;
+    local_chunk_body<LMAX>(d, c, s0, s1, measure, smraw);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();  // release the chunk before publishing it
+      atomicExch((int*)&progress[c], q + 1);
+    }
+  }
+}
+
 // -------------------------------------------- block moves with chunk propagators
 // For block moves the n_wrap-slice products M_q = B_lo^T .. B_{hi-1}^T (chunk q covers
 // slices [q n_wrap, min((q+1) n_wrap, L))) are formed once per block-move phase.  A move
@@ -1061,6 +1102,36 @@ cudaError_t launch_stack_build(const Dev& d, cudaStream_t s) {
 cudaError_t launch_local_chunk(const Dev& d, int s0, int s1, int measure, cudaStream_t s) {
   HQ_DISPATCH(local_chunk_kernel, d, s, d, s0, s1, measure);
   return cudaGetLastError();
+}
+
+template <int LMAX>
+static cudaError_t launch_local_phase_t(const Dev& d, int measure, cudaStream_t s) {
+  const size_t sb = smem_bytes(d);
+  allow_smem(local_phase_kernel<LMAX>, sb);
+  int dev = 0, sms = 0, occ = 0;
+  cudaError_t st = cudaGetDevice(&dev);
+  if (st == cudaSuccess) st = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (st == cudaSuccess)
+    st = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, local_phase_kernel<LMAX>, HQ_THREADS, sb);
+  if (st != cudaSuccess) return st;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  // as in the block-move phase: one wave at most, at most one worker per active chain
+  int workers = sms * (occ < kWorkersPerSm ? occ : kWorkersPerSm);
+  if (workers > d.n_active) workers = d.n_active;
+  if (workers < 1) workers = 1;
+  st = cudaMemsetAsync(d.sched, 0, sizeof(int) * (kSchedHeader + d.n_chains), s);
+  if (st != cudaSuccess) return st;
+  local_phase_kernel<LMAX><<<workers, HQ_THREADS, sb, s>>>(d, measure);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_local_phase(const Dev& d, int measure, cudaStream_t s) {
+  switch (lmax_of(d.nx, d.ny)) {
+    case 2: return launch_local_phase_t<2>(d, measure, s);
+    case 4: return launch_local_phase_t<4>(d, measure, s);
+    case 8: return launch_local_phase_t<8>(d, measure, s);
+    default: return launch_local_phase_t<16>(d, measure, s);
+  }
 }
 
 template <int LMAX>
