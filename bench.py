@@ -833,8 +833,11 @@ def run_largest_learned(args):
     import numpy as np
     import torch
     import paper_1905_07440_gb300 as hq
-    big = workloads.LARGEST
-    C = args.chains or 64
+    if args.deploy == "medium":
+        big, C0, wname = workloads.MEDIUM, workloads.MEDIUM_RUN["n_chains"], "12x12 beta=8 L=80, g=sqrt2, mu=-2"
+    else:
+        big, C0, wname = workloads.LARGEST, workloads.LARGEST_RUN["n_chains"], "16x16 beta=16 L=160, g=sqrt2, mu=-2"
+    C = args.chains or C0
     small = big.with_(nx=8, ny=8)
     x0 = -big.g / (big.mass * big.omega ** 2)
     dev = torch.device("cuda", 0)
@@ -920,12 +923,12 @@ def run_largest_learned(args):
         full = {"seconds_per_sweep": t_full, "chains_timed": 8,
                 "indep_samples_per_s_upper_bound": C / t_full,
                 "learned_gain_lower_bound": {k: (l_rate / (2 * l_tau[k][0])) / (C / t_full) for k in l_tau}}
-    line = {"metric": METRIC, "mode": "learned vs plain, largest lattice",
+    line = {"metric": METRIC, "mode": "learned vs plain, " + args.deploy + " lattice",
             "value": l_rate / (2 * l_tau["s_cdw"][0]), "unit": "independent samples/s of S_CDW(pi,pi) (learned)",
             "higher_is_better": True, "dtype": "f64 weights, bf16-weight/fp32 network", "data": "synthetic",
-            "config": {"workload": "16x16 beta=16 L=160, g=sqrt2, mu=-2", "chains": C, "warmup": W, "measured": M,
-                       "network": "patch network trained at 8x8 beta=16 (%d samples, %d epochs)"
-                                  % (Xtr.shape[0], args.epochs),
+            "config": {"workload": wname, "chains": C, "warmup": W, "measured": M,
+                       "network": "patch network trained at 8x8 beta=%g (%d samples, %d epochs)"
+                                  % (big.beta, Xtr.shape[0], args.epochs),
                        "plain": "local sweeps (no block moves)",
                        "inner_window_slices": args.window or big.n_slices, "skip_plain": args.skip_plain},
             "learned": {"steps_per_s": l_rate, "cumulative_acceptance": acc,
@@ -988,6 +991,8 @@ def main():
     ap.add_argument("--train-snapshots", type=int, default=32)
     ap.add_argument("--tau-steps", type=int, default=150)
     ap.add_argument("--cnn", action="store_true", help="learned mode: convolutional action for block moves")
+    ap.add_argument("--deploy", choices=("largest", "medium"), default="largest",
+                    help="largest-learned mode: deploy at 16x16 beta=16 or 12x12 beta=8")
     ap.add_argument("--window", type=int, default=0, help="learned modes: local moves per step on this many slices")
     ap.add_argument("--skip-plain", action="store_true", help="largest-learned mode: learned sampler only")
     ap.add_argument("--plain-full", action="store_true",
