@@ -337,46 +337,54 @@ __device__ void local_chunk_body(const Dev& d, int c, int s0, int s1, int measur
     HQ_TOC(pp, SEC_PROP_PREP);
     HQ_TIC(seq);
     int kk = 0;
-    for (int i = 0; i < n; ++i) {
-      const int slot = i & 1;
+    // Thread 0 runs the decisions in site order; a rejected proposal changes nothing, so it
+    // walks on to the next accepted site before the CTA meets (one barrier per accepted move
+    // instead of one per proposal).  sm.sint[2 + slot] = the accepted site, n when none is left.
+    for (int i0 = 0, it = 0; i0 < n; ++it) {
+      const int slot = it & 1;
       if (threadIdx.x == 0) {
-        // ratio of one spin: R1 = 1 + delta (1 - G_ii), G_ii including pending updates
-        const double gii = G[(size_t)i * n + i] + sm.dcorr[i];
-        const double delta = sm.dlt[i];
-        const double R1 = 1.0 + delta * (1.0 - gii);
-        const double prob = R1 * R1 * sm.es[i];
-        const int accept = sm.u2[i] < prob;
-        sm.sint[2 + slot] = accept;
-        sm.scal[slot] = delta / R1;
-        if (accept) {
-          X[(size_t)s * n + i] = sm.xn[i];
-          ++n_acc;
+        int next = n;
+        for (int i = i0; i < n; ++i) {
+          // ratio of one spin: R1 = 1 + delta (1 - G_ii), G_ii including pending updates
+          const double gii = G[(size_t)i * n + i] + sm.dcorr[i];
+          const double delta = sm.dlt[i];
+          const double R1 = 1.0 + delta * (1.0 - gii);
+          const double prob = R1 * R1 * sm.es[i];
+          if (!isfinite(R1)) d.status[c] = HQ_ENAN;
+          if (sm.u2[i] < prob) {
+            X[(size_t)s * n + i] = sm.xn[i];
+            ++n_acc;
+            sm.scal[slot] = delta / R1;
+            next = i;
+            break;
+          }
         }
-        if (!isfinite(R1)) d.status[c] = HQ_ENAN;
+        sm.sint[2 + slot] = next;
       }
       __syncthreads();
-      if (sm.sint[2 + slot]) {
+      const int i = sm.sint[2 + slot];
+      i0 = i + 1;
+      if (i < n) {
         // G' = Gc + a b^T with a = (delta/R1)(Gc[:, i] - e_i), b = Gc[i, :],
         // Gc = G + sum_m A[:, m] B[:, m]^T (updates not yet flushed).
         const double f = sm.scal[slot];
-        for (int idx = threadIdx.x; idx < 2 * n; idx += HQ_THREADS) {
-          if (idx < n) {
-            const int r = idx;
-            double v = G[(size_t)i * n + r];
-            for (int m = 0; m < kk; ++m) v = fma(A[m * n + r], B[m * n + i], v);
-            if (r == i) v -= 1.0;
-            A[kk * n + r] = f * v;
-          } else {
-            const int col = idx - n;
-            double v = G[(size_t)col * n + i];
-            for (int m = 0; m < kk; ++m) v = fma(A[m * n + i], B[m * n + col], v);
-            B[kk * n + col] = v;
+        // entry r of both new vectors in one thread, so the diagonal correction needs no
+        // barrier of its own
+        for (int r = threadIdx.x; r < n; r += HQ_THREADS) {
+          double va = G[(size_t)i * n + r], vb = G[(size_t)r * n + i];
+          for (int m = 0; m < kk; ++m) {
+            va = fma(A[m * n + r], B[m * n + i], va);
+            vb = fma(A[m * n + i], B[m * n + r], vb);
           }
+          if (r == i) va -= 1.0;
+          const double a = f * va;
+          A[kk * n + r] = a;
+          B[kk * n + r] = vb;
+          sm.dcorr[r] = fma(a, vb, sm.dcorr[r]);
         }
-        __syncthreads();
-        for (int r = threadIdx.x; r < n; r += HQ_THREADS) sm.dcorr[r] = fma(A[kk * n + r], B[kk * n + r], sm.dcorr[r]);
         ++kk;
         if (kk == k) {
+          __syncthreads();
           // flush: G += A B^T, an n x n x k FP64 contraction
           for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
             const int r = idx % n, col = idx / n;
