@@ -372,7 +372,7 @@ int hq_cnn_gradient(hq_engine* e, const double* X_device, const double* y_device
  * limit it gives up, marks the chains HQ_ETIMEOUT and the kernel returns, so a stuck phase
  * leaves a usable context.  This entry point runs that same wait on a device flag that nothing
  * sets, with a limit of limit_seconds (0 < limit <= 2), on the stream, synchronises, and writes
- * the kernel's verdict to *status_out: HQ_ETIMEOUT when the wait ran out (the expected
+ * the kernel's result to *status_out: HQ_ETIMEOUT when the wait ran out (the expected
  * result).  Returns HQ_OK, HQ_EINVAL for a bad limit or pointer, HQ_ECUDA on a CUDA error. */
 int hq_wait_probe(double limit_seconds, void* stream, int* status_out);
 
