@@ -24,6 +24,8 @@ namespace hq {
 
 // parameter layout: W1[25][64], b1[64], W2[64][64], b2[64], W3[64], b3
 constexpr int NN_IN = 25, NN_H = 64;
+constexpr int NN_HP = NN_H + 1;  // padded stride of the groups' hidden rows: the 4 groups of a
+                                 // warp then read h1[v] from 4 different banks
 constexpr int NN_W1 = 0, NN_B1 = NN_IN * NN_H, NN_W2 = NN_B1 + NN_H, NN_B2 = NN_W2 + NN_H * NN_H,
               NN_W3 = NN_B2 + NN_H, NN_B3 = NN_W3 + NN_H, NN_NP = NN_B3 + 1;
 static_assert(NN_NP == HQ_NN_PARAMS, "parameter count");
@@ -51,8 +53,12 @@ __device__ __forceinline__ float nn_patch_eval(const float* w, const float* z, f
   for (int j = 0; j < 8; ++j) a[j] = b1[u0 + j];
   for (int k = 0; k < NN_IN; ++k) {
     const float zk = z[k];
+    // the lane's 8 weights of this input as two 16-byte loads (fewer shared-memory requests)
+    const float4 wa = *reinterpret_cast<const float4*>(W1 + k * NN_H + u0);
+    const float4 wb = *reinterpret_cast<const float4*>(W1 + k * NN_H + u0 + 4);
+    const float w8[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
 #pragma unroll
-    for (int j = 0; j < 8; ++j) a[j] = fmaf(zk, W1[k * NN_H + u0 + j], a[j]);
+    for (int j = 0; j < 8; ++j) a[j] = fmaf(zk, w8[j], a[j]);
   }
 #pragma unroll
   for (int j = 0; j < 8; ++j) h1[u0 + j] = fmaxf(a[j], 0.f);
@@ -62,8 +68,11 @@ __device__ __forceinline__ float nn_patch_eval(const float* w, const float* z, f
   for (int j = 0; j < 8; ++j) c[j] = b2[u0 + j];
   for (int v = 0; v < NN_H; ++v) {
     const float hv = h1[v];
+    const float4 wa = *reinterpret_cast<const float4*>(W2 + v * NN_H + u0);
+    const float4 wb = *reinterpret_cast<const float4*>(W2 + v * NN_H + u0 + 4);
+    const float w8[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
 #pragma unroll
-    for (int j = 0; j < 8; ++j) c[j] = fmaf(hv, W2[v * NN_H + u0 + j], c[j]);
+    for (int j = 0; j < 8; ++j) c[j] = fmaf(hv, w8[j], c[j]);
   }
   float o = 0.f;
 #pragma unroll
@@ -98,7 +107,7 @@ __device__ __forceinline__ void fill_patch(const Dev& d, const double* X, int l,
 struct NNSmem {
   float* w;      // [NN_WPAD]
   float* z;      // [NN_GROUPS][NN_IN + 3]
-  float* h1;     // [NN_GROUPS][NN_H]
+  float* h1;     // [NN_GROUPS][NN_HP]
   double* red;   // [HQ_WARPS]
   double* pu2;   // [n] proposal uniforms (local)
   double* pxn;   // [n] proposed values
@@ -111,7 +120,7 @@ struct NNSmem {
 
 __host__ __device__ inline size_t nn_smem_bytes(int n, bool with_cnn = false) {
   size_t b = sizeof(double) * (HQ_WARPS + 3 * (size_t)n + NN_GROUPS + 8) +
-             sizeof(float) * (NN_WPAD + NN_GROUPS * (NN_IN + 3) + NN_GROUPS * NN_H);
+             sizeof(float) * (NN_WPAD + NN_GROUPS * (NN_IN + 3) + NN_GROUPS * NN_HP);
   if (with_cnn) b += sizeof(float) * CN_WPAD + sizeof(int) * (4 + 3 * CN_WIN + 2 * (size_t)n);
   return b;
 }
@@ -128,7 +137,7 @@ __device__ inline NNSmem nn_carve(int n, char* base, bool with_cnn = false) {
   float* f = (float*)p;
   s.w = f; f += NN_WPAD;
   s.z = f; f += NN_GROUPS * (NN_IN + 3);
-  s.h1 = f; f += NN_GROUPS * NN_H;
+  s.h1 = f; f += NN_GROUPS * NN_HP;
   s.cw = nullptr;
   if (with_cnn) {
     s.cw = f; f += CN_WPAD;
@@ -146,7 +155,7 @@ __device__ inline double fc_eval_all(const Dev& d, const NNSmem& s, const double
   const int n = d.n, NL = d.n * d.L;
   const int g = threadIdx.x / 8, sub = threadIdx.x % 8;
   float* z = s.z + g * (NN_IN + 3);
-  float* h1 = s.h1 + g * NN_H;
+  float* h1 = s.h1 + g * NN_HP;
   double part = 0.0;
   for (int base = 0; base < NL; base += NN_GROUPS) {
     const int row = base + g;
@@ -210,7 +219,7 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
   }
   const int g = threadIdx.x / 8, sub = threadIdx.x % 8;
   float* z = s.z + g * (NN_IN + 3);
-  float* h1 = s.h1 + g * NN_H;
+  float* h1 = s.h1 + g * NN_HP;
   const uint32_t* id = d.cid + 4 * (size_t)c;
   const uint32_t key0 = id[0], key1 = id[1], chain = id[2], step = id[3];
   long long nl_acc = 0, nb_acc = 0;
@@ -437,7 +446,7 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_batch_forward_kernel(Dev d, NNS
   const double* X = Xs + (size_t)idx[a] * NL;
   const int g = threadIdx.x / 8, sub = threadIdx.x % 8;
   float* z = s.z + g * (NN_IN + 3);
-  float* h1 = s.h1 + g * NN_H;
+  float* h1 = s.h1 + g * NN_HP;
   double part = 0.0;
   for (int base = 0; base < NL; base += NN_GROUPS) {
     const int row = base + g;
