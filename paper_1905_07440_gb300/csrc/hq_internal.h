@@ -146,7 +146,6 @@ cudaError_t opt_in_smem(const void* kernel, size_t bytes);
 
 // Launchers (asynchronous on the stream).  Return cudaGetLastError().
 cudaError_t launch_stack_build(const Dev& d, cudaStream_t s);
-cudaError_t launch_local_chunk(const Dev& d, int s0, int s1, int measure, cudaStream_t s);
 // The whole local phase (every chunk of every chain) as one persistent launch.
 cudaError_t launch_local_phase(const Dev& d, int measure, cudaStream_t s);
 cudaError_t launch_global_phase(const Dev& d, cudaStream_t s);

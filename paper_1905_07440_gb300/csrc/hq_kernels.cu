@@ -2,7 +2,7 @@
 //
 //   stack_build   fields -> left UDV stack of B_L..B_{b+1} at every restabilisation
 //                 boundary b, fresh G_0 and log|det M|           (DQMC section: M = I + B_L..B_1)
-//   local_chunk   n_wrap slices of local Metropolis moves with delayed rank-k updates of
+//   local_phase   n_wrap-slice chunks of local Metropolis moves with delayed rank-k updates of
 //                 G and the wrap G <- B_l G B_l^-1, then the right UDV update and a fresh
 //                 G_l from the right factors and the left stack  (local updates at each
 //                 spacetime point, fast update of the paper's ref. WhitePRB1989)
@@ -481,11 +481,6 @@ __device__ void local_chunk_body(const Dev& d, int c, int s0, int s1, int measur
   HQ_TOC(ms, SEC_MEASURE);
 }
 
-template <int LMAX>
-__global__ void __launch_bounds__(HQ_THREADS) local_chunk_kernel(Dev d, int s0, int s1, int measure) {
-  extern __shared__ double smraw[];
-  local_chunk_body<LMAX>(d, blockIdx.x, s0, s1, measure, smraw);
-}
 
 // The local phase of a sweep as one persistent launch, like the block-move phase: task
 // t = q * C + chain is chunk q (slices [q n_wrap, min((q + 1) n_wrap, L))) of that chain;
@@ -1107,10 +1102,6 @@ cudaError_t launch_stack_build(const Dev& d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_local_chunk(const Dev& d, int s0, int s1, int measure, cudaStream_t s) {
-  HQ_DISPATCH(local_chunk_kernel, d, s, d, s0, s1, measure);
-  return cudaGetLastError();
-}
 
 template <int LMAX>
 static cudaError_t launch_local_phase_t(const Dev& d, int measure, cudaStream_t s) {

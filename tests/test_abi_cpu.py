@@ -106,3 +106,12 @@ def test_wait_probe_rejects_bad_limits():
     for bad in (0.0, -1.0, 3.0):
         assert lib.hq_wait_probe(bad, None, ctypes.byref(st)) == hq.HQ_EINVAL
     assert lib.hq_wait_probe(0.1, None, None) == hq.HQ_EINVAL
+
+
+def test_group_arena_rejects_empty_sets():
+    import paper_1905_07440_gb300 as hq
+    lib = hq.load_library()
+    assert lib.hq_group_arena_bytes(None, 0) == 0
+    assert lib.hq_group_arena_bytes(None, 3) == 0
+    arr = (ctypes.c_void_p * 1)(None)
+    assert lib.hq_group_arena_bytes(arr, 1) == 0          # null engine
