@@ -827,7 +827,7 @@ constexpr int kNNParamsPad = (HQ_NN_PARAMS + 3) & ~3;
 constexpr int kCnnParamsPad = (HQ_CNN_PARAMS + 3) & ~3;
 
 struct NNLayout {
-  size_t wbf, master, grad, am, av, partials, fcache, fnew, X0, ld0, F0, F1, pc, Fb, loss, idx, counters, dFpath;
+  size_t wbf, master, grad, am, av, partials, fcache, fnew, X0, ld0, F0, F1, pc, Fb, loss, idx, counters, dFpath, G0;
   size_t cwbf, cmaster, cgrad, cam, cav, cpartials, h1c, h2c, o3c, h1p, h2p, o3p, tr, cFb, cF;
   int train_ctas;
   size_t total;
@@ -856,6 +856,7 @@ NNLayout nn_layout(const hq::Dev& d, int max_batch, int max_samples) {
   l.idx = take(4 * (size_t)max_samples);
   l.counters = take(8 * C * hq::kNNCounters);
   l.dFpath = take(8 * C);
+  l.G0 = take(8 * C * (size_t)d.n * d.n);
   // convolutional action
   const size_t PC = kCnnParamsPad, CH = hq::kCnnC;
   l.train_ctas = max_batch < hq::kCnnTrainCtas ? max_batch : hq::kCnnTrainCtas;
@@ -925,6 +926,7 @@ int hq_nn_attach(hq_engine* e, void* arena, size_t bytes, int max_batch, int max
   nn.idx = (int*)(a + l.idx);
   nn.counters = (long long*)(a + l.counters);
   nn.dFpath = (double*)(a + l.dFpath);
+  nn.G0 = (double*)(a + l.G0);
   nn.x0 = -e->p.g / (e->p.mass * e->p.omega * e->p.omega);
   hq::CnnState& cn = e->cn;
   cn.on = 0;
@@ -1065,12 +1067,18 @@ int hq_cumulative_sweep(hq_engine* e, int n_steps, int n_inner, unsigned flags) 
   if (use_cnn && !e->cn.on) return set_err(e, HQ_EINVAL, "HQ_CNN_BLOCK needs convolutional parameters (hq_cnn_set_params)");
   const hq::Dev& d = e->d;
   const size_t fbytes = sizeof(double) * (size_t)d.n_chains * d.L * d.n;
+  const bool meas = flags & HQ_MEASURE;
   for (int k = 0; k < n_steps; ++k) {
-    if (!e->logdet_valid) {
+    // the step needs log|det M(X)|, and for a measured step G_0 of X (kept for rejection)
+    if (!e->logdet_valid || (meas && !e->green_valid)) {
       rc = ensure_state(e);
       if (rc) return rc;
     }
-    rc = cuda_check(e, cudaMemcpyAsync(e->nn.X0, d.X, fbytes, cudaMemcpyDeviceToDevice, e->stream), "X0 copy");
+    if (meas)
+      rc = cuda_check(e, cudaMemcpyAsync(e->nn.G0, d.G, sizeof(double) * (size_t)d.n_chains * d.n * d.n,
+                                         cudaMemcpyDeviceToDevice, e->stream), "G0 copy");
+    rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(e->nn.X0, d.X, fbytes, cudaMemcpyDeviceToDevice, e->stream),
+                              "X0 copy");
     rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(e->nn.ld0, d.logdet, sizeof(double) * d.n_chains,
                                                  cudaMemcpyDeviceToDevice, e->stream), "ld0 copy");
     // caches of the current fields (the previous step may have restored X)
@@ -1081,14 +1089,14 @@ int hq_cumulative_sweep(hq_engine* e, int n_steps, int n_inner, unsigned flags) 
                                                      e->stream), "nn inner");
     e->stack_valid = false;
     rc = rc ? rc : ensure_state(e);  // log|det M(X')| (and G, stack of X')
-    rc = rc ? rc : cuda_check(e, hq::nn_launch_decide(d, e->nn, e->stream), "nn decide");
+    // a rejected chain gets back X, log|det M(X)| and, for a measured step, G_0 of X
+    rc = rc ? rc : cuda_check(e, hq::nn_launch_decide(d, e->nn, meas ? 1 : 0, e->stream), "nn decide");
     if (rc) return rc;
-    e->stack_valid = e->green_valid = false;  // fields may have been restored to X
+    e->stack_valid = false;  // the stack is X''s; rejected chains are back at X
+    e->green_valid = meas;   // measured steps: every chain's G is G_0 of its final fields
     e->logdet_valid = true;
-    const bool meas = flags & HQ_MEASURE;
     if (meas) {
-      rc = ensure_state(e);
-      rc = rc ? rc : cuda_check(e, hq::launch_measure_g0(d, e->stream), "measure");
+      rc = cuda_check(e, hq::launch_measure_g0(d, e->stream), "measure");
       if (rc) return rc;
     }
     rc = cuda_check(e, hq::launch_sweep_end(d, meas ? 1 : 0, e->stream), "sweep_end launch");

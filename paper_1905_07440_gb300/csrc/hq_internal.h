@@ -109,6 +109,7 @@ struct NNState {
   int* idx;             // [max samples] minibatch order
   long long* counters;  // [C][kNNCounters]
   double* dFpath;       // [C] sum of the accepted inner moves' network changes (cumulative step)
+  double* G0;           // [C][N*N] G_0 of the step's starting fields (measured steps)
   double x0;            // input shift -g/(M Omega^2)
 };
 
@@ -164,7 +165,7 @@ cudaError_t launch_measure_g0(const Dev& d, cudaStream_t s);
 cudaError_t nn_launch_eval(const Dev& d, const NNState& nn, const double* X, double* F, int write_cache,
                            cudaStream_t s);
 
-cudaError_t nn_launch_decide(const Dev& d, const NNState& nn, cudaStream_t s);
+cudaError_t nn_launch_decide(const Dev& d, const NNState& nn, int restore_g, cudaStream_t s);
 cudaError_t nn_launch_set(const NNState& nn, const float* src_device, cudaStream_t s);
 cudaError_t nn_launch_batch(const Dev& d, const NNState& nn, const double* Xs, const double* ys, const int* idx,
                             int B, float lr, int t_step, cudaStream_t s);

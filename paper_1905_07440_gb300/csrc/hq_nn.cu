@@ -390,7 +390,9 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
 
 // Cumulative accept of X' (fields now in d.X, log|det M(X')| in d.logdet after the stack
 // build) against X (saved in nn.X0 with nn.ld0): p_c = exp(2 dlog|det M| - 2 nn.dFpath).
-__global__ void __launch_bounds__(HQ_THREADS) nn_decide_kernel(Dev d, NNState nn) {
+// With restore_g, a rejected chain also gets back G_0 of X (saved in nn.G0 before the inner
+// sweep), so every chain's G holds G_0 of its final fields without another stack build.
+__global__ void __launch_bounds__(HQ_THREADS) nn_decide_kernel(Dev d, NNState nn, int restore_g) {
   const int c = blockIdx.x, NL = d.n * d.L;
   if (!d.active[c]) return;
   __shared__ int acc;
@@ -414,6 +416,12 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_decide_kernel(Dev d, NNState nn
     double* X = d.X + (size_t)c * NL;
     const double* X0 = nn.X0 + (size_t)c * NL;
     for (int k = threadIdx.x; k < NL; k += HQ_THREADS) X[k] = X0[k];
+    if (restore_g) {
+      const size_t nn2 = (size_t)d.n * d.n;
+      double* G = d.G + (size_t)c * nn2;
+      const double* G0 = nn.G0 + (size_t)c * nn2;
+      for (size_t k = threadIdx.x; k < nn2; k += HQ_THREADS) G[k] = G0[k];
+    }
   }
 }
 
@@ -640,8 +648,8 @@ cudaError_t nn_launch_inner(const Dev& d, const NNState& nn, const CnnState& cn,
   return cudaGetLastError();
 }
 
-cudaError_t nn_launch_decide(const Dev& d, const NNState& nn, cudaStream_t s) {
-  nn_decide_kernel<<<d.n_chains, HQ_THREADS, 0, s>>>(d, nn);
+cudaError_t nn_launch_decide(const Dev& d, const NNState& nn, int restore_g, cudaStream_t s) {
+  nn_decide_kernel<<<d.n_chains, HQ_THREADS, 0, s>>>(d, nn, restore_g);
   return cudaGetLastError();
 }
 

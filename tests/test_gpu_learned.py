@@ -228,3 +228,39 @@ def test_cumulative_window_matches_oracle(hq, window):
         # slices outside every window visited keep their values unless a block move shifted them
         d = Xg[c] - X0[c]
         assert np.all(np.isfinite(d))
+
+
+def test_measured_cumulative_steps_match_oracle_measurements(hq):
+    """Measured cumulative steps: the recorded density, double occupancy and S_CDW(pi,pi) of
+    each step are those of G_0 of the chain's fields after the step (the oracle's fresh G_0),
+    for accepted and rejected steps alike (a rejected step restores the saved G_0)."""
+    from oracle import dqmc, nn
+    p = HolsteinParams(nx=4, ny=4, beta=1.0, seed=43)
+    C, steps = 3, 4
+    X0 = initial_fields(p, C, seed=8)
+    th = scaled_params(7, 2.0)
+    eng = hq.Engine(p, C, max_series=steps)
+    eng.attach_network(4, 8)
+    eng.set_params(th)
+    eng.set_fields(X0)
+    eng.cumulative(n_steps=steps, n_inner=1, measure=True)
+    Xg = eng.get_fields()
+    ser = {k: eng.series(k) for k in (hq.HQ_OBS_DENSITY, hq.HQ_OBS_DOUBLE_OCC, hq.HQ_OBS_SCDW)}
+    thb = nn.to_bfloat16(th.astype(np.float32))
+    expK, _ = dqmc.kinetic_propagators(p)
+    checked = 0
+    for c in range(C):
+        ch = nn.CumulativeChain(p, X0[c], thb, chain=c)
+        recs = []
+        for k in range(steps):
+            ch.step(k, 1)
+            recs.append(dqmc.measure_green(p, dqmc.green_at(p, expK, ch.X, 0)[0]))
+        if not np.array_equal(Xg[c], ch.X):
+            assert ch.min_margin < 1e-4, ch.min_margin
+            continue
+        checked += 1
+        for k in range(steps):
+            for oid, name in ((hq.HQ_OBS_DENSITY, "density"), (hq.HQ_OBS_DOUBLE_OCC, "double_occ"),
+                              (hq.HQ_OBS_SCDW, "s_cdw")):
+                assert abs(ser[oid][c, k] - recs[k][name]) < 1e-9, (c, k, name)
+    assert checked >= 2
