@@ -475,6 +475,7 @@ def run_learned(args):
     lrn.attach_network(4, 8)
     lrn.set_params(theta)
     lrn.set_inner_window(args.window)
+    lrn.set_inner_sites(args.sites)
     if theta_cnn is not None:
         lrn.cnn_set_params(theta_cnn)
     use_cnn = theta_cnn is not None
@@ -515,7 +516,7 @@ def run_learned(args):
     line = {"metric": METRIC, "mode": "learned vs plain", "value": indep_l["s_cdw"],
             "unit": "independent samples/s of S_CDW(pi,pi) (learned)", "higher_is_better": True,
             "dtype": "f64 weights, bf16-weight/fp32 network", "data": "synthetic",
-            "config": {"workload": wname, "chains": C, "n_inner": args.n_inner, "train_samples": int(Xtr.shape[0]),
+            "config": {"workload": wname, "chains": C, "n_inner": args.n_inner, "window": args.window, "sites": args.sites, "train_samples": int(Xtr.shape[0]),
                        "epochs": args.epochs, "lr": args.lr},
             "learned": {"cumulative_steps_per_s": step_rate, "tau_int_steps": tau_l, "indep_samples_per_s": indep_l,
                         "cumulative_acceptance": acc, "inner_local_acceptance": inner_l,
@@ -881,6 +882,7 @@ def run_largest_learned(args):
     lrn.attach_network(4, 8)
     lrn.set_params(theta)
     lrn.set_inner_window(args.window)
+    lrn.set_inner_sites(args.sites)
     lrn.set_fields(X0)
     lrn.cumulative(W, args.n_inner, measure=True)
     torch.cuda.synchronize()
@@ -930,7 +932,8 @@ def run_largest_learned(args):
                        "network": "patch network trained at 8x8 beta=%g (%d samples, %d epochs)"
                                   % (big.beta, Xtr.shape[0], args.epochs),
                        "plain": "local sweeps (no block moves)",
-                       "inner_window_slices": args.window or big.n_slices, "skip_plain": args.skip_plain},
+                       "inner_window_slices": args.window or big.n_slices,
+                       "inner_block_sites": args.sites or big.n_sites, "skip_plain": args.skip_plain},
             "learned": {"steps_per_s": l_rate, "cumulative_acceptance": acc,
                         "tau_int_and_mean": l_tau},
             "plain": {"sweeps_per_s": p_rate, "tau_int_and_mean": p_tau},
@@ -994,6 +997,7 @@ def main():
     ap.add_argument("--deploy", choices=("largest", "medium"), default="largest",
                     help="largest-learned mode: deploy at 16x16 beta=16 or 12x12 beta=8")
     ap.add_argument("--window", type=int, default=0, help="learned modes: local moves per step on this many slices")
+    ap.add_argument("--sites", type=int, default=0, help="learned modes: block moves per step on this many sites")
     ap.add_argument("--skip-plain", action="store_true", help="largest-learned mode: learned sampler only")
     ap.add_argument("--plain-full", action="store_true",
                     help="largest-learned mode: also time one full plain sweep (minutes at 16x16)")

@@ -335,6 +335,11 @@ int hq_get_learned_stats(hq_engine* e, hq_learned_stats* out);
  * and a higher cumulative acceptance at the same exact-weight cost per step.  0 (default) or
  * slices >= L: every slice.  Errors: HQ_EINVAL for a null engine or slices < 0. */
 int hq_set_inner_window(hq_engine* e, int slices);
+/* The same for block moves: with sites > 0 (and < N) each inner sweep's block moves visit only
+ * `sites` consecutive sites j0, j0 + 1, ... (mod N, site index order), j0 = floor(u N) with u
+ * the second uniform of event 1 of the step's tag-4 block.  0 (default) or sites >= N: every
+ * site.  Errors: HQ_EINVAL for a null engine or sites < 0. */
+int hq_set_inner_sites(hq_engine* e, int sites);
 
 /* ------------------------------------------------------------------------------------
  * Convolutional action for block moves (paper, "Global Updates": a convolutional network on

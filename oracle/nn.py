@@ -226,7 +226,7 @@ class CumulativeChain:
         self.min_margin = min(self.min_margin, abs(u - prob) / max(prob, 1e-300))
         return bool(u < prob)
 
-    def step(self, k, n_inner, local=True, block=True, window=0):
+    def step(self, k, n_inner, local=True, block=True, window=0, site_window=0):
         """One cumulative step.  The inner moves run forward (local moves l, i ascending, then
         block moves i ascending) or as the exact reverse of that sequence, each with
         probability 1/2 (second uniform of the step's tag-4 Philox block): a fixed order of
@@ -234,15 +234,22 @@ class CumulativeChain:
 
         window > 0 (and < L): the local moves visit only `window` consecutive slices starting at
         l0 = floor(u L), u the first uniform of event 1 of the step's tag-4 block (chosen
-        independently of the fields, so each window's sequence is reversible on its own)."""
+        independently of the fields, so each window's sequence is reversible on its own).
+        site_window > 0 (and < N): the block moves visit only `site_window` consecutive sites
+        (index order, periodic) from j0 = floor(v N), v the second uniform of that block."""
         p, X = self.p, self.X
         L, N = X.shape
         W = window if 0 < window < L else L
-        l0 = 0
-        if W < L:
-            wu, _ = proposal_uniforms(p.seed, self.chain, k, [1], TAG_CUMULATIVE)
-            l0 = min(int(float(wu[0]) * L), L - 1)
+        Wb = site_window if 0 < site_window < N else N
+        l0 = j0 = 0
+        if W < L or Wb < N:
+            wu, wv = proposal_uniforms(p.seed, self.chain, k, [1], TAG_CUMULATIVE)
+            if W < L:
+                l0 = min(int(float(wu[0]) * L), L - 1)
+            if Wb < N:
+                j0 = min(int(float(wv[0]) * N), N - 1)
         slices = [(l0 + j) % L for j in range(W)]
+        sites = [(j0 + j) % N for j in range(Wb)]
         X0 = X.copy()
         ld0 = self.logdet
         path = 0.0
@@ -266,7 +273,8 @@ class CumulativeChain:
                                 path += dF
                 if part == "block" and block:
                     u1, u2 = proposal_uniforms(p.seed, self.chain, isw, np.arange(N), TAG_NN_BLOCK)
-                    for i in order(N):
+                    for jb in order(Wb):
+                        i = sites[jb]
                         dx = p.dx_global * (2.0 * u1[i] - 1.0)
                         dS = dqmc.global_action_change(p, X, i, dx)
                         dF = self.cnn.delta_block(X, i, dx) if self.cnn is not None else self.act.delta_block(X, i, dx)

@@ -105,6 +105,7 @@ _SIGNATURES = {
     "hq_nn_gradient": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _P(ctypes.c_float), _dp]),
     "hq_cumulative_sweep": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint]),
     "hq_set_inner_window": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "hq_set_inner_sites": (ctypes.c_int, [_vp, ctypes.c_int]),
     "hq_cnn_set_params": (ctypes.c_int, [_vp, _P(ctypes.c_float)]),
     "hq_cnn_get_params": (ctypes.c_int, [_vp, _P(ctypes.c_float), ctypes.c_int]),
     "hq_cnn_eval": (ctypes.c_int, [_vp, _dp]),
@@ -353,6 +354,10 @@ class Engine:
     def set_inner_window(self, slices):
         """Local moves of each cumulative step on `slices` consecutive slices (0: all)."""
         self._check(self.lib.hq_set_inner_window(self._h, int(slices)), "hq_set_inner_window")
+
+    def set_inner_sites(self, sites):
+        """Block moves of each cumulative step on `sites` consecutive sites (0: all)."""
+        self._check(self.lib.hq_set_inner_sites(self._h, int(sites)), "hq_set_inner_sites")
 
     # convolutional action (block moves)
     def cnn_set_params(self, theta):

@@ -49,6 +49,7 @@ struct hq_engine {
   int nn_max_batch = 0, nn_max_samples = 0;
   int cn_t_step = 0;
   int nn_window = 0;  // local moves of a cumulative step on this many slices (0: all)
+  int nn_site_window = 0;  // block moves of a cumulative step on this many sites (0: all)
   long long cum_steps = 0;
   int nn_t_step = 0;
   ~hq_engine() {
@@ -1086,7 +1087,7 @@ int hq_cumulative_sweep(hq_engine* e, int n_steps, int n_inner, unsigned flags) 
     if (use_cnn) rc = rc ? rc : cuda_check(e, hq::cnn_launch_eval(d, e->cn, d.X, e->cn.F, 1, e->stream), "cnn eval");
     rc = rc ? rc : cuda_check(e, hq::nn_launch_inner(d, e->nn, e->cn, n_inner, (flags & HQ_LOCAL) ? 1 : 0,
                                                      (flags & HQ_GLOBAL) ? 1 : 0, use_cnn, e->nn_window,
-                                                     e->stream), "nn inner");
+                                                     e->nn_site_window, e->stream), "nn inner");
     e->stack_valid = false;
     rc = rc ? rc : ensure_state(e);  // log|det M(X')| (and G, stack of X')
     // a rejected chain gets back X, log|det M(X)| and, for a measured step, G_0 of X
@@ -1109,6 +1110,12 @@ int hq_cumulative_sweep(hq_engine* e, int n_steps, int n_inner, unsigned flags) 
 int hq_set_inner_window(hq_engine* e, int slices) {
   if (!e || slices < 0) return HQ_EINVAL;
   e->nn_window = slices >= e->d.L ? 0 : slices;
+  return HQ_OK;
+}
+
+int hq_set_inner_sites(hq_engine* e, int sites) {
+  if (!e || sites < 0) return HQ_EINVAL;
+  e->nn_site_window = sites >= e->d.n ? 0 : sites;
   return HQ_OK;
 }
 

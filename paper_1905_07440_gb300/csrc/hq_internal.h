@@ -170,10 +170,10 @@ cudaError_t nn_launch_set(const NNState& nn, const float* src_device, cudaStream
 cudaError_t nn_launch_batch(const Dev& d, const NNState& nn, const double* Xs, const double* ys, const int* idx,
                             int B, float lr, int t_step, cudaStream_t s);
 cudaError_t nn_launch_loss(const NNState& nn, const double* ys, const int* idx, int B, double scale, cudaStream_t s);
-// Inner network sweeps; window > 0 limits local moves to `window` consecutive slices from a
-// random start per step.
+// Inner network sweeps; window > 0 limits local moves to `window` consecutive slices and
+// site_window > 0 block moves to `site_window` consecutive sites, from random starts per step.
 cudaError_t nn_launch_inner(const Dev& d, const NNState& nn, const CnnState& cn, int n_inner, int do_local,
-                            int do_block, int use_cnn, int window, cudaStream_t s);
+                            int do_block, int use_cnn, int window, int site_window, cudaStream_t s);
 cudaError_t cnn_launch_eval(const Dev& d, const CnnState& cn, const double* X, double* F, int write_cache,
                             cudaStream_t s);
 cudaError_t cnn_launch_set(const CnnState& cn, const float* src_device, cudaStream_t s);

@@ -198,7 +198,8 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_eval_kernel(Dev d, NNState nn, 
 // valid on entry; with use_cnn each network's cache is rebuilt before its part when the other
 // part has changed the fields.
 __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn, CnnState cn, int n_inner,
-                                                              int do_local, int do_block, int use_cnn, int window) {
+                                                              int do_local, int do_block, int use_cnn, int window,
+                                                              int site_window) {
   extern __shared__ __align__(16) char nraw[];
   const int c = blockIdx.x, n = d.n, L = d.L, NL = n * L;
   if (!d.active[c]) return;
@@ -229,15 +230,22 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
   double du1, du2;
   proposal_uniforms(key0, key1, 0u, step, chain, 4u, du1, du2);
   const bool fwd = du2 < 0.5;
-  // local moves on W consecutive slices from a random start l0 (event 1 of the step's tag-4
-  // stream; independent of the fields, so each window's move sequence stays reversible)
+  // local moves on W consecutive slices from a random start l0, block moves on Wb consecutive
+  // sites (in index order, periodic) from a random start j0: the two uniforms of event 1 of
+  // the step's tag-4 stream, independent of the fields, so each window's move sequence stays
+  // reversible
   const int W = (window > 0 && window < L) ? window : L;
-  int l0 = 0;
-  if (W < L) {
+  const int Wb = (site_window > 0 && site_window < n) ? site_window : n;
+  int l0 = 0, j0 = 0;
+  if (W < L || Wb < n) {
     double wu1, wu2;
     proposal_uniforms(key0, key1, 1u, step, chain, 4u, wu1, wu2);
     l0 = (int)(wu1 * (double)L);
     if (l0 > L - 1) l0 = L - 1;
+    j0 = (int)(wu2 * (double)n);
+    if (j0 > n - 1) j0 = n - 1;
+    if (W == L) l0 = 0;
+    if (Wb == n) j0 = 0;
   }
   for (int u = 0; u < n_inner; ++u) {
     const uint32_t isw = step * (uint32_t)n_inner + (uint32_t)u;
@@ -304,8 +312,8 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
         cn_forward_all(d, s.cw, X, nn.x0, h1c, h2c, o3c, s.red);
         cn_stale = false;
       }
-      for (int i0 = 0; i0 < n; ++i0) {
-        const int i = fwd ? i0 : n - 1 - i0;
+      for (int i0 = 0; i0 < Wb; ++i0) {
+        const int i = (j0 + (fwd ? i0 : Wb - 1 - i0)) % n;
         if (threadIdx.x == 0) {
           double u1, u2;
           proposal_uniforms(key0, key1, (uint32_t)i, isw, chain, 3u, u1, u2);
@@ -382,7 +390,7 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
     long long* cnt = nn.counters + (size_t)c * kNNCounters;
     cnt[0] += (long long)n_inner * (do_local ? W * n : 0);
     cnt[1] += nl_acc;
-    cnt[2] += (long long)n_inner * (do_block ? n : 0);
+    cnt[2] += (long long)n_inner * (do_block ? Wb : 0);
     cnt[3] += nb_acc;
     nn.dFpath[c] = path;
   }
@@ -641,10 +649,11 @@ cudaError_t nn_launch_eval(const Dev& d, const NNState& nn, const double* X, dou
 }
 
 cudaError_t nn_launch_inner(const Dev& d, const NNState& nn, const CnnState& cn, int n_inner, int do_local,
-                            int do_block, int use_cnn, int window, cudaStream_t s) {
+                            int do_block, int use_cnn, int window, int site_window, cudaStream_t s) {
   const size_t sb = nn_smem_bytes(d.n, use_cnn != 0);
   smem_opt_in((const void*)nn_inner_kernel, sb);
-  nn_inner_kernel<<<d.n_chains, HQ_THREADS, sb, s>>>(d, nn, cn, n_inner, do_local, do_block, use_cnn, window);
+  nn_inner_kernel<<<d.n_chains, HQ_THREADS, sb, s>>>(d, nn, cn, n_inner, do_local, do_block, use_cnn, window,
+                                                      site_window);
   return cudaGetLastError();
 }
 

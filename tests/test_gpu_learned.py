@@ -200,9 +200,10 @@ def test_trained_network_sampler_agrees_with_plain_and_accepts(hq):
         assert abs(a - b) < 4 * math.hypot(ea, eb), (oid, a, b, ea, eb, rates)
 
 
-@pytest.mark.parametrize("window", [3, 7])
-def test_cumulative_window_matches_oracle(hq, window):
-    """Cumulative steps whose local moves visit a random window of slices follow the oracle."""
+@pytest.mark.parametrize("window,sites", [(3, 0), (7, 0), (0, 5), (4, 6)])
+def test_cumulative_window_matches_oracle(hq, window, sites):
+    """Cumulative steps whose local moves visit a random window of slices and whose block
+    moves visit a random run of sites follow the oracle."""
     from oracle import nn
     p = HolsteinParams(nx=4, ny=4, beta=1.0, seed=37)
     C = 3
@@ -212,15 +213,17 @@ def test_cumulative_window_matches_oracle(hq, window):
     eng.attach_network(4, 8)
     eng.set_params(th)
     eng.set_inner_window(window)
+    eng.set_inner_sites(sites)
     eng.set_fields(X0)
     eng.cumulative(n_steps=3, n_inner=1)
     Xg = eng.get_fields()
     stats = eng.learned_stats()
     thb = nn.to_bfloat16(th.astype(np.float32))
     for c in range(C):
-        assert stats[c]["inner_local_proposed"] == 3 * window * p.n_sites
+        assert stats[c]["inner_local_proposed"] == 3 * (window or p.n_slices) * p.n_sites
+        assert stats[c]["inner_block_proposed"] == 3 * (sites or p.n_sites)
         ch = nn.CumulativeChain(p, X0[c], thb, chain=c)
-        acc = sum(ch.step(k, 1, window=window)[1] for k in range(3))
+        acc = sum(ch.step(k, 1, window=window, site_window=sites)[1] for k in range(3))
         if np.array_equal(Xg[c], ch.X):
             assert stats[c]["cumulative_accepted"] == acc
         else:
