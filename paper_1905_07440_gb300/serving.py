@@ -179,18 +179,18 @@ class Server:
 
     def run(self, requests, sleep=1e-4):
         """Serve requests arriving at their `arrival` times (seconds from the start)."""
-        todo = sorted(requests, key=lambda r: r.arrival)
+        queued = sorted(requests, key=lambda r: r.arrival)
         t0 = self.clock()
         k = 0
-        while k < len(todo) or self.pending():
+        while k < len(queued) or self.pending():
             now = self.clock() - t0
-            while k < len(todo) and todo[k].arrival <= now:
-                todo[k].arrival = t0 + todo[k].arrival
-                self.submit(todo[k])
+            while k < len(queued) and queued[k].arrival <= now:
+                queued[k].arrival = t0 + queued[k].arrival
+                self.submit(queued[k])
                 k += 1
             self.poll()
-            if k < len(todo) and not self.pending():
-                time.sleep(min(sleep, max(0.0, todo[k].arrival - (self.clock() - t0))))
+            if k < len(queued) and not self.pending():
+                time.sleep(min(sleep, max(0.0, queued[k].arrival - (self.clock() - t0))))
         self.close()
         return self.finished
 
