@@ -89,3 +89,23 @@ def test_linear_closed_form():
     X = act.x0 + np.abs(random_fields(p, 1, seed=3)[0])
     ref = prm["W3"].sum() * w.sum() * np.sum(X - act.x0)
     assert abs(act.F(X) - ref) < 1e-10 * abs(ref)
+
+
+def test_full_windows_equal_the_full_sweep():
+    """A slice window of L and a site window of N are the full inner sweep: same fields, same
+    p_c, same decisions; a smaller window only moves points inside it."""
+    p = HolsteinParams(nx=4, ny=4, beta=0.6, seed=19)
+    th = nn.init_params(3)
+    th[-nn.N_H - 1:] *= 10.0
+    X0 = random_fields(p, 1, seed=5, offset=-1.4)[0]
+    a = nn.CumulativeChain(p, X0, th, chain=2)
+    b = nn.CumulativeChain(p, X0, th, chain=2)
+    for k in range(2):
+        ra = a.step(k, 1)
+        rb = b.step(k, 1, window=p.n_slices, site_window=p.n_sites)
+        assert ra == rb
+        assert np.array_equal(a.X, b.X)
+    c = nn.CumulativeChain(p, X0, th, chain=2)
+    c.step(0, 1, local=True, block=False, window=2)
+    moved = np.any(c.X != X0, axis=1)
+    assert moved.sum() <= 2   # only the two slices of the window can change
