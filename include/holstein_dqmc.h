@@ -323,7 +323,8 @@ int hq_nn_gradient(hq_engine* e, const double* X_device, const double* y_device,
 /* n_steps cumulative steps of every chain: n_inner network-driven sweeps (flags HQ_LOCAL:
  * a local move at every (l, i); HQ_GLOBAL: a block move at every site, with HQ_CNN_BLOCK on
  * F_cnn), then the exact accept of the cumulative move; HQ_MEASURE also records electronic
- * observables after each step (one more stabilised G per step).  Asynchronous.
+ * observables of G_0 after each step (G_0 of the starting fields is kept, so a rejected chain
+ * needs no second stabilised determinant).  Asynchronous.
  * Errors: HQ_EINVAL for bad arguments, HQ_CNN_BLOCK without convolutional parameters, or no
  * attached network state. */
 int hq_cumulative_sweep(hq_engine* e, int n_steps, int n_inner, unsigned flags);
