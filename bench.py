@@ -1,16 +1,21 @@
-"""Benchmark of the GB300 Holstein DQMC engine (plain DQMC, batched chains).
+"""Benchmark of the GB300 Holstein DQMC engine.
 
-Workload (default): 8x8 periodic lattice (N = 64), t = M = Omega = 1, g = sqrt(2),
-mu = -2 (half filling), beta = 8, dtau = 0.1 (L = 80), 256 independent chains, delayed
-rank k = 16, n_wrap = 10; one step = one sweep of every chain: local moves at every
-(l, i) with dX ~ U[-0.5, 0.5), then one block move per site with dX ~ U[-1, 1) accepted
-on the full stabilised determinant ratio.  FP64 throughout.  Fields start i.i.d.
-N(0, 1/(M Omega^2)) from seed 20190517 + chain id (synthetic; the paper has no dataset).
+Default (the headline): learned vs plain sampling at the largest lattice, 16x16 periodic
+(N = 256), t = M = Omega = 1, g = sqrt(2), mu = -2 (half filling), beta = 16, dtau = 0.1
+(L = 160), 64 chains per GPU.
+  * Learned sampler: cumulative steps of the patch network (local moves on a window of 32
+    consecutive slices, a block move at every site), each accepted on the exact FP64
+    log|det M|.  The network is trained first on plain-sampler configurations at 8x8 (same
+    beta and couplings) by the library's tensor-core kernels.
+  * Plain sampler: a full sweep (local moves at every (l, i), one block move per site on the
+    full stabilised determinant), timed with block moves on a run of sites and scaled per
+    move; its independent samples/s are bounded by one per sweep.
+Metric: independent samples/s (tau_int-corrected, tau_int from the series of this run) of the
+learned sampler, with the plain sampler's bound and their ratio; one JSON line on rank 0.
+Fields start at the mean field -g/(M Omega^2) + N(0, 1/(M Omega^2)) (synthetic; the paper has
+no dataset).  `--workload batched` is the plain 8x8, beta = 8, 256-chain workload alone.
 
-Metric: chain-sweeps per second over all ranks (every rank runs its own chains: weak
-scaling, no collective on the data path).  Prints one JSON line on rank 0.
-
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload ...]
 """
 import argparse
 import json
@@ -77,6 +82,51 @@ def flops_local_phase(p, acc_rate):
     return L * per_slice + restab
 
 
+def flops_udv_chunk(p, m, first):
+    """One chunk of a stabilised product: m slice applications through the separable
+    exp(-dtau K) with the exp(-dtau V) scaling, Householder QR after the column ordering
+    4/3 N^3, explicit Q 4/3 N^3, T update N^3 (not for the first chunk)."""
+    n = p.n_sites
+    return m * (2.0 * n * n * (p.nx + p.ny) + n * n) + (8.0 / 3.0) * n ** 3 + (0.0 if first else n ** 3)
+
+
+def chunk_sizes_top_down(p, stop=0):
+    """Chunk lengths of the top-down product from L down to the boundary `stop`."""
+    L, nw = p.n_slices, p.n_wrap
+    lo, hi, out = ((L - 1) // nw) * nw, L, []
+    while True:
+        out.append(hi - lo)
+        if lo <= stop:
+            return out
+        hi, lo = lo, lo - nw
+
+
+def split_boundary(p):
+    q = math.ceil(p.n_slices / p.n_wrap)
+    return (q // 2) * p.n_wrap if q >= 2 else 0
+
+
+def flops_split_halves(p):
+    """FP64 flops of one chain in the two-half log|det M| launch: the slices above the
+    boundary m (top down, chunks of n_wrap from the top) and below it (right factors)."""
+    m, nw = split_boundary(p), p.n_wrap
+    top = sum(flops_udv_chunk(p, k, j == 0) for j, k in enumerate(chunk_sizes_top_down(p, m)))
+    bottom = sum(flops_udv_chunk(p, min(nw, m - s0), s0 == 0) for s0 in range(0, m, nw))
+    return top + bottom
+
+
+def flops_split_join(p):
+    """FP64 flops of one chain in the join: two N^3 GEMMs, LU 2/3 N^3, solve 2 N^3, GEMM 2 N^3."""
+    n = p.n_sites
+    return (4.0 + 2.0 / 3.0 + 2.0 + 2.0) * n ** 3
+
+
+def flops_stack_build(p):
+    """FP64 flops of one chain's stack build: the whole top-down product, LU and G_0 solve."""
+    n = p.n_sites
+    return sum(flops_udv_chunk(p, k, j == 0) for j, k in enumerate(chunk_sizes_top_down(p))) + (8.0 / 3.0) * n ** 3
+
+
 # -------------------------------------------------------------- CPU baseline
 def _oracle_worker(args):
     params, chain, n_sweeps = args
@@ -101,6 +151,44 @@ def oracle_throughput(params, workers, sweeps_per_worker=1, first_chain=0):
     rate = sum(n / t for n, t in res)
     cpu_s = sum(t for _, t in res)
     return rate, cpu_s
+
+
+def _oracle_learned_worker(args):
+    """One chain of the oracle's learned sampler (seeded random network: its cost per step does
+    not depend on the weights), `steps` cumulative steps timed after the initial log|det M|."""
+    params, chain, steps, window = args
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    import numpy as np
+    from oracle import nn
+    x0 = -params.g / (params.mass * params.omega ** 2)
+    X0 = workloads.initial_fields(params, 1, seed=workloads.DEFAULT_SEED + chain)[0] + x0
+    th = nn.to_bfloat16(nn.init_params(1).astype(np.float32))
+    ch = nn.CumulativeChain(params, X0, th, chain=chain)
+    t0 = time.perf_counter()
+    for k in range(steps):
+        ch.step(k, 1, window=window)
+    return steps, time.perf_counter() - t0
+
+
+def oracle_learned_throughput(params, workers, steps, window, first_chain=0):
+    """Oracle cumulative steps/s with one chain per process (BLAS pinned to one thread)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        res = pool.map(_oracle_learned_worker, [(params, first_chain + w, steps, window) for w in range(workers)])
+    return sum(n / t for n, t in res), sum(t for _, t in res), min(n / t for n, t in res)
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
 
 
 def cpu_count():
@@ -174,10 +262,46 @@ def workload_params(name):
     raise SystemExit(f"unknown workload {name}")
 
 
+def run_reference_headline(args):
+    """The oracle's learned sampler on the headline workload, on the host cores: each step is a
+    bounded sample of one cumulative step of as many chains as there are cores (up to 16).  With
+    no tau_int measured here, samples/s take tau_int = 1/2 step (at most one independent sample
+    per step): an upper bound for the oracle, so the ratio against it is a lower bound."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    big = workloads.LARGEST
+    workers = min(cpu_count(), 16)
+    for _ in range(args.warmup):
+        oracle_learned_throughput(big, workers, 1, args.window)
+    rates, cpu_s = [], 0.0
+    for k in range(args.steps):
+        r, c, _ = oracle_learned_throughput(big, workers, 1, args.window, first_chain=(k * workers) % 64)
+        rates.append(r)
+        cpu_s += c
+    value = statistics.mean(rates)
+    unit = "independent samples/s (S_CDW, tau_int-corrected)"
+    sample = (f"{workers} chains x 1 cumulative step per step of the oracle's learned sampler (16x16, beta=16, "
+              f"window {args.window}), one chain per process, BLAS 1 thread, {cpu_s:.1f} s CPU; tau_int = 1/2 step "
+              f"(upper bound on the oracle's samples/s)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"16x16 beta=16 L=160 64 chains: learned (patch network, window {args.window}) "
+                                   "vs plain", "chains_per_rank": 64},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": workers, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    if args.workload == "headline":
+        return run_reference_headline(args)
     params, chains, wname = workload_params(args.workload)
     cores = cpu_count()
     workers = min(cores, chains)
@@ -373,6 +497,311 @@ def run_ours(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def series_stats(hq, eng, first, names):
+    """Per observable: tau_int (Madras-Sokal, mean over chains), mean and chain error of the
+    series from index `first`, and the second-half minus first-half difference with its error."""
+    import numpy as np
+    out = {}
+    for oid, name in names:
+        ser = eng.series(oid)[:, first:]
+        C, M = ser.shape
+        pcm = ser.mean(axis=1)
+        h = ser[:, M // 2:].mean(axis=1) - ser[:, : M // 2].mean(axis=1)
+        taus = np.array([hq.tau_int(ser[c])[0] for c in range(C)])
+        out[name] = {"tau_int": float(taus.mean()), "tau_int_err": float(taus.std(ddof=1) / math.sqrt(C)),
+                     "mean": float(pcm.mean()), "err": float(pcm.std(ddof=1) / math.sqrt(C)),
+                     "half_diff": float(h.mean()), "half_diff_err": float(h.std(ddof=1) / math.sqrt(C)),
+                     "blocks": [round(float(ser[:, k * M // 8:(k + 1) * M // 8].mean()), 4) for k in range(8)]}
+    return out
+
+
+def run_headline(args):
+    """Learned vs plain at 16x16, beta = 16 (L = 160), 64 chains per GPU (see the module doc)."""
+    rank, world, local_rank = dist_env()
+    big, C = workloads.LARGEST, workloads.LARGEST_RUN["n_chains"]
+    if args.chains:
+        C = args.chains
+    small = big.with_(nx=8, ny=8)
+    x0 = -big.g / (big.mass * big.omega ** 2)
+    W = args.window
+
+    # CPU baseline first (spawned before any CUDA call), rank 0 at N = 1 only: the oracle's
+    # learned sampler on the same workload, one chain per host core
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        workers = min(cpu_count(), 16)
+        rate, cpu_s, slowest = oracle_learned_throughput(big, workers, args.cpu_steps, W)
+        cpu = {"steps_per_s": rate, "per_core_steps_per_s": rate / workers, "cores": workers, "cpu_s": cpu_s,
+               "cpu_model": cpu_model()}
+
+    import numpy as np
+    import torch
+    import paper_1905_07440_gb300 as hq
+    from paper_1905_07440_gb300 import replicas
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", device_id=dev)
+    stream = torch.cuda.Stream(device=dev)
+    first, _ = replicas.shard(C * world, world, rank)
+    names = ((hq.HQ_OBS_X2, "x2"), (hq.HQ_OBS_DOUBLE_OCC, "double_occ"), (hq.HQ_OBS_SCDW, "s_cdw"))
+    K, Wm = args.steps, args.warmup
+    t_all = time.perf_counter()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    with torch.cuda.stream(stream):
+        peak = hq.fp64_peak_tflops(20, stream.cuda_stream, kind=hq.HQ_PROBE_DFMA)
+        dgemm = measure_dgemm(dev)
+        # ---- 1. training data: plain sampler at 8x8 (same beta and couplings), fresh Philox key
+        t0 = time.perf_counter()
+        tr = hq.Engine(small.with_(seed=small.seed + 7), args.train_chains, first_chain=first, device=dev, stream=stream)
+        tr.set_fields(workloads.initial_fields(small, args.train_chains, seed=workloads.DEFAULT_SEED + 5000 + first) + x0)
+        tr.sweep(args.train_warmup)
+        Xs, ys = [], []
+        for _ in range(args.train_snapshots):
+            tr.sweep(1)
+            Xs.append(tr.get_fields())
+            ys.append(tr.log_weight()[1])
+        tr.close()
+        t_data = time.perf_counter() - t0
+        Xtr, ytr = np.concatenate(Xs), np.concatenate(ys)
+        ytr = ytr - ytr.mean()
+        # ---- 2. network training on the tensor cores (lr halved every third of the epochs)
+        net = hq.Engine(small, 1, device=dev, stream=stream)
+        net.attach_network(64, Xtr.shape[0])
+        net.set_params(hq.init_network(args.nn_seed))
+        Xd, yd = torch.from_numpy(Xtr).to(dev), torch.from_numpy(ytr).to(dev)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        losses = []
+        for k in range(3):
+            ep = args.epochs // 3 + (args.epochs % 3 if k == 2 else 0)
+            losses.extend(net.nn_train(Xd, yd, epochs=ep, batch=64, lr=args.lr * 0.5 ** k, seed=args.nn_seed + k))
+        torch.cuda.synchronize(dev)
+        t_train = time.perf_counter() - t1
+        theta = net.get_params()
+        net.close()
+        del Xd, yd
+        # ---- 3. learned sampler at 16x16: relaxation, timed steps, then the tau series
+        lrn = hq.Engine(big, C, first_chain=first, max_series=args.relax + Wm + K + args.tau_steps + 4, device=dev,
+                        stream=stream)
+        lrn.attach_network(4, 8)
+        lrn.set_params(theta)
+        lrn.set_inner_window(W)
+        split_m = lrn.set_logdet_split(0)
+        lrn.set_fields(workloads.initial_fields(big, C, seed=workloads.DEFAULT_SEED + first) + x0)
+        lrn.cumulative(args.relax + Wm, 1, measure=True)
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+        torch.cuda.synchronize(dev)
+        lrn.set_timing(True)
+        lrn.timing()
+        uuid = None
+        try:
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+        except Exception:
+            pass
+        clocks = ClockSampler(uuid)
+        clocks.start()
+        barrier()
+        torch.cuda.synchronize(dev)
+        evs = []
+        for _ in range(K):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lrn.cumulative(1, 1, measure=True)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize(dev)
+        barrier()
+        clk = clocks.stop()
+        phases = lrn.timing()
+        lrn.set_timing(False)
+        t_dev = replicas.max_over_ranks(sum(a.elapsed_time(b) for a, b in evs) / 1e3, dev)
+        step_rate = C * world * K / t_dev
+        lrn.cumulative(args.tau_steps, 1, measure=True)
+        stats = series_stats(hq, lrn, args.relax + Wm, names)
+        st = lrn.learned_stats()
+        acc = sum(x["cumulative_accepted"] for x in st) / max(1, sum(x["cumulative_proposed"] for x in st))
+        # ---- 4. end to end through the C ABI with host buffers (pinned), copies timed
+        Xh = torch.empty(lrn.field_shape, dtype=torch.float64, pin_memory=True).numpy()
+        Xh[:] = lrn.get_fields()
+        barrier()
+        torch.cuda.synchronize(dev)
+        te = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            lrn.set_fields(Xh)
+            lrn.cumulative(1, 1, measure=True)
+            lrn.get_fields(Xh)
+            obs = lrn.observables()
+        t_e2e = replicas.max_over_ranks(time.perf_counter() - te, dev)
+        status_ok = all(o["status"] == 0 for o in obs)
+        Xeq = lrn.get_fields()
+        lrn.close()
+        # ---- 5. plain sampler at 16x16 from the learned chains' fields, fresh Philox key: one
+        # full sweep with block moves on a run of sites, scaled to a block move per site
+        pl = hq.Engine(big.with_(seed=big.seed + 11), C, first_chain=first, device=dev, stream=stream)
+        pl.set_block_sites(args.plain_block_sites)
+        pl.set_fields(Xeq)
+        pl.sweep(1)
+        pl.set_timing(True)
+        pl.timing()
+        pl.sweep(1)
+        ph = pl.timing()
+        pl.set_timing(False)
+        pobs = pl.observables()
+        pl.close()
+        S = min(args.plain_block_sites or big.n_sites, big.n_sites)
+        t_full = (ph["stack_build"][0] + ph["local_chunk"][0] + ph["sweep_end"][0] +
+                  ph["block_moves"][0] * big.n_sites / S) / 1e3
+        t_full = replicas.max_over_ranks(t_full, dev)
+        # ---- 6. the plain batched workload (8x8, beta = 8, 256 chains) as a second line
+        sec = measure_batched(args, hq, dev, stream, world, first, peak, dgemm, steps=args.batched_steps) \
+            if args.batched_steps > 0 else None
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    tau = {k: v["tau_int"] for k, v in stats.items()}
+    indep = {k: step_rate / (2.0 * tau[k]) for k in tau}
+    plain_bound = C * world / t_full
+    # roofline of the dominant kernel of the timed steps
+    dom = max(phases, key=lambda k: phases[k][0])
+    ms, launches = phases[dom]
+    per_launch_s = ms / 1e3 / max(launches, 1)
+    kernel_names = {"split_halves": "split_halves_kernel", "split_join": "split_join_kernel",
+                    "stack_build": "stack_build_kernel", "network_inner": "nn_inner_kernel",
+                    "network_eval": "nn_eval_kernel", "sweep_end": "measure_g0_kernel + sweep_end_kernel"}
+    fl = {"split_halves": C * flops_split_halves(big), "split_join": C * flops_split_join(big),
+          "stack_build": C * flops_stack_build(big)}.get(dom)
+    achieved = fl / per_launch_s / 1e12 if fl else None
+    total_ms = sum(m for m, _ in phases.values())
+    xbytes = 8 * C * big.n_slices * big.n_sites
+    e2e = C * world * args.e2e_steps / t_e2e / (2.0 * tau["s_cdw"])
+    if cpu is not None:
+        cpu = {"value": cpu["steps_per_s"] / (2.0 * tau["s_cdw"]), "unit": "independent samples/s (S_CDW)",
+               "cores": cpu["cores"], "kind": "oracle",
+               "per_core": cpu["per_core_steps_per_s"] / (2.0 * tau["s_cdw"]),
+               "steps_per_s": cpu["steps_per_s"], "cpu_model": cpu["cpu_model"],
+               "sample": f"{cpu['cores']} chains x {args.cpu_steps} cumulative steps of the oracle's learned sampler "
+                         f"(16x16, beta=16, window {W}, random network), one chain per process, BLAS 1 thread, "
+                         f"{cpu['cpu_s']:.1f} s CPU; samples/s with this run's tau_int(S_CDW)"}
+    line = {
+        "metric": METRIC, "value": indep["s_cdw"], "unit": "independent samples/s (S_CDW, tau_int-corrected)",
+        "n_gpus": world, "steps": K, "warmup": Wm, "ms_per_step": t_dev * 1e3 / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 (determinants); bf16 operands / fp32 accumulation "
+                                                          "(network)", "data": "synthetic",
+        "config": {"workload": f"16x16 beta=16 L=160 {C} chains: learned (patch network, window {W}) vs plain",
+                   "lattice": "16x16", "beta": big.beta, "dtau": big.dtau, "L": big.n_slices, "chains_per_rank": C,
+                   "n_wrap": big.n_wrap, "delay_k": big.delay_k, "parallelism": f"replicas x{world}",
+                   "logdet_split_boundary": split_m,
+                   "l2": "flushed (512 MB write) before every timed step; flush outside the events"},
+        "learned": {"chain_steps_per_s": step_rate, "tau_int_steps": tau, "indep_samples_per_s": indep,
+                    "cumulative_acceptance": acc, "observables": stats, "relax_steps": args.relax + Wm,
+                    "measured_steps": K + args.tau_steps,
+                    "stationary_2sigma": all(abs(v["half_diff"]) <= 2.0 * v["half_diff_err"] for v in stats.values())},
+        "plain": {"seconds_per_full_sweep": t_full, "chain_sweeps_per_s": plain_bound,
+                  "indep_samples_per_s_upper_bound": plain_bound,
+                  "protocol": f"local moves at every (l, i) + one block move per site; timed with block moves on "
+                              f"{S} sites and scaled per move; tau_int >= 1/2 sweep bounds the samples/s",
+                  "phases_ms": {k: v[0] for k, v in ph.items() if v[1]},
+                  "block_acceptance": sum(o["global_accepted"] for o in pobs) / max(1, sum(o["global_proposed"] for o in pobs))},
+        "gain_lower_bound": {k: indep[k] / plain_bound for k in indep},
+        "training": {"lattice": "8x8", "samples": int(Xtr.shape[0]), "data_s": t_data, "train_s": t_train,
+                     "epochs": args.epochs, "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+                     "target_variance": float(np.var(ytr))},
+        "e2e": {"value": e2e, "unit": "independent samples/s (S_CDW, tau_int-corrected)",
+                "h2d_bytes_per_step": xbytes, "d2h_bytes_per_step": xbytes + 104 * C,
+                "note": "per step: fields in from pinned host memory (state rebuilt), one cumulative step, fields "
+                        "and observables out"},
+        "gpu_launches": sum(n for _, n in phases.values()) + K,
+        "roofline": {"bound": "alu", "kernel": kernel_names.get(dom, dom), "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "peak_source": "FP64 DFMA probe measured in this run (hq_fp64_peak_tflops)",
+                     "frac_vs_cublas_dgemm": (achieved / dgemm) if (achieved and dgemm) else None,
+                     "cublas_dgemm_tflops": dgemm, "flops_per_launch": fl, "ms_per_launch": per_launch_s * 1e3,
+                     "share": ms / total_ms if total_ms else None},
+        "phases_ms_per_step": {k: v[0] / K for k, v in phases.items() if v[1]},
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "status_ok": status_ok,
+        "batched_plain_8x8": sec,
+        "wall_s": time.perf_counter() - t_all,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def measure_dgemm(dev, n=4096, reps=4):
+    """cuBLAS DGEMM TFLOP/s (torch.matmul in float64), the second FP64 denominator."""
+    import torch
+    x = torch.randn(n, n, dtype=torch.float64, device=dev)
+    y = x @ x
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        y = x @ x
+    b.record()
+    torch.cuda.synchronize(dev)
+    del x, y
+    return 2.0 * n ** 3 * reps / (a.elapsed_time(b) / 1e3) / 1e12
+
+
+def measure_batched(args, hq, dev, stream, world, first, peak, dgemm, steps=5, warmup=3):
+    """The plain batched workload (8x8, beta = 8, L = 80, 256 chains per GPU): device-timed
+    sweeps with the L2 flushed between them, and the roofline of its dominant phase."""
+    import torch
+    from paper_1905_07440_gb300 import replicas
+    params, chains = workloads.BATCHED, workloads.BATCHED_RUN["n_chains"]
+    eng = hq.Engine(params.with_(seed=params.seed + 3), chains, first_chain=first, max_series=warmup + steps + 2,
+                    device=dev, stream=stream)
+    eng.set_fields(workloads.initial_fields(params, chains, seed=workloads.DEFAULT_SEED + first))
+    eng.sweep(warmup)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize(dev)
+    eng.set_timing(True)
+    eng.timing()
+    evs = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        eng.sweep(1)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize(dev)
+    phases = eng.timing()
+    eng.set_timing(False)
+    obs = eng.observables()
+    method = eng.block_move_method
+    eng.close()
+    t_dev = replicas.max_over_ranks(sum(a.elapsed_time(b) for a, b in evs) / 1e3, dev)
+    ms_b, n_b = phases["block_moves"]
+    fl = chains * (params.n_sites * flops_block_move(params, method) + (flops_chunk_build(params) if method == 1 else 0.0))
+    achieved = fl / (ms_b / 1e3 / max(n_b, 1)) / 1e12 if n_b else None
+    acc_l = sum(o["local_accepted"] for o in obs) / max(1, sum(o["local_proposed"] for o in obs))
+    ms_l = phases["local_chunk"][0]
+    fl_l = chains * flops_local_phase(params, acc_l)
+    return {"workload": "batched plain DQMC 8x8 beta=8 L=80", "chains_per_rank": chains,
+            "value": chains * world * steps / t_dev, "unit": UNIT, "ms_per_sweep": t_dev * 1e3 / steps,
+            "roofline_block_moves": {"kernel": "global_phase_kernel", "achieved": achieved, "peak": peak,
+                                     "frac": achieved / peak if achieved else None,
+                                     "frac_vs_cublas_dgemm": achieved / dgemm if achieved else None},
+            "roofline_local_phase": {"kernel": "local_phase_kernel", "achieved": fl_l / (ms_l / 1e3 / steps) / 1e12,
+                                     "frac": fl_l / (ms_l / 1e3 / steps) / 1e12 / peak},
+            "phases_ms_per_sweep": {k: v[0] / steps for k, v in phases.items() if v[1]}}
 
 
 def run_tau(args):
@@ -978,10 +1407,16 @@ def run_peaks():
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", default="batched")
+    ap.add_argument("--workload", default="headline")
+    ap.add_argument("--relax", type=int, default=200, help="headline: learned steps before the measured series")
+    ap.add_argument("--train-chains", type=int, default=256, help="headline: plain chains for training data")
+    ap.add_argument("--cpu-steps", type=int, default=2, help="headline: oracle steps per core in the CPU baseline")
+    ap.add_argument("--e2e-steps", type=int, default=5, help="headline: steps through host buffers")
+    ap.add_argument("--plain-block-sites", type=int, default=16, help="headline: block-move sites timed per plain sweep")
+    ap.add_argument("--batched-steps", type=int, default=5, help="headline: sweeps of the plain 8x8 line (0: skip)")
     ap.add_argument("--chains", type=int, default=0, help="override chains per rank (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--peaks", action="store_true", help="print the FP64/FP32 pipe probes and exit")
@@ -990,13 +1425,13 @@ def main():
     ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--nn-seed", type=int, default=1)
-    ap.add_argument("--train-warmup", type=int, default=30)
+    ap.add_argument("--train-warmup", type=int, default=24)
     ap.add_argument("--train-snapshots", type=int, default=32)
-    ap.add_argument("--tau-steps", type=int, default=150)
+    ap.add_argument("--tau-steps", type=int, default=240)
     ap.add_argument("--cnn", action="store_true", help="learned mode: convolutional action for block moves")
     ap.add_argument("--deploy", choices=("largest", "medium"), default="largest",
                     help="largest-learned mode: deploy at 16x16 beta=16 or 12x12 beta=8")
-    ap.add_argument("--window", type=int, default=0, help="learned modes: local moves per step on this many slices")
+    ap.add_argument("--window", type=int, default=32, help="learned modes: local moves per step on this many slices")
     ap.add_argument("--sites", type=int, default=0, help="learned modes: block moves per step on this many sites")
     ap.add_argument("--skip-plain", action="store_true", help="largest-learned mode: learned sampler only")
     ap.add_argument("--plain-full", action="store_true",
@@ -1034,8 +1469,10 @@ def main():
     if args.tau_sweeps:
         sys.exit(run_tau(args))
     if args.warmup < 3 and args.impl == "ours":
-        print("warning: fewer than 3 warm-up sweeps", file=sys.stderr)
-    sys.exit(run_reference(args) if args.impl == "reference" else run_ours(args))
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        sys.exit(run_reference(args))
+    sys.exit(run_headline(args) if args.workload == "headline" else run_ours(args))
 
 
 if __name__ == "__main__":

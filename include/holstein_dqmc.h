@@ -45,7 +45,7 @@ extern "C" {
 #define HQ_EINVAL (-1)     /* bad argument or parameter set */
 #define HQ_ENOMEM (-2)     /* arena too small / misaligned */
 #define HQ_ECUDA (-3)      /* a CUDA runtime call failed */
-#define HQ_EUNSTABLE (-4)  /* wrap error above tolerance (reported, chain kept) */
+#define HQ_EUNSTABLE (-4)  /* wrap error above wrap_tol at the n_wrap floor (reported, chain kept) */
 #define HQ_ENAN (-5)       /* non-finite G, ratio or log-determinant */
 #define HQ_ETIMEOUT (-6)   /* a bounded device wait expired (chain state incomplete) */
 
@@ -80,7 +80,15 @@ typedef struct hq_params {
   int block_method; /* block-move algorithm: 0 chosen by the FP64 flop model, 1 every slice
                        through the separable exp(-dtau K), 2 chunk propagators (same results
                        up to rounding; hq_autotune measures them) */
-  int reserved;     /* must be 0 */
+  int n_wrap_min;   /* stabilisation back-off floor (with wrap_tol > 0): 1..n_wrap, 0 = 1 */
+  double wrap_tol;  /* stabilisation back-off: 0 off; > 0, after every sweep with local moves
+                       hq_sweep reads whether a chain's largest |G_wrapped - G_fresh| of that
+                       sweep exceeded wrap_tol (one device-to-host read and a stream
+                       synchronisation per sweep), and if so halves n_wrap for the whole engine
+                       (restabilising twice as often; its chains share one chunk structure) down
+                       to n_wrap_min; at the floor the chains concerned get status HQ_EUNSTABLE
+                       and hq_sweep returns HQ_EUNSTABLE (the sweeps are done, the chains kept).
+                       The arena is sized for n_wrap_min. */
 } hq_params;
 
 typedef struct hq_obs {   /* per chain, accumulated since hq_create / hq_restore */
@@ -92,8 +100,9 @@ typedef struct hq_obs {   /* per chain, accumulated since hq_create / hq_restore
   double x_mean, x2;                  /* means over sweeps */
   double max_wrap_error;              /* max over all restabilisations */
   double logdet;                      /* log|det M| of the current fields */
-  int32_t status;                     /* 0, or HQ_ENAN / HQ_ETIMEOUT */
-  int32_t pad;
+  int32_t status;                     /* 0, or HQ_ENAN / HQ_ETIMEOUT / HQ_EUNSTABLE */
+  int32_t n_wrap;                     /* the engine's current restabilisation interval */
+  int64_t wrap_exceeded;              /* sweeps whose largest wrap error exceeded wrap_tol */
 } hq_obs;
 
 typedef struct hq_engine hq_engine;
@@ -143,6 +152,15 @@ int hq_get_series(hq_engine* e, int obs_id, double* out, int* n_out);
 int hq_checkpoint(hq_engine* e, void* buf, size_t* len);
 /* Restore a state written by hq_checkpoint for the same parameters and chain count. */
 int hq_restore(hq_engine* e, const void* buf, size_t len);
+
+/* Block moves of a plain sweep on a run of sites (the reduced protocol for large lattices,
+ * where a block move costs a whole stabilised determinant): with sites > 0 (and < N) each
+ * sweep's block moves visit `sites` consecutive sites j0, j0 + 1, ... (mod N, index order) with
+ * j0 = floor(u N), u the first uniform of event N of the chain's tag-1 Philox block of that
+ * sweep; the moves themselves draw from their site's event as in a full sweep.  0 (default) or
+ * sites >= N: every site.  Applies to hq_sweep and hq_group_sweep.  Errors: HQ_EINVAL for a
+ * null engine or sites < 0. */
+int hq_set_block_sites(hq_engine* e, int sites);
 
 /* Block-move algorithm in use: 0 = every slice applied through the separable exp(-dtau K)
  * per move, 1 = chunk propagators (the n_wrap-slice products kept per chain, updated by a
@@ -221,13 +239,17 @@ int hq_proposal_uniforms(uint64_t seed, uint32_t chain, uint32_t sweep, uint32_t
  * tau, stores W in *window if non-NULL.  n < 2 gives 0.5. */
 double hq_tau_int(const double* series, int n, double c, int* window);
 
-/* Kernel timing of hq_sweep: when enabled, CUDA events on the engine's stream bracket
- * every launch group -- phase 0: stack build (1 launch), 1: local chunks (one launch per
- * n_wrap slices), 2: block moves (1 launch), 3: sweep end (1 launch).
- * hq_get_timing synchronises, returns the milliseconds and launches per phase
- * accumulated since the last call (ms[4], launches[4]) and clears them.  The block-move
- * phase is one persistent launch per sweep (N x n_chains moves). */
-#define HQ_N_PHASES 4
+/* Kernel timing of hq_sweep and hq_cumulative_sweep: when enabled, CUDA events on the
+ * engine's stream bracket every launch group -- phase 0: stack build (1 launch), 1: local phase
+ * (1 persistent launch), 2: block moves (1 persistent launch: N x n_chains moves, or the run of
+ * sites set by hq_set_block_sites), 3: sweep end (with a measured cumulative step also the
+ * measurement launch), 4: the two-half log|det M| of cumulative steps (1 launch, two CTAs per
+ * chain), 5: its join (1 launch), 6: network evaluation of the current fields (patch network,
+ * and the convolutional action when used), 7: the inner network-driven sweep (1 launch).  The
+ * cumulative decide launch is not timed.  hq_get_timing synchronises, returns the milliseconds
+ * and launches per phase accumulated since the last call (ms[HQ_N_PHASES],
+ * launches[HQ_N_PHASES]) and clears them. */
+#define HQ_N_PHASES 8
 int hq_set_timing(hq_engine* e, int enable);
 
 /* CUDA-graph replay of sweeps (no counterpart in the paper; it trims the host's launch cost,
@@ -247,21 +269,22 @@ int hq_get_timing(hq_engine* e, double* ms, int64_t* launches);
  * framework whose own memory pool owns the device (and forbids cudaMalloc/cudaFree next
  * to it), or code that must not allocate once it is running, such as a latency-bound
  * serving loop.  Such a caller passes only its inputs and outputs:
- *   p          model and run shape (as for hq_create; delay_k is not used),
+ *   p          model and run shape (as for hq_create; delay_k is not used but must still be
+ *              valid, 1..32),
  *   n_chains   number of chains, >= 1,
  *   X_device   device pointer, fields X[chain][l][i] (n_chains * L * N doubles, read only),
  *   logdet_device  device pointer, n_chains doubles written with log|det(I + B_L..B_1)|,
  *   stream     cudaStream_t (NULL = legacy default stream); the call is asynchronous.
- * Scratch (kinetic factors, a status word and 7 N x N FP64 matrices per chain) comes from a
+ * The kernel builds the kinetic factors exp(-+dtau K) in shared memory from their closed form,
+ * so the call reads no host memory.  Its scratch (7 N x N FP64 matrices per chain) comes from a
  * file-scope static device array of HQ_NOALLOC_SCRATCH_BYTES = 64 MiB, which every GPU that
- * loads the library holds until the process exits.  Calls needing more (roughly more than
- * 290 chains of N = 64, or 17 of N = 256) are rejected with HQ_ENOMEM and a message in
- * hq_last_error(NULL); invalid parameters give HQ_EINVAL.  The first call on a device looks
- * up the array's device address once for that device; make that first call before any
- * stream capture.  Every call shares the one array, so calls that overlap on the GPU (other
- * streams, other host threads) race on it: serialise them.  Non-finite results show up as
- * NaN/Inf in logdet_device.  The result equals hq_log_weight's log|det M| for the same
- * fields. */
+ * loads the library holds until the process exits.  Calls needing more (more than 292 chains of
+ * N = 64, or 18 of N = 256) are rejected with HQ_ENOMEM and a message in hq_last_error(NULL);
+ * invalid parameters give HQ_EINVAL.  The first call on a device looks up the array's device
+ * address once for that device; make that first call before any stream capture.  Every call
+ * shares the one array, so calls that overlap on the GPU (other streams, other host threads)
+ * race on it: serialise them.  Non-finite results show up as NaN/Inf in logdet_device.  The
+ * result equals hq_log_weight's log|det M| for the same fields. */
 #define HQ_NOALLOC_SCRATCH_BYTES (64u << 20)
 int hq_logdet_noalloc(const hq_params* p, int n_chains, const double* X_device, double* logdet_device,
                       void* stream);
@@ -336,6 +359,17 @@ int hq_get_learned_stats(hq_engine* e, hq_learned_stats* out);
  * and a higher cumulative acceptance at the same exact-weight cost per step.  0 (default) or
  * slices >= L: every slice.  Errors: HQ_EINVAL for a null engine or slices < 0. */
 int hq_set_inner_window(hq_engine* e, int slices);
+/* How a cumulative step computes the exact log|det M(X')| (no counterpart in the paper, which
+ * gives no implementation): mode 1, one CTA per chain builds the whole stabilised product (the
+ * stack build; measured steps record the observables of G_0); mode 2, two CTAs per chain build
+ * the slices above and below a restabilisation boundary m near L/2 at the same time, and a
+ * second launch joins the halves with the two-sided formula of the local sweep's
+ * restabilisation (measured steps record the observables of G_m, an equally valid equal-time
+ * estimator); mode 0 (default) takes mode 2 when two CTAs per chain fit the device's SMs
+ * (2 n_chains <= SMs) and the product has at least two chunks, else mode 1.  Both give the same
+ * log|det M| up to rounding.  Returns the boundary m in use (0 for mode 1) or a negative error:
+ * HQ_EINVAL for a null engine, a mode outside 0..2, or mode 2 with fewer than two chunks. */
+int hq_set_logdet_split(hq_engine* e, int mode);
 /* The same for block moves: with sites > 0 (and < N) each inner sweep's block moves visit only
  * `sites` consecutive sites j0, j0 + 1, ... (mod N, site index order), j0 = floor(u N) with u
  * the second uniform of event 1 of the step's tag-4 block.  0 (default) or sites >= N: every

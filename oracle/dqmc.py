@@ -126,16 +126,17 @@ def slice_order(L, l):
     return list(range(l, L)) + list(range(0, l))
 
 
-def green_at(p, expK, X, l):
-    """(G_l, log|det M|) for fields X[L][N], G_l = (I + B_l..B_1 B_L..B_{l+1})^-1."""
+def green_at(p, expK, X, l, n_wrap=None):
+    """(G_l, log|det M|) for fields X[L][N], G_l = (I + B_l..B_1 B_L..B_{l+1})^-1, with QR every
+    n_wrap products (default p.n_wrap)."""
     L = X.shape[0]
     mats = [slice_matrix(p, expK, X[s]) for s in slice_order(L, l % L)]
-    return green_logdet_from_udv(*udv_chain(mats, p.n_wrap))
+    return green_logdet_from_udv(*udv_chain(mats, n_wrap or p.n_wrap))
 
 
-def log_det_M(p, expK, X):
+def log_det_M(p, expK, X, n_wrap=None):
     """log|det(I + B_L ... B_1)|."""
-    return green_at(p, expK, X, 0)[1]
+    return green_at(p, expK, X, 0, n_wrap)[1]
 
 
 # ------------------------------------------------------------------------ phonon action
@@ -220,9 +221,12 @@ class OracleChain:
         self.chain = int(chain)
         self.sweep_index = int(sweep)
         self.expK, self.expKinv = kinetic_propagators(p)
+        self.n_wrap = p.n_wrap
         self.G, self.logdet = green_at(p, self.expK, self.X, 0)
         self.record = record
         self.moves = []
+        self.wrap_exceeded = 0
+        self.unstable = False
 
     # -- local moves with the fast (rank-1) update, then the wrap
     def local_sweep(self, measure=True):
@@ -257,8 +261,8 @@ class OracleChain:
             d = slice_diagonal(p, X[s])
             G = self.expK @ ((d[:, None] * G) / d[None, :]) @ self.expKinv
             l = s + 1
-            if l % p.n_wrap == 0 or l == L:
-                Gf, ld = green_at(p, self.expK, X, l)
+            if l % self.n_wrap == 0 or l == L:
+                Gf, ld = green_at(p, self.expK, X, l, self.n_wrap)
                 max_err = max(max_err, float(np.max(np.abs(G - Gf))))
                 G = Gf
                 if measure:
@@ -272,18 +276,24 @@ class OracleChain:
         return out
 
     # -- block moves: one per site, each with the full stabilised determinant
-    def global_sweep(self):
+    def global_sweep(self, sites=0):
+        """sites > 0 (and < N): only a run of `sites` consecutive sites (index order, periodic)
+        from j0 = floor(u N), u the first uniform of event N of this sweep's block-move stream."""
         p, X = self.p, self.X
         L, N = X.shape
-        u1, u2 = proposal_uniforms(p.seed, self.chain, self.sweep_index, np.arange(N), TAG_GLOBAL)
+        u1, u2 = proposal_uniforms(p.seed, self.chain, self.sweep_index, np.arange(N + 1), TAG_GLOBAL)
+        order = list(range(N))
+        if 0 < sites < N:
+            j0 = min(int(float(u1[N]) * N), N - 1)
+            order = [(j0 + k) % N for k in range(sites)]
         ld = self.logdet
         acc = 0
-        for i in range(N):
+        for i in order:
             dx = p.dx_global * (2.0 * u1[i] - 1.0)
             dS = global_action_change(p, X, i, dx)
             Xn = X.copy()
             Xn[:, i] += dx
-            ldn = log_det_M(p, self.expK, Xn)
+            ldn = log_det_M(p, self.expK, Xn, self.n_wrap)
             prob = _exp(2.0 * (ldn - ld) - dS)
             accepted = bool(u2[i] < prob)
             if self.record:
@@ -294,19 +304,35 @@ class OracleChain:
                 ld = ldn
                 acc += 1
         self.X = X
-        self.G, self.logdet = green_at(p, self.expK, X, 0)
+        self.G, self.logdet = green_at(p, self.expK, X, 0, self.n_wrap)
         return dict(global_accepted=acc)
 
-    def sweep(self, do_local=True, do_global=True, measure=True):
+    def sweep(self, do_local=True, do_global=True, measure=True, block_sites=0):
         out = {}
         if do_local:
             out.update(self.local_sweep(measure=measure))
         if do_global:
-            out.update(self.global_sweep())
+            out.update(self.global_sweep(sites=block_sites))
         if measure:
             out.update(measure_fields(self.X))
         self.sweep_index += 1
+        if do_local and getattr(self.p, "wrap_tol", 0.0) > 0.0:
+            self._backoff(out["max_wrap_error"])
         return out
+
+    def _backoff(self, err):
+        """Stabilisation back-off (reading of the design notes; the paper defers stabilisation to
+        its references): a sweep whose largest |G_wrapped - G_fresh| exceeds wrap_tol halves the
+        restabilisation interval for the following sweeps, down to n_wrap_min; at that floor the
+        chain is reported unstable."""
+        if err <= self.p.wrap_tol:
+            return
+        self.wrap_exceeded += 1
+        floor = self.p.n_wrap_min if self.p.n_wrap_min > 0 else 1
+        if self.n_wrap <= floor:
+            self.unstable = True
+        else:
+            self.n_wrap = max(floor, self.n_wrap // 2)
 
     def log_weight(self):
         return 2.0 * self.logdet - phonon_action(self.p, self.X)

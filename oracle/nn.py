@@ -208,8 +208,10 @@ class CumulativeChain:
     any decision is kept in min_margin (for parity checks).
     """
 
-    def __init__(self, p, X, theta, chain=0, cnn_theta=None):
+    def __init__(self, p, X, theta, chain=0, cnn_theta=None, record=False):
         self.p = p
+        self.record = record
+        self.moves = []   # with record: every inner move of the last step (state before, proposal, u, decision)
         self.X = np.array(X, dtype=np.float64, copy=True)
         self.chain = int(chain)
         self.act = EffectiveAction(p, theta)
@@ -225,6 +227,11 @@ class CumulativeChain:
     def _decide(self, u, prob):
         self.min_margin = min(self.min_margin, abs(u - prob) / max(prob, 1e-300))
         return bool(u < prob)
+
+    def _log(self, kind, X, where, value, u, dF, accepted):
+        if self.record:
+            self.moves.append(dict(kind=kind, before=X.copy(), where=where, value=value, u=float(u), dF=dF,
+                                   accepted=accepted))
 
     def step(self, k, n_inner, local=True, block=True, window=0, site_window=0):
         """One cumulative step.  The inner moves run forward (local moves l, i ascending, then
@@ -253,8 +260,10 @@ class CumulativeChain:
         X0 = X.copy()
         ld0 = self.logdet
         path = 0.0
+        self.moves = []
         uc, ud = proposal_uniforms(p.seed, self.chain, k, [0], TAG_CUMULATIVE)
         fwd = bool(ud[0] < 0.5)
+        self.last_forward = fwd
         order = (lambda m: range(m)) if fwd else (lambda m: range(m - 1, -1, -1))
         for u in range(n_inner):
             isw = k * n_inner + u
@@ -268,7 +277,9 @@ class CumulativeChain:
                             xn = X[s, i] + p.dx_local * (2.0 * u1[i] - 1.0)
                             dS = dqmc.local_action_change(p, X, s, i, xn)
                             dF = self.act.delta_local(X, s, i, xn)
-                            if self._decide(u2[i], math.exp(min(2.0 * dF - dS, 709.0))):
+                            ok = self._decide(u2[i], math.exp(min(2.0 * dF - dS, 709.0)))
+                            self._log("local", X, (s, i), xn, u2[i], dF, ok)
+                            if ok:
                                 X[s, i] = xn
                                 path += dF
                 if part == "block" and block:
@@ -278,7 +289,9 @@ class CumulativeChain:
                         dx = p.dx_global * (2.0 * u1[i] - 1.0)
                         dS = dqmc.global_action_change(p, X, i, dx)
                         dF = self.cnn.delta_block(X, i, dx) if self.cnn is not None else self.act.delta_block(X, i, dx)
-                        if self._decide(u2[i], math.exp(min(2.0 * dF - dS, 709.0))):
+                        ok = self._decide(u2[i], math.exp(min(2.0 * dF - dS, 709.0)))
+                        self._log("block", X, i, dx, u2[i], dF, ok)
+                        if ok:
                             X[:, i] += dx
                             path += dF
         ld1 = dqmc.log_det_M(p, self.expK, X)

@@ -41,7 +41,8 @@ class hq_params(ctypes.Structure):
                 ("omega", ctypes.c_double), ("mass", ctypes.c_double), ("g", ctypes.c_double),
                 ("beta", ctypes.c_double), ("dtau", ctypes.c_double), ("n_wrap", ctypes.c_int),
                 ("delay_k", ctypes.c_int), ("dx_local", ctypes.c_double), ("dx_global", ctypes.c_double),
-                ("seed", ctypes.c_uint64), ("block_method", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("seed", ctypes.c_uint64), ("block_method", ctypes.c_int), ("n_wrap_min", ctypes.c_int),
+                ("wrap_tol", ctypes.c_double)]
 
 
 class hq_obs(ctypes.Structure):
@@ -50,7 +51,8 @@ class hq_obs(ctypes.Structure):
                 ("global_proposed", ctypes.c_int64), ("global_accepted", ctypes.c_int64),
                 ("density", ctypes.c_double), ("double_occ", ctypes.c_double), ("s_cdw", ctypes.c_double),
                 ("x_mean", ctypes.c_double), ("x2", ctypes.c_double), ("max_wrap_error", ctypes.c_double),
-                ("logdet", ctypes.c_double), ("status", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("logdet", ctypes.c_double), ("status", ctypes.c_int32), ("n_wrap", ctypes.c_int32),
+                ("wrap_exceeded", ctypes.c_int64)]
 
 
 class hq_learned_stats(ctypes.Structure):
@@ -106,6 +108,8 @@ _SIGNATURES = {
     "hq_cumulative_sweep": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint]),
     "hq_set_inner_window": (ctypes.c_int, [_vp, ctypes.c_int]),
     "hq_set_inner_sites": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "hq_set_logdet_split": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "hq_set_block_sites": (ctypes.c_int, [_vp, ctypes.c_int]),
     "hq_cnn_set_params": (ctypes.c_int, [_vp, _P(ctypes.c_float)]),
     "hq_cnn_get_params": (ctypes.c_int, [_vp, _P(ctypes.c_float), ctypes.c_int]),
     "hq_cnn_eval": (ctypes.c_int, [_vp, _dp]),
@@ -124,8 +128,9 @@ _SIGNATURES = {
                                    ctypes.c_int, _dp, _P(ctypes.c_int), _P(ctypes.c_int)]),
     "hq_get_timing": (ctypes.c_int, [_vp, _dp, _P(ctypes.c_int64)]),
 }
-HQ_N_PHASES = 4
-PHASES = ("stack_build", "local_chunk", "block_moves", "sweep_end")
+HQ_N_PHASES = 8
+PHASES = ("stack_build", "local_chunk", "block_moves", "sweep_end", "split_halves", "split_join", "network_eval",
+          "network_inner")
 EXPORTED = tuple(_SIGNATURES)
 
 _lib = None
@@ -159,7 +164,8 @@ class HQError(RuntimeError):
 def make_params(p):
     """hq_params from any object with the workloads.HolsteinParams attributes."""
     return hq_params(p.nx, p.ny, p.t, p.mu, p.omega, p.mass, p.g, p.beta, p.dtau, p.n_wrap, p.delay_k,
-                     p.dx_local, p.dx_global, p.seed, int(getattr(p, "block_method", 0)), 0)
+                     p.dx_local, p.dx_global, p.seed, int(getattr(p, "block_method", 0)),
+                     int(getattr(p, "n_wrap_min", 0)), float(getattr(p, "wrap_tol", 0.0)))
 
 
 def arena_bytes(params, n_chains, max_series=0):
@@ -233,6 +239,8 @@ class Engine:
         return out
 
     def sweep(self, n=1, local=True, global_=True, measure=True):
+        """Raises HQError (code HQ_EUNSTABLE = -4) when the stabilisation back-off reached its floor;
+        the sweeps have run and the chains are kept."""
         flags = (HQ_LOCAL if local else 0) | (HQ_GLOBAL if global_ else 0) | (HQ_MEASURE if measure else 0)
         self._check(self.lib.hq_sweep(self._h, int(n), flags), "hq_sweep")
 
@@ -251,7 +259,7 @@ class Engine:
     def observables(self):
         arr = (hq_obs * self.n_chains)()
         self._check(self.lib.hq_get_observables(self._h, arr), "hq_get_observables")
-        return [{f: getattr(o, f) for f, _ in hq_obs._fields_ if f != "pad"} for o in arr]
+        return [{f: getattr(o, f) for f, _ in hq_obs._fields_} for o in arr]
 
     def series(self, obs_id):
         out = np.full((self.n_chains, max(self.max_series, 1)), np.nan)
@@ -355,6 +363,18 @@ class Engine:
         """Local moves of each cumulative step on `slices` consecutive slices (0: all)."""
         self._check(self.lib.hq_set_inner_window(self._h, int(slices)), "hq_set_inner_window")
 
+    def set_block_sites(self, sites):
+        """Block moves of each plain sweep on a run of `sites` consecutive sites (0: all)."""
+        self._check(self.lib.hq_set_block_sites(self._h, int(sites)), "hq_set_block_sites")
+
+    def set_logdet_split(self, mode):
+        """Exact log|det M| of cumulative steps: 0 automatic, 1 one CTA per chain (G_0), 2 two
+        halves joined at a boundary m (G_m).  Returns m (0 when not split)."""
+        rc = self.lib.hq_set_logdet_split(self._h, int(mode))
+        if rc < 0:
+            self._check(rc, "hq_set_logdet_split")
+        return int(rc)
+
     def set_inner_sites(self, sites):
         """Block moves of each cumulative step on `sites` consecutive sites (0: all)."""
         self._check(self.lib.hq_set_inner_sites(self._h, int(sites)), "hq_set_inner_sites")
@@ -454,9 +474,22 @@ NOALLOC_SCRATCH_BYTES = 64 << 20
 
 def logdet_noalloc(params, X, out, stream=None):
     """hq_logdet_noalloc on caller-owned CUDA tensors: X float64 [chains][L][N], out float64
-    [chains].  The library allocates nothing; its static scratch is shared by all calls."""
+    [chains].  The library allocates nothing; its static scratch is shared by all calls.
+    The tensors are checked here (dtype, shape, device, layout) before the library sees their
+    addresses, since the kernel trusts the sizes it is given."""
+    import torch
+    L, N = int(round(params.beta / params.dtau)), params.nx * params.ny
+    if X.dtype != torch.float64 or out.dtype != torch.float64:
+        raise TypeError("X and out must be float64 tensors")
+    if X.dim() != 3 or tuple(X.shape[1:]) != (L, N) or X.shape[0] < 1:
+        raise ValueError(f"X must have shape [chains][{L}][{N}] for these parameters, got {tuple(X.shape)}")
+    if out.numel() < X.shape[0]:
+        raise ValueError(f"out holds {out.numel()} values, {X.shape[0]} chains need as many")
+    if not (X.is_cuda and out.is_cuda) or X.device != out.device:
+        raise ValueError("X and out must be CUDA tensors on the same device")
+    if not (X.is_contiguous() and out.is_contiguous()):
+        raise ValueError("X and out must be contiguous")
     lib = load_library()
-    assert X.is_cuda and out.is_cuda and X.is_contiguous() and out.is_contiguous()
     rc = lib.hq_logdet_noalloc(ctypes.byref(make_params(params)), int(X.shape[0]), ctypes.c_void_p(X.data_ptr()),
                                ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream or 0))
     if rc != HQ_OK:

@@ -28,7 +28,10 @@ struct hq_engine {
   long long sweeps;     // sweeps run (Philox sweep counter)
   bool stack_valid;     // left stack, G_0 and log|det M| match the fields
   bool logdet_valid;    // log|det M| matches the fields
-  bool green_valid;     // G holds G_0 of the fields
+  bool green_valid;     // G holds G_l of the fields, l = green_slice
+  int green_slice = 0;  // 0 (G_0, after a stack build or a local phase) or the split boundary
+  int split_mode = 0;   // learned steps' log|det M|: 0 automatic, 1 one CTA per chain, 2 two halves
+  int split_auto = 0;   // automatic choice: two halves when 2 chains fit the device's SMs
   std::vector<int> act;  // host mirror of the active flags
   std::string err;
   // optional per-phase timing
@@ -40,8 +43,8 @@ struct hq_engine {
   long long gkey = -1, gwarm = -1;
   std::vector<Span> spans;
   std::vector<cudaEvent_t> spare;
-  double phase_ms[HQ_N_PHASES] = {0, 0, 0, 0};
-  long long phase_launches[HQ_N_PHASES] = {0, 0, 0, 0};
+  double phase_ms[HQ_N_PHASES] = {};
+  long long phase_launches[HQ_N_PHASES] = {};
   // learned effective action (optional)
   bool nn_on = false;
   hq::NNState nn{};
@@ -52,6 +55,7 @@ struct hq_engine {
   int nn_site_window = 0;  // block moves of a cumulative step on this many sites (0: all)
   long long cum_steps = 0;
   int nn_t_step = 0;
+  int backoffs = 0;  // stabilisation back-offs (n_wrap halvings) so far
   ~hq_engine() {
     for (auto& s : spans) { cudaEventDestroy(s.a); cudaEventDestroy(s.b); }
     for (auto ev : spare) cudaEventDestroy(ev);
@@ -66,7 +70,7 @@ thread_local std::string g_call_error;  // message of the last failing call with
 
 struct Layout {
   size_t kin, X, G, logdet, UR, TR, DR, work, stU, stT, stD, Adl, Bdl, acc, tot, series, counters, status, sched, tmp,
-      expV, cmat, cbuf, corr, cid, active, slen;
+      expV, cmat, cbuf, corr, cid, active, slen, flag;
   size_t total;
 };
 
@@ -91,8 +95,15 @@ const char* validate(const hq_params* p, int n_chains, int max_series) {
   if (n_chains < 1) return "n_chains must be >= 1";
   if (max_series < 0) return "max_series must be >= 0";
   if (p->block_method < 0 || p->block_method > 2) return "block_method must be 0, 1 or 2";
-  if (p->reserved != 0) return "reserved must be 0";
+  if (!(p->wrap_tol >= 0.0) || !std::isfinite(p->wrap_tol)) return "wrap_tol must be finite and >= 0";
+  if (p->n_wrap_min < 0 || p->n_wrap_min > p->n_wrap) return "n_wrap_min must be in 0..n_wrap";
   return nullptr;
+}
+
+// Smallest restabilisation interval the engine can reach (the arena is sized for it).
+int n_wrap_floor(const hq_params& p) {
+  if (!(p.wrap_tol > 0.0)) return p.n_wrap;
+  return p.n_wrap_min > 0 ? p.n_wrap_min : 1;
 }
 
 // chunk propagators for block moves: forced by block_method, else by the flop model
@@ -105,7 +116,7 @@ bool use_chunks(const hq_params& p) {
 Layout layout(const hq_params& p, int C, int max_series) {
   Layout l{};
   const size_t n = (size_t)p.nx * p.ny, L = (size_t)n_slices(p), nn = n * n;
-  const size_t nb = (L - 1) / (size_t)p.n_wrap;
+  const size_t nb = (L - 1) / (size_t)n_wrap_floor(p);  // stack boundaries at the smallest n_wrap
   const size_t k = (size_t)p.delay_k;
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes); return o; };
@@ -132,8 +143,9 @@ Layout layout(const hq_params& p, int C, int max_series) {
   l.cid = take(sizeof(uint32_t) * 4 * C);
   l.active = take(sizeof(int) * C);
   l.slen = take(sizeof(int) * C);
+  l.flag = take(sizeof(int));
   if (use_chunks(p)) {
-    const size_t nch = (L + p.n_wrap - 1) / p.n_wrap;
+    const size_t nch = (L + n_wrap_floor(p) - 1) / n_wrap_floor(p);
     l.expV = take(sizeof(double) * C * L * n);
     l.cmat = take(sizeof(double) * C * 2 * nch * nn);
     l.cbuf = take(sizeof(int) * C);
@@ -202,6 +214,33 @@ int ensure_state(hq_engine* e) {
   int rc = cuda_check(e, hq::launch_stack_build(e->d, e->stream), "stack_build launch");
   if (rc) return rc;
   e->stack_valid = e->logdet_valid = e->green_valid = true;
+  e->green_slice = 0;
+  return HQ_OK;
+}
+
+// Split boundary used by the learned steps' exact log|det M| (0: one CTA per chain).
+int split_in_use(const hq_engine* e) {
+  const bool on = e->split_mode == 2 || (e->split_mode == 0 && e->split_auto);
+  return on ? hq::split_point(e->d) : 0;
+}
+
+// log|det M| and G_m of the current fields by the two-half build (the left stack is not
+// rebuilt: it stays invalid).
+int split_state(hq_engine* e, int m) {
+  int rc;
+  {
+    PhaseTimer pt(e, 4, 1);
+    rc = cuda_check(e, hq::launch_split_logdet(e->d, m, 0, e->stream), "split halves launch");
+  }
+  if (rc) return rc;
+  {
+    PhaseTimer pt(e, 5, 1);
+    rc = cuda_check(e, hq::launch_split_logdet(e->d, m, 1, e->stream), "split join launch");
+  }
+  if (rc) return rc;
+  e->stack_valid = false;
+  e->logdet_valid = e->green_valid = true;
+  e->green_slice = m;
   return HQ_OK;
 }
 
@@ -275,6 +314,9 @@ int hq_create(const hq_params* p, int n_chains, int first_chain, int max_series,
   d.cid = (uint32_t*)(a + l.cid);
   d.active = (int*)(a + l.active);
   d.slen = (int*)(a + l.slen);
+  d.wrap_flag = (int*)(a + l.flag);
+  d.wrap_tol = p->wrap_tol;
+  d.n_wrap_min = n_wrap_floor(*p);
   d.use_cm = use_chunks(*p) ? 1 : 0;
   d.n_chunks = (d.L + d.n_wrap - 1) / d.n_wrap;
   if (d.use_cm) {
@@ -310,6 +352,12 @@ int hq_create(const hq_params* p, int n_chains, int first_chain, int max_series,
   e->series_len = 0;
   e->sweeps = 0;
   e->stack_valid = e->logdet_valid = e->green_valid = false;
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      e->split_auto = (2 * n_chains <= sms && hq::split_point(d) > 0) ? 1 : 0;
+  }
   *out = e;
   return HQ_OK;
 }
@@ -368,6 +416,7 @@ int sweep_once(hq_engine* e, unsigned flags) {
     if (rc) return rc;
     e->stack_valid = false;  // fields changed; G_0 and log|det M| are fresh (restabilised at l = L)
     e->logdet_valid = e->green_valid = true;
+    e->green_slice = 0;
   }
   if (do_global) {
     PhaseTimer pt(e, 2, 1);
@@ -388,11 +437,15 @@ int sweep_once(hq_engine* e, unsigned flags) {
 // The host-side state changes of sweep_once without its launches (graph replay).
 void sweep_state(hq_engine* e, unsigned flags) {
   if ((flags & HQ_LOCAL) || !e->logdet_valid) {
-    if (!e->stack_valid) e->stack_valid = e->logdet_valid = e->green_valid = true;
+    if (!e->stack_valid) {
+      e->stack_valid = e->logdet_valid = e->green_valid = true;
+      e->green_slice = 0;
+    }
   }
   if (flags & HQ_LOCAL) {
     e->stack_valid = false;
     e->logdet_valid = e->green_valid = true;
+    e->green_slice = 0;
   }
   if (flags & HQ_GLOBAL) e->stack_valid = e->green_valid = false;
   e->sweeps++;
@@ -405,8 +458,49 @@ void drop_graph(hq_engine* e) {
 }
 }  // namespace
 
+namespace {
+// Stabilisation back-off after a sweep with local moves (wrap_tol > 0): read the flag the
+// sweep-end kernel sets when a chain's largest wrap error exceeded wrap_tol; halve n_wrap for
+// the engine if it is above the floor (the restabilisation boundaries, the stack and the chunk
+// propagators follow from n_wrap and are rebuilt), else report HQ_EUNSTABLE.
+int wrap_backoff(hq_engine* e, bool* unstable) {
+  int flag = 0;
+  int rc = cuda_check(e, cudaMemcpyAsync(&flag, e->d.wrap_flag, sizeof(int), cudaMemcpyDeviceToHost, e->stream),
+                      "wrap flag copy");
+  rc = rc ? rc : cuda_check(e, cudaStreamSynchronize(e->stream), "wrap flag sync");
+  if (rc || !flag) return rc;
+  rc = cuda_check(e, cudaMemsetAsync(e->d.wrap_flag, 0, sizeof(int), e->stream), "wrap flag clear");
+  if (rc) return rc;
+  hq::Dev& d = e->d;
+  if (d.n_wrap <= d.n_wrap_min) {
+    *unstable = true;
+    return HQ_OK;
+  }
+  d.n_wrap = std::max(d.n_wrap_min, d.n_wrap / 2);
+  d.n_bound = (d.L - 1) / d.n_wrap;
+  d.n_chunks = (d.L + d.n_wrap - 1) / d.n_wrap;
+  e->backoffs++;
+  e->stack_valid = e->green_valid = false;  // log|det M| does not depend on n_wrap
+  drop_graph(e);
+  return HQ_OK;
+}
+}  // namespace
+
 int hq_sweep(hq_engine* e, int n_sweeps, unsigned flags) {
   if (!e || n_sweeps < 0 || (flags & ~(HQ_LOCAL | HQ_GLOBAL | HQ_MEASURE))) return HQ_EINVAL;
+  if (e->d.wrap_tol > 0.0 && (flags & HQ_LOCAL)) {
+    // one sweep at a time, each followed by the back-off check
+    bool unstable = false;
+    for (int it = 0; it < n_sweeps; ++it) {
+      int rc = sweep_once(e, flags);
+      rc = rc ? rc : wrap_backoff(e, &unstable);
+      if (rc) return rc;
+    }
+    if (unstable)
+      return set_err(e, HQ_EUNSTABLE, "wrap error above wrap_tol at the smallest n_wrap (" +
+                                          std::to_string(e->d.n_wrap) + "); chains with status HQ_EUNSTABLE");
+    return HQ_OK;
+  }
   for (int it = 0; it < n_sweeps; ++it) {
     if (!e->graphs || e->timing) {
       const int rc = sweep_once(e, flags);
@@ -481,7 +575,7 @@ int hq_log_weight(hq_engine* e, double* logw_host, double* logdet_host) {
 int hq_get_green(hq_engine* e, int chain, double* G_host, int* slice) {
   if (!e || !G_host || chain < 0 || chain >= e->d.n_chains) return HQ_EINVAL;
   int rc = HQ_OK;
-  if (!e->green_valid) {
+  if (!e->green_valid || e->green_slice != 0) {
     e->stack_valid = false;
     rc = ensure_state(e);
     if (rc) return rc;
@@ -538,6 +632,8 @@ int hq_get_observables(hq_engine* e, hq_obs* out) {
     o.max_wrap_error = t[hq::TOT_WRAP];
     o.logdet = ld[c];
     o.status = aborted ? HQ_ETIMEOUT : st[c];
+    o.n_wrap = e->d.n_wrap;
+    o.wrap_exceeded = k[4];
     out[c] = o;
   }
   return HQ_OK;
@@ -589,7 +685,7 @@ int hq_set_active(hq_engine* e, int slot, int active) {
   return rc;
 }
 
-// checkpoint: header, then X, counters, totals, series (host byte order).
+// checkpoint: header (with the current n_wrap), then X, counters, totals, series (host byte order).
 struct CkHeader {
   char magic[8];
   int32_t version, n_chains, first_chain, max_series, series_len, pad;
@@ -615,8 +711,9 @@ int hq_checkpoint(hq_engine* e, void* buf, size_t* len) {
   *len = need;
   const size_t C = (size_t)e->d.n_chains;
   CkHeader h{};
-  std::memcpy(h.magic, "HQCKPT2", 8);
-  h.version = 2;
+  std::memcpy(h.magic, "HQCKPT3", 8);
+  h.version = 3;
+  h.pad = e->d.n_wrap;  // the current restabilisation interval (after any back-off)
   h.n_chains = e->d.n_chains;
   h.first_chain = e->d.first_chain;
   h.max_series = e->d.max_series;
@@ -653,7 +750,8 @@ int hq_restore(hq_engine* e, const void* buf, size_t len) {
   if (!e || !buf || len < sizeof(CkHeader)) return HQ_EINVAL;
   CkHeader h;
   std::memcpy(&h, buf, sizeof h);
-  if (std::memcmp(h.magic, "HQCKPT2", 8) != 0 || h.version != 2) return set_err(e, HQ_EINVAL, "not a checkpoint");
+  if (std::memcmp(h.magic, "HQCKPT3", 8) != 0 || h.version != 3) return set_err(e, HQ_EINVAL, "not a checkpoint");
+  if (h.pad < e->d.n_wrap_min || h.pad > e->p.n_wrap) return set_err(e, HQ_EINVAL, "checkpoint n_wrap out of range");
   if (h.n_chains != e->d.n_chains || h.max_series != e->d.max_series ||
       std::memcmp(&h.params, &e->p, sizeof(hq_params)) != 0)
     return set_err(e, HQ_EINVAL, "checkpoint is for another parameter set or chain count");
@@ -692,6 +790,10 @@ int hq_restore(hq_engine* e, const void* buf, size_t len) {
   if (rc) return rc;
   e->sweeps = h.sweeps;
   e->series_len = h.series_len;
+  e->d.n_wrap = h.pad;
+  e->d.n_bound = (e->d.L - 1) / e->d.n_wrap;
+  e->d.n_chunks = (e->d.L + e->d.n_wrap - 1) / e->d.n_wrap;
+  drop_graph(e);
   e->stack_valid = e->logdet_valid = e->green_valid = false;
   return HQ_OK;
 }
@@ -806,13 +908,7 @@ int hq_logdet_noalloc(const hq_params* p, int n_chains, const double* X_device, 
   d.g = p->g;
   d.dtau = p->dtau;
   d.X = const_cast<double*>(X_device);
-  // kinetic factors on the stack (at most 4 * 16 * 16 doubles), copied into the scratch
-  double kin[4 * hq::kMaxSide * hq::kMaxSide];
-  ring_propagator(d.nx, p->t, p->dtau, +1.0, kin);
-  ring_propagator(d.nx, p->t, p->dtau, -1.0, kin + d.nx * d.nx);
-  ring_propagator(d.ny, p->t, p->dtau, +1.0, kin + 2 * d.nx * d.nx);
-  ring_propagator(d.ny, p->t, p->dtau, -1.0, kin + 2 * d.nx * d.nx + d.ny * d.ny);
-  const cudaError_t st = hq::launch_logdet_noalloc(d, kin, logdet_device, (cudaStream_t)stream);
+  const cudaError_t st = hq::launch_logdet_noalloc(d, logdet_device, (cudaStream_t)stream);
   if (st != cudaSuccess) {
     g_call_error = std::string("hq_logdet_noalloc: ") + cudaGetErrorString(st);
     return HQ_ECUDA;
@@ -1069,12 +1165,20 @@ int hq_cumulative_sweep(hq_engine* e, int n_steps, int n_inner, unsigned flags) 
   const hq::Dev& d = e->d;
   const size_t fbytes = sizeof(double) * (size_t)d.n_chains * d.L * d.n;
   const bool meas = flags & HQ_MEASURE;
+  // the exact log|det M(X')| of every step: one CTA per chain (stack build, G_0), or with few
+  // chains two CTAs per chain (halves above and below the boundary m joined by the two-sided
+  // formula, G_m); measured steps record the observables of that G
+  const int m = split_in_use(e);
   for (int k = 0; k < n_steps; ++k) {
-    // the step needs log|det M(X)|, and for a measured step G_0 of X (kept for rejection)
-    if (!e->logdet_valid || (meas && !e->green_valid)) {
+    // the step needs log|det M(X)|, and for a measured step G of X at the slice used (kept for
+    // rejection)
+    if (m > 0) {
+      if (!e->logdet_valid || (meas && !(e->green_valid && e->green_slice == m))) rc = split_state(e, m);
+    } else if (!e->logdet_valid || (meas && !(e->green_valid && e->green_slice == 0))) {
+      e->stack_valid = e->stack_valid && e->green_slice == 0 && e->green_valid;
       rc = ensure_state(e);
-      if (rc) return rc;
     }
+    if (rc) return rc;
     if (meas)
       rc = cuda_check(e, cudaMemcpyAsync(e->nn.G0, d.G, sizeof(double) * (size_t)d.n_chains * d.n * d.n,
                                          cudaMemcpyDeviceToDevice, e->stream), "G0 copy");
@@ -1083,28 +1187,51 @@ int hq_cumulative_sweep(hq_engine* e, int n_steps, int n_inner, unsigned flags) 
     rc = rc ? rc : cuda_check(e, cudaMemcpyAsync(e->nn.ld0, d.logdet, sizeof(double) * d.n_chains,
                                                  cudaMemcpyDeviceToDevice, e->stream), "ld0 copy");
     // caches of the current fields (the previous step may have restored X)
-    rc = rc ? rc : cuda_check(e, hq::nn_launch_eval(d, e->nn, d.X, e->nn.F0, 1, e->stream), "nn eval F0");
-    if (use_cnn) rc = rc ? rc : cuda_check(e, hq::cnn_launch_eval(d, e->cn, d.X, e->cn.F, 1, e->stream), "cnn eval");
-    rc = rc ? rc : cuda_check(e, hq::nn_launch_inner(d, e->nn, e->cn, n_inner, (flags & HQ_LOCAL) ? 1 : 0,
-                                                     (flags & HQ_GLOBAL) ? 1 : 0, use_cnn, e->nn_window,
-                                                     e->nn_site_window, e->stream), "nn inner");
+    {
+      PhaseTimer pt(e, 6, use_cnn ? 2 : 1);
+      rc = rc ? rc : cuda_check(e, hq::nn_launch_eval(d, e->nn, d.X, e->nn.F0, 1, e->stream), "nn eval F0");
+      if (use_cnn) rc = rc ? rc : cuda_check(e, hq::cnn_launch_eval(d, e->cn, d.X, e->cn.F, 1, e->stream), "cnn eval");
+    }
+    {
+      PhaseTimer pt(e, 7, 1);
+      rc = rc ? rc : cuda_check(e, hq::nn_launch_inner(d, e->nn, e->cn, n_inner, (flags & HQ_LOCAL) ? 1 : 0,
+                                                       (flags & HQ_GLOBAL) ? 1 : 0, use_cnn, e->nn_window,
+                                                       e->nn_site_window, e->stream), "nn inner");
+    }
+    if (rc) return rc;
     e->stack_valid = false;
-    rc = rc ? rc : ensure_state(e);  // log|det M(X')| (and G, stack of X')
-    // a rejected chain gets back X, log|det M(X)| and, for a measured step, G_0 of X
+    // log|det M(X')| (and G of X')
+    rc = m > 0 ? split_state(e, m) : ensure_state(e);
+    // a rejected chain gets back X, log|det M(X)| and, for a measured step, G of X
     rc = rc ? rc : cuda_check(e, hq::nn_launch_decide(d, e->nn, meas ? 1 : 0, e->stream), "nn decide");
     if (rc) return rc;
     e->stack_valid = false;  // the stack is X''s; rejected chains are back at X
-    e->green_valid = meas;   // measured steps: every chain's G is G_0 of its final fields
+    e->green_valid = meas;   // measured steps: every chain's G is G_m (or G_0) of its final fields
+    e->green_slice = m;
     e->logdet_valid = true;
-    if (meas) {
-      rc = cuda_check(e, hq::launch_measure_g0(d, e->stream), "measure");
-      if (rc) return rc;
+    {
+      PhaseTimer pt(e, 3, meas ? 2 : 1);
+      if (meas) rc = cuda_check(e, hq::launch_measure_g0(d, e->stream), "measure");
+      rc = rc ? rc : cuda_check(e, hq::launch_sweep_end(d, meas ? 1 : 0, e->stream), "sweep_end launch");
     }
-    rc = cuda_check(e, hq::launch_sweep_end(d, meas ? 1 : 0, e->stream), "sweep_end launch");
     if (rc) return rc;
     e->cum_steps++;
   }
   return HQ_OK;
+}
+
+int hq_set_block_sites(hq_engine* e, int sites) {
+  if (!e || sites < 0) return HQ_EINVAL;
+  e->d.block_sites = sites >= e->d.n ? 0 : sites;
+  drop_graph(e);
+  return HQ_OK;
+}
+
+int hq_set_logdet_split(hq_engine* e, int mode) {
+  if (!e || mode < 0 || mode > 2) return HQ_EINVAL;
+  if (mode == 2 && hq::split_point(e->d) == 0) return set_err(e, HQ_EINVAL, "fewer than two restabilisation chunks");
+  e->split_mode = mode;
+  return split_in_use(e);
 }
 
 int hq_set_inner_window(hq_engine* e, int slices) {
@@ -1391,10 +1518,14 @@ int hq_group_sweep(hq_group* g, int n_sweeps, unsigned flags) {
                                                          need_stack ? 1 : 0, g->stream), "group sweep");
     if (rc) break;
     for (hq_engine* e : g->eng) {
-      if (need_stack) e->stack_valid = e->logdet_valid = e->green_valid = true;
+      if (need_stack) {
+        e->stack_valid = e->logdet_valid = e->green_valid = true;
+        e->green_slice = 0;
+      }
       if (do_local) {
         e->stack_valid = false;
         e->logdet_valid = e->green_valid = true;
+        e->green_slice = 0;
       }
       if (do_global) e->stack_valid = e->green_valid = false;
       e->sweeps++;

@@ -12,7 +12,7 @@ constexpr int kMaxK = 32;
 constexpr int kWorkMats = 7;   // per-chain N x N work matrices
 constexpr int kAccSlots = 8;   // per-chain per-sweep accumulators
 constexpr int kTotSlots = 16;  // per-chain running totals
-constexpr int kCounters = 4;   // local proposed / accepted, global proposed / accepted
+constexpr int kCounters = 5;   // local proposed / accepted, global proposed / accepted, wrap_tol exceeded
 constexpr int kSchedHeader = 32;  // block-move task queue: counter, abort flag, then progress[C]
 constexpr int kWorkersPerSm = 2;
 constexpr int kMaxDevices = 64;
@@ -55,7 +55,11 @@ struct Dev {
   uint32_t* cid;      // [C][4] per chain: Philox key (2 words), chain word, sweep/step counter
   int* active;        // [C] 0: the slot takes no work
   int* slen;          // [C] per-sweep records kept for the chain
+  double wrap_tol;    // stabilisation back-off threshold (0: off)
+  int n_wrap_min;     // back-off floor
+  int* wrap_flag;     // [1] set by a chain whose sweep exceeded wrap_tol
   int n_active;       // host count of active slots (sizes the persistent launch)
+  int block_sites;    // block moves per sweep: 0 every site, else a run of this many sites
   // chunk propagators for block moves (used when use_cm != 0)
   int use_cm, n_chunks;
   double* expV;       // [C][L][N] exp(-dtau V) of the current fields
@@ -189,8 +193,15 @@ int lmax_class(int nx, int ny);
 // the stack build first).
 cudaError_t launch_group_sweep(const GroupDev& g, int lmax, size_t sb, int n_active, int flags, int stack,
                                cudaStream_t s);
+// Split boundary of the two-half log|det M| (a restabilisation boundary near L/2), 0 if the
+// product has fewer than two chunks.
+int split_point(const Dev& d);
+// log|det M| and G_m of every chain's fields by two CTAs per chain (slices above and below the
+// boundary m; part 0) joined by the two-sided formula (part 1, after part 0); writes the stack
+// slot of boundary m and the right factors UR, DR, TR (part 0), d.logdet and d.G = G_m (part 1).
+cudaError_t launch_split_logdet(const Dev& d, int m, int part, cudaStream_t s);
 size_t noalloc_scratch_needed(int nx, int ny, int n_chains);
 // log|det M| per chain with all scratch in the library's static device array (no allocation).
-cudaError_t launch_logdet_noalloc(Dev d, const double* kin_host, double* out, cudaStream_t s);
+cudaError_t launch_logdet_noalloc(Dev d, double* out, cudaStream_t s);
 
 }  // namespace hq

@@ -128,10 +128,11 @@ __device__ double finish_logdet(const Dev& d, int c, const Smem& sm, const doubl
 // by pivoted QR after every chunk that ends on a restabilisation boundary.  The field at
 // `site` (if >= 0) is shifted by dx in every slice (block-move proposal).  With `store`
 // the factors at each boundary b > 0 go to the left stack.  Returns log|det M|; with
-// G0 != nullptr also writes G_0 = (I + B_L..B_1)^-1.
+// G0 != nullptr also writes G_0 = (I + B_L..B_1)^-1.  With stop > 0 (a boundary) only the
+// slices above it are taken: the factors end in the stack slot of `stop` and 0 is returned.
 template <int LMAX>
 __device__ double udv_top_down(const Dev& d, int c, const Smem& sm, const double* X, int site, double dx,
-                               bool store, double* G0) {
+                               bool store, double* G0, int stop = 0) {
   const int n = d.n, L = d.L, nw = d.n_wrap;
   double* P = chain_work(d, c, WK_P);
   double* U = chain_work(d, c, WK_U);
@@ -179,11 +180,12 @@ __device__ double udv_top_down(const Dev& d, int c, const Smem& sm, const double
       __syncthreads();
     }
     first = false;
-    if (lo == 0) break;
+    if (lo <= stop) break;
     hi = lo;
     lo -= nw;
   }
-  return finish_logdet(d, c, sm, U, Tc, G0);
+  // with stop > 0 the factors of (B_L .. B_{stop+1})^T are in the stack slot of boundary stop
+  return stop > 0 ? 0.0 : finish_logdet(d, c, sm, U, Tc, G0);
 }
 
 template <int LMAX>
@@ -204,6 +206,76 @@ template <int LMAX>
 __global__ void __launch_bounds__(HQ_THREADS) stack_build_kernel(Dev d) {
   extern __shared__ double smraw[];
   stack_build_body<LMAX>(d, blockIdx.x, smraw);
+}
+
+// ---------------------------------------------- log|det M| from two halves at once
+// For few chains (2 C <= SMs) the stabilised product is built by two CTAs per chain: one takes
+// the slices above the split boundary m (left factors (B_L..B_{m+1})^T into the stack slot of
+// m, exactly as the stack build), the other the slices below it (right factors
+// B_m..B_1 = UR DR TR, as the local phase's restabilisation).  A second launch joins them with
+// the two-sided formula (green_two_sided): log|det M| and G_m.  The per-chain work matrices are
+// shared out so that the halves never touch the same buffer: the top half uses P, U, T, T2,
+// M1; the bottom half M2, M3 and the chain's G (overwritten by the join anyway).
+template <int LMAX>
+__device__ void udv_bottom_half(const Dev& d, int c, const Smem& sm, int m) {
+  const int n = d.n, nw = d.n_wrap;
+  const double* X = d.X + (size_t)c * d.L * n;
+  double* UR = d.UR + (size_t)c * n * n;
+  double* TR = d.TR + (size_t)c * n * n;
+  double* DR = d.DR + (size_t)c * n;
+  double* P = chain_work(d, c, WK_M2);
+  double* Q = chain_work(d, c, WK_M3);
+  double* T2 = d.G + (size_t)c * n * n;
+  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint};
+  for (int s0 = 0; s0 < m; s0 += nw) {
+    const int s1 = s0 + nw < m ? s0 + nw : m;
+    const bool first = (s0 == 0);
+    if (first) set_identity(P, n, n);
+    else copy_scale_cols(P, UR, n, n, DR);
+    __syncthreads();
+    for (int s = s0; s < s1; ++s) {
+      for (int r = threadIdx.x; r < n; r += HQ_THREADS) sm.dl[r] = exp(-d.dtau * (d.g * X[(size_t)s * n + r] - d.mu));
+      __syncthreads();
+      // B_s P = exp(-dtau K) exp(-dtau V_s) P
+      kin_rows<LMAX, KIN_SCALE_BEFORE>(P, n, n, sm.ex, sm.ey, d.nx, d.ny, sm.dl);
+    }
+    prepivot(P, Q, n, n, qs, sm.norm2);
+    qr_householder(Q, n, n, qs);
+    form_q(Q, n, n, UR, qs);
+    t_update(Q, n, n, qs, DR, first ? nullptr : TR, T2);
+    copy_mat(TR, T2, n, n);
+    __syncthreads();
+  }
+}
+
+template <int LMAX>
+__global__ void __launch_bounds__(HQ_THREADS) split_halves_kernel(Dev d, int m) {
+  extern __shared__ double smraw[];
+  const int C = d.n_chains;
+  const int c = blockIdx.x % C;
+  if (!d.active[c]) return;
+  const Smem sm = carve(d, smraw);
+  load_kinetic(d, sm);
+  if (blockIdx.x < C) {
+    udv_top_down<LMAX>(d, c, sm, d.X + (size_t)c * d.L * d.n, -1, 0.0, true, nullptr, m);
+  } else {
+    udv_bottom_half<LMAX>(d, c, sm, m);
+  }
+}
+
+__device__ double green_two_sided(const Dev& d, int c, const Smem& sm, int l, double* Gf);
+
+template <int LMAX>
+__global__ void __launch_bounds__(HQ_THREADS) split_join_kernel(Dev d, int m) {
+  extern __shared__ double smraw[];
+  const int c = blockIdx.x;
+  if (!d.active[c]) return;
+  const Smem sm = carve(d, smraw);
+  const double ld = green_two_sided(d, c, sm, m, d.G + (size_t)c * d.n * d.n);
+  if (threadIdx.x == 0) {
+    d.logdet[c] = ld;
+    flag_nonfinite(d, c, ld);
+  }
 }
 
 // Fresh G_l at boundary l from the right factors (B_l..B_1 = UR DR TR) and, if l < L,
@@ -707,6 +779,24 @@ __device__ double udv_top_down_cm(const Dev& d, int c, const Smem& sm, int site,
   return finish_logdet(d, c, sm, U, Tc, nullptr);
 }
 
+// Sites visited by a sweep's block moves: all N in index order, or with d.block_sites = S
+// (0 < S < N) a run of S consecutive sites (index order, periodic) from j0 = floor(u N), u the
+// first uniform of event N of the chain's block-move (tag 1) Philox block of this sweep -- a
+// start independent of the fields, drawn afresh each sweep.
+__device__ inline int block_move_count(const Dev& d) {
+  return (d.block_sites > 0 && d.block_sites < d.n) ? d.block_sites : d.n;
+}
+
+__device__ inline int block_move_site(const Dev& d, int c, int k) {
+  if (!(d.block_sites > 0 && d.block_sites < d.n)) return k;
+  const uint32_t* id = d.cid + 4 * (size_t)c;
+  double u1, u2;
+  proposal_uniforms(id[0], id[1], (uint32_t)d.n, id[3], id[2], 1u, u1, u2);
+  int j0 = (int)(u1 * (double)d.n);
+  if (j0 > d.n - 1) j0 = d.n - 1;
+  return (j0 + k) % d.n;
+}
+
 // One block move X(site, .) += dX of chain c: Philox draw, dtau dS_ph, the full stabilised
 // log|det M(X')| and the Metropolis decision (all threads of the CTA).
 template <int LMAX>
@@ -775,7 +865,7 @@ __global__ void __launch_bounds__(HQ_THREADS) global_phase_kernel(Dev d) {
   __shared__ int s_task;
   const Smem sm = carve(d, smraw);
   load_kinetic(d, sm);
-  const int C = d.n_chains, ntask = (d.n + (d.use_cm ? 1 : 0)) * C;
+  const int C = d.n_chains, ntask = (block_move_count(d) + (d.use_cm ? 1 : 0)) * C;
   int* counter = d.sched;
   volatile int* abort_flag = d.sched + 1;
   volatile int* progress = d.sched + kSchedHeader;
@@ -806,9 +896,9 @@ __global__ void __launch_bounds__(HQ_THREADS) global_phase_kernel(Dev d) {
     if (d.active[t % C]) {
       if (d.use_cm) {
         if (step == 0) build_chunks<LMAX>(d, sm, t % C);
-        else block_move<LMAX>(d, sm, t % C, step - 1);
+        else block_move<LMAX>(d, sm, t % C, block_move_site(d, t % C, step - 1));
       } else {
-        block_move<LMAX>(d, sm, t % C, step);
+        block_move<LMAX>(d, sm, t % C, block_move_site(d, t % C, step));
       }
     }
     __syncthreads();
@@ -850,6 +940,13 @@ __device__ void sweep_end_body(const Dev& d, int c, int measured, double* red) {
       d.slen[c] = slot + 1;
     }
     d.cid[4 * (size_t)c + 3] += 1u;  // the chain's sweep (or cumulative step) counter
+    if (d.wrap_tol > 0.0 && acc[ACC_WRAP] > d.wrap_tol) {
+      // stabilisation back-off: the host halves n_wrap before the next sweep, or at the floor
+      // reports the chain
+      d.counters[(size_t)c * kCounters + 4] += 1;
+      atomicOr(d.wrap_flag, 1);
+      if (d.n_wrap <= d.n_wrap_min) d.status[c] = HQ_EUNSTABLE;
+    }
     if (has) {
       tot[TOT_DENSITY] += vals[HQ_OBS_DENSITY];
       tot[TOT_DOCC] += vals[HQ_OBS_DOUBLE_OCC];
@@ -909,7 +1006,7 @@ __global__ void __launch_bounds__(HQ_THREADS) group_sweep_kernel(GroupDev g, int
       }
     if (do_global) {
       if (sd.use_cm) build_chunks<LMAX>(sd, sm, c);
-      for (int site = 0; site < sd.n; ++site) block_move<LMAX>(sd, sm, c, site);
+      for (int k = 0, nb = block_move_count(sd); k < nb; ++k) block_move<LMAX>(sd, sm, c, block_move_site(sd, c, k));
     }
     sweep_end_body(sd, c, (meas && do_local) ? 1 : 0, sm.red);
     __syncthreads();
@@ -1035,18 +1132,37 @@ static inline void allow_smem(K kernel, size_t bytes) {
   } while (0)
 
 // ------------------------------------------------- log|det M| without allocation
-// File-scope scratch for hq_logdet_noalloc: the kinetic factors, a status word per chain
-// and kWorkMats N x N work matrices per chain live here instead of in a caller arena.
-// Every GPU that loads the library holds it until the process exits.  All calls share it,
-// so calls that overlap on the GPU race on it.
+// File-scope scratch for hq_logdet_noalloc: kWorkMats N x N work matrices per chain live here
+// instead of in a caller arena.  Every GPU that loads the library holds it until the process
+// exits.  All calls share it, so calls that overlap on the GPU race on it.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// exp(-sgn dtau K_ring) of a ring of m sites (K_ab = -t per displacement +-1) straight into
+// shared memory: the ring is diagonal in plane waves with eigenvalues -2t cos(2 pi q/m), so
+// E_ab = (1/m) sum_q cos(2 pi q (a-b)/m) exp(sgn 2 t dtau cos(2 pi q/m)).
+__device__ inline void ring_propagators_smem(const Dev& d, const Smem& s) {
+  const double two_pi = 6.283185307179586476925286766559;
+  const int a2 = d.nx * d.nx, b2 = d.ny * d.ny;
+  for (int idx = threadIdx.x; idx < 2 * a2 + 2 * b2; idx += HQ_THREADS) {
+    int m, e;
+    double sgn;
+    if (idx < 2 * a2) { m = d.nx; e = idx % a2; sgn = idx < a2 ? 1.0 : -1.0; }
+    else { m = d.ny; e = (idx - 2 * a2) % b2; sgn = idx - 2 * a2 < b2 ? 1.0 : -1.0; }
+    const int a = e / m, b = e % m;
+    double acc = 0.0;
+    for (int q = 0; q < m; ++q)
+      acc += cos(two_pi * q * (a - b) / m) * exp(sgn * 2.0 * d.t * d.dtau * cos(two_pi * q / m));
+    s.ex[idx] = acc / m;  // ex, exi, ey, eyi are contiguous
+  }
+  __syncthreads();
+}
 
 template <int LMAX>
 __global__ void __launch_bounds__(HQ_THREADS) logdet_noalloc_kernel(Dev d, double* out) {
   extern __shared__ double smraw[];
   const int c = blockIdx.x;
   const Smem sm = carve(d, smraw);
-  load_kinetic(d, sm);
+  ring_propagators_smem(d, sm);
   const double* X = d.X + (size_t)c * d.L * d.n;
   const double ld = udv_top_down<LMAX>(d, c, sm, X, -1, 0.0, false, nullptr);
   if (threadIdx.x == 0) out[c] = ld;
@@ -1054,9 +1170,7 @@ __global__ void __launch_bounds__(HQ_THREADS) logdet_noalloc_kernel(Dev d, doubl
 
 size_t noalloc_scratch_needed(int nx, int ny, int n_chains) {
   const size_t n = (size_t)nx * ny;
-  const size_t kin = ((sizeof(double) * (2 * nx * nx + 2 * ny * ny) + 255) / 256) * 256;
-  const size_t st = ((sizeof(int) * (size_t)n_chains + 255) / 256) * 256;
-  return kin + st + sizeof(double) * (size_t)n_chains * kWorkMats * n * n;
+  return sizeof(double) * (size_t)n_chains * kWorkMats * n * n;
 }
 
 // Device address of the scratch on the current device, looked up once per device (the
@@ -1079,20 +1193,14 @@ static cudaError_t noalloc_scratch_address(void** out) {
   return cudaSuccess;
 }
 
-cudaError_t launch_logdet_noalloc(Dev d, const double* kin_host, double* out, cudaStream_t s) {
+cudaError_t launch_logdet_noalloc(Dev d, double* out, cudaStream_t s) {
   void* base = nullptr;
   cudaError_t st = noalloc_scratch_address(&base);
   if (st != cudaSuccess) return st;
-  char* p = (char*)base;
-  const size_t kin_bytes = sizeof(double) * (2 * d.nx * d.nx + 2 * d.ny * d.ny);
-  const size_t kin_span = ((kin_bytes + 255) / 256) * 256;
-  const size_t st_span = ((sizeof(int) * (size_t)d.n_chains + 255) / 256) * 256;
-  d.kin = (const double*)p;
-  d.status = (int*)(p + kin_span);
-  d.work = (double*)(p + kin_span + st_span);
-  st = cudaMemcpyAsync((void*)d.kin, kin_host, kin_bytes, cudaMemcpyHostToDevice, s);
-  if (st == cudaSuccess) st = cudaMemsetAsync(d.status, 0, sizeof(int) * d.n_chains, s);
-  if (st != cudaSuccess) return st;
+  // the kernel builds the kinetic factors in shared memory and needs no status word
+  d.kin = nullptr;
+  d.status = nullptr;
+  d.work = (double*)base;
   HQ_DISPATCH(logdet_noalloc_kernel, d, s, d, out);
   return cudaGetLastError();
 }
@@ -1100,6 +1208,34 @@ cudaError_t launch_logdet_noalloc(Dev d, const double* kin_host, double* out, cu
 cudaError_t launch_stack_build(const Dev& d, cudaStream_t s) {
   HQ_DISPATCH(stack_build_kernel, d, s, d);
   return cudaGetLastError();
+}
+
+int split_point(const Dev& d) {
+  const int q = (d.L + d.n_wrap - 1) / d.n_wrap;
+  return q >= 2 ? (q / 2) * d.n_wrap : 0;
+}
+
+template <int LMAX>
+static cudaError_t launch_split_t(const Dev& d, int m, int part, cudaStream_t s) {
+  const size_t sb = smem_bytes(d);
+  if (part == 0) {
+    allow_smem(split_halves_kernel<LMAX>, sb);
+    split_halves_kernel<LMAX><<<2 * d.n_chains, HQ_THREADS, sb, s>>>(d, m);
+  } else {
+    allow_smem(split_join_kernel<LMAX>, sb);
+    split_join_kernel<LMAX><<<d.n_chains, HQ_THREADS, sb, s>>>(d, m);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_logdet(const Dev& d, int m, int part, cudaStream_t s) {
+  if (m <= 0 || m >= d.L || m % d.n_wrap != 0) return cudaErrorInvalidValue;
+  switch (lmax_of(d.nx, d.ny)) {
+    case 2: return launch_split_t<2>(d, m, part, s);
+    case 4: return launch_split_t<4>(d, m, part, s);
+    case 8: return launch_split_t<8>(d, m, part, s);
+    default: return launch_split_t<16>(d, m, part, s);
+  }
 }
 
 

@@ -12,11 +12,13 @@
 // periodic convolutional action F_cnn in place of F (hq_cnn.cuh).  Each move is reversible for
 // its own weight, so p_c = exp(2 dlog|det M| - 2 sum of the accepted moves' network changes)
 // (the phonon action cancels; for one network the sum telescopes to F(X') - F(X)).
-// Every kernel evaluates f through nn_patch_eval (one 8-lane group per patch, fixed order),
-// so the inner chain and the acceptance see bit-identical values of f.
+// Every kernel evaluates f through nn_tile_f (hq_nn_tc.cuh: 16 patches per warp on the tensor
+// cores, bfloat16 operands, FP32 accumulation), so the inner chain and the acceptance see
+// bit-identical values of f.
 #include <cstdio>
 #include "hq_cnn.cuh"
 #include "hq_device.cuh"
+#include "hq_nn_tc.cuh"
 #include "hq_internal.h"
 #include "../../include/holstein_dqmc.h"
 
@@ -24,8 +26,6 @@ namespace hq {
 
 // parameter layout: W1[25][64], b1[64], W2[64][64], b2[64], W3[64], b3
 constexpr int NN_IN = 25, NN_H = 64;
-constexpr int NN_HP = NN_H + 1;  // padded stride of the groups' hidden rows: the 4 groups of a
-                                 // warp then read h1[v] from 4 different banks
 constexpr int NN_W1 = 0, NN_B1 = NN_IN * NN_H, NN_W2 = NN_B1 + NN_H, NN_B2 = NN_W2 + NN_H * NN_H,
               NN_W3 = NN_B2 + NN_H, NN_B3 = NN_W3 + NN_H, NN_NP = NN_B3 + 1;
 static_assert(NN_NP == HQ_NN_PARAMS, "parameter count");
@@ -33,81 +33,10 @@ constexpr int NN_WPAD = (NN_NP + 3) & ~3;
 constexpr int NN_GROUPS = HQ_THREADS / 8;
 
 
-__device__ inline void load_weights(const uint16_t* wb, float* w) {
-  for (int k = threadIdx.x; k < NN_WPAD; k += HQ_THREADS) w[k] = (k < NN_NP) ? bf16_to_float(wb[k]) : 0.f;
-  __syncthreads();
-}
-
-// f of one patch by the 8 lanes of a group (sub = lane in group): lane `sub` owns hidden units
-// 8 sub .. 8 sub + 7.  z: the patch's 25 inputs, h1: 64 floats of group scratch.  All 32 lanes
-// of the warp must call it together (group shuffles).  Returns f in every lane of the group.
-__device__ __forceinline__ float nn_patch_eval(const float* w, const float* z, float* h1, int sub) {
-  const float* W1 = w + NN_W1;
-  const float* b1 = w + NN_B1;
-  const float* W2 = w + NN_W2;
-  const float* b2 = w + NN_B2;
-  const float* W3 = w + NN_W3;
-  const int u0 = sub * 8;
-  float a[8];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) a[j] = b1[u0 + j];
-  for (int k = 0; k < NN_IN; ++k) {
-    const float zk = z[k];
-    // the lane's 8 weights of this input as two 16-byte loads (fewer shared-memory requests)
-    const float4 wa = *reinterpret_cast<const float4*>(W1 + k * NN_H + u0);
-    const float4 wb = *reinterpret_cast<const float4*>(W1 + k * NN_H + u0 + 4);
-    const float w8[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-#pragma unroll
-    for (int j = 0; j < 8; ++j) a[j] = fmaf(zk, w8[j], a[j]);
-  }
-#pragma unroll
-  for (int j = 0; j < 8; ++j) h1[u0 + j] = fmaxf(a[j], 0.f);
-  __syncwarp();
-  float c[8];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) c[j] = b2[u0 + j];
-  for (int v = 0; v < NN_H; ++v) {
-    const float hv = h1[v];
-    const float4 wa = *reinterpret_cast<const float4*>(W2 + v * NN_H + u0);
-    const float4 wb = *reinterpret_cast<const float4*>(W2 + v * NN_H + u0 + 4);
-    const float w8[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-#pragma unroll
-    for (int j = 0; j < 8; ++j) c[j] = fmaf(hv, w8[j], c[j]);
-  }
-  float o = 0.f;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) o = fmaf(fmaxf(c[j], 0.f), W3[u0 + j], o);
-  o += __shfl_xor_sync(HQ_FULL, o, 4);
-  o += __shfl_xor_sync(HQ_FULL, o, 2);
-  o += __shfl_xor_sync(HQ_FULL, o, 1);
-  __syncwarp();
-  return o + w[NN_B3];
-}
-
-// Inputs of the patch centred at (l, i), with an optional change: points of site `cs` get
-// +cdx on every slice (block move) or, if cl >= 0, only the point (cl, cs) is set to cx.
-__device__ __forceinline__ void fill_patch(const Dev& d, const double* X, int l, int i, double x0, float* z,
-                                           int sub, int cs, int cl, double cx, double cdx) {
-  const int n = d.n, L = d.L, x = i % d.nx, y = i / d.nx;
-  for (int k = sub; k < NN_IN; k += 8) {
-    const int dl = k / 5 - 2, cidx = k % 5;
-    const int cx_ = (cidx == 1) - (cidx == 2), cy_ = (cidx == 3) - (cidx == 4);
-    const int ll = (l + dl + L) % L;
-    const int j = (x + cx_ + d.nx) % d.nx + d.nx * ((y + cy_ + d.ny) % d.ny);
-    double v = X[(size_t)ll * n + j];
-    if (j == cs) {
-      if (cl < 0) v = v + cdx;
-      else if (ll == cl) v = cx;
-    }
-    z[k] = (float)(v - x0);
-  }
-  __syncwarp();
-}
-
 struct NNSmem {
-  float* w;      // [NN_WPAD]
-  float* z;      // [NN_GROUPS][NN_IN + 3]
-  float* h1;     // [NN_GROUPS][NN_HP]
+  uint2* frag;   // [TC_FRAGS] weight fragments of the tensor-core layers
+  float* tcf;    // [TC_FLOATS] b1, b2, W3, b3
+  float* f25;    // [32] f of the patches of a local move
   double* red;   // [HQ_WARPS]
   double* pu2;   // [n] proposal uniforms (local)
   double* pxn;   // [n] proposed values
@@ -119,15 +48,16 @@ struct NNSmem {
 };
 
 __host__ __device__ inline size_t nn_smem_bytes(int n, bool with_cnn = false) {
-  size_t b = sizeof(double) * (HQ_WARPS + 3 * (size_t)n + NN_GROUPS + 8) +
-             sizeof(float) * (NN_WPAD + NN_GROUPS * (NN_IN + 3) + NN_GROUPS * NN_HP);
+  size_t b = sizeof(uint2) * TC_FRAGS + sizeof(double) * (HQ_WARPS + 3 * (size_t)n + NN_GROUPS + 8) +
+             sizeof(float) * (TC_FLOATS + 32);
   if (with_cnn) b += sizeof(float) * CN_WPAD + sizeof(int) * (4 + 3 * CN_WIN + 2 * (size_t)n);
   return b;
 }
 
 __device__ inline NNSmem nn_carve(int n, char* base, bool with_cnn = false) {
   NNSmem s;
-  double* p = (double*)base;
+  s.frag = (uint2*)base;
+  double* p = (double*)(s.frag + TC_FRAGS);
   s.red = p; p += HQ_WARPS;
   s.pu2 = p; p += n;
   s.pxn = p; p += n;
@@ -135,9 +65,8 @@ __device__ inline NNSmem nn_carve(int n, char* base, bool with_cnn = false) {
   s.gacc = p; p += NN_GROUPS;
   s.scal = p; p += 8;
   float* f = (float*)p;
-  s.w = f; f += NN_WPAD;
-  s.z = f; f += NN_GROUPS * (NN_IN + 3);
-  s.h1 = f; f += NN_GROUPS * NN_HP;
+  s.tcf = f; f += TC_FLOATS;
+  s.f25 = f; f += 32;
   s.cw = nullptr;
   if (with_cnn) {
     s.cw = f; f += CN_WPAD;
@@ -149,28 +78,60 @@ __device__ inline NNSmem nn_carve(int n, char* base, bool with_cnn = false) {
   return s;
 }
 
-// F of one configuration by the whole CTA (groups of 8 lanes per patch, fixed order); the
-// patch values go to fc when fc != nullptr.  Returns F in every thread.
-__device__ inline double fc_eval_all(const Dev& d, const NNSmem& s, const double* X, double x0, float* fc) {
+// Input k of the patch centred at (l, i): X at slice l + dl, cross site c (k = 5 (dl + 2) + c),
+// minus the mean field x0.  Optional change: points of site `cs` get + cdx on every slice (block
+// move), or, if cl >= 0, only the point (cl, cs) is set to cx (local move).
+__device__ __forceinline__ float patch_input(const Dev& d, const double* X, int l, int i, int k, double x0, int cs,
+                                             int cl, double cx, double cdx) {
+  const int n = d.n, L = d.L, x = i % d.nx, y = i / d.nx;
+  const int dl = k / 5 - 2, cidx = k % 5;
+  const int cx_ = (cidx == 1) - (cidx == 2), cy_ = (cidx == 3) - (cidx == 4);
+  const int ll = (l + dl + L) % L;
+  const int j = (x + cx_ + d.nx) % d.nx + d.nx * ((y + cy_ + d.ny) % d.ny);
+  double v = X[(size_t)ll * n + j];
+  if (j == cs) {
+    if (cl < 0) v = v + cdx;
+    else if (ll == cl) v = cx;
+  }
+  return (float)(v - x0);
+}
+
+// Warp sum in a fixed order (every lane gets the same bits).
+__device__ __forceinline__ double warp_sum_fixed(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(HQ_FULL, v, o);
+  return v;
+}
+
+// F of one configuration by the whole CTA: warp w takes the tiles of 16 patch rows w, w + 8, ...
+// (fixed order); the patch values go to fc when fc != nullptr.  Returns F in every thread.
+__device__ inline double fc_eval_all(const Dev& d, const NNSmem& s, const NNFrags& w, const double* X, double x0,
+                                     float* fc) {
   const int n = d.n, NL = d.n * d.L;
-  const int g = threadIdx.x / 8, sub = threadIdx.x % 8;
-  float* z = s.z + g * (NN_IN + 3);
-  float* h1 = s.h1 + g * NN_HP;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, g = lane >> 2, t = lane & 3;
   double part = 0.0;
-  for (int base = 0; base < NL; base += NN_GROUPS) {
-    const int row = base + g;
-    const bool on = row < NL;
-    fill_patch(d, X, on ? row / n : 0, on ? row % n : 0, x0, z, sub, -1, -1, 0.0, 0.0);
-    const float f = nn_patch_eval(s.w, z, h1, sub);
-    if (on && sub == 0) {
-      if (fc) fc[row] = f;
-      part += (double)f;
+  for (int base = warp * 16; base < NL; base += HQ_WARPS * 16) {
+    float f0, f1;
+    nn_tile_f(w, [&](int row, int k) {
+      const int r = base + row < NL ? base + row : NL - 1;
+      return patch_input(d, X, r / n, r % n, k, x0, -1, -1, 0.0, 0.0);
+    }, f0, f1);
+    if (t == 0) {
+      if (base + g < NL) {
+        part += (double)f0;
+        if (fc) fc[base + g] = f0;
+      }
+      if (base + g + 8 < NL) {
+        part += (double)f1;
+        if (fc) fc[base + g + 8] = f1;
+      }
     }
   }
-  if (sub == 0) s.gacc[g] = part;
+  part = warp_sum_fixed(part);
+  if (lane == 0) s.gacc[warp] = part;
   __syncthreads();
   double F = 0.0;
-  for (int k = 0; k < NN_GROUPS; ++k) F += s.gacc[k];
+  for (int k = 0; k < HQ_WARPS; ++k) F += s.gacc[k];
   __syncthreads();
   return F;
 }
@@ -181,8 +142,8 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_eval_kernel(Dev d, NNState nn, 
   extern __shared__ __align__(16) char nraw[];
   const int c = blockIdx.x, n = d.n, NL = d.n * d.L;
   const NNSmem s = nn_carve(n, nraw);
-  load_weights(nn.wbf, s.w);
-  const double F = fc_eval_all(d, s, Xall + (size_t)c * NL, nn.x0, write_cache ? nn.fcache + (size_t)c * NL : nullptr);
+  const NNFrags w = nn_build_frags(nn.wbf, s.frag, s.tcf);
+  const double F = fc_eval_all(d, s, w, Xall + (size_t)c * NL, nn.x0, write_cache ? nn.fcache + (size_t)c * NL : nullptr);
   if (threadIdx.x == 0) Fout[c] = F;
 }
 
@@ -204,7 +165,7 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
   const int c = blockIdx.x, n = d.n, L = d.L, NL = n * L;
   if (!d.active[c]) return;
   const NNSmem s = nn_carve(n, nraw, use_cnn != 0);
-  load_weights(nn.wbf, s.w);
+  const NNFrags w = nn_build_frags(nn.wbf, s.frag, s.tcf);
   if (use_cnn) cn_load_weights(cn.wbf, s.cw);
   double* X = d.X + (size_t)c * NL;
   float* fc = nn.fcache + (size_t)c * NL;
@@ -218,9 +179,7 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
     h2p = cn.h2p + (size_t)c * 25 * L * CN_C;
     o3p = cn.o3p + (size_t)c * CN_WIN * L;
   }
-  const int g = threadIdx.x / 8, sub = threadIdx.x % 8;
-  float* z = s.z + g * (NN_IN + 3);
-  float* h1 = s.h1 + g * NN_HP;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, g = lane >> 2, t = lane & 3;
   const uint32_t* id = d.cid + 4 * (size_t)c;
   const uint32_t key0 = id[0], key1 = id[1], chain = id[2], step = id[3];
   long long nl_acc = 0, nb_acc = 0;
@@ -253,7 +212,7 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
     const bool local_part = (part == 0) == fwd;
     if (local_part && do_local) {
       if (fc_stale) {
-        fc_eval_all(d, s, X, nn.x0, fc);
+        fc_eval_all(d, s, w, X, nn.x0, fc);
         fc_stale = false;
       }
       for (int sl0 = 0; sl0 < W; ++sl0) {
@@ -272,19 +231,35 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
         __syncthreads();
         for (int i0 = 0; i0 < n; ++i0) {
           const int i = fwd ? i0 : n - 1 - i0;
-          // the 25 patches containing (sl, i): centres (sl - dl, i - c), one per group
-          float f = 0.f;
-          int row = -1;
-          if (g < 25) {
-            const int dl = g / 5 - 2, cidx = g % 5;
-            const int cx_ = (cidx == 1) - (cidx == 2), cy_ = (cidx == 3) - (cidx == 4);
+          // the 25 patches containing (sl, i): patch q has centre (sl - dl, i - c), q = 5 (dl + 2) + c;
+          // warps 0 and 1 evaluate q = 0..15 and 16..31 (q >= 25: padding)
+          if (warp < 2) {
+            const double xn = s.pxn[i];
             const int x = i % d.nx, y = i / d.nx;
-            const int j = (x - cx_ + d.nx) % d.nx + d.nx * ((y - cy_ + d.ny) % d.ny);
-            row = ((sl - dl + L) % L) * n + j;
+            auto centre = [&](int q) {
+              const int dl = q / 5 - 2, cidx = q % 5;
+              const int cx_ = (cidx == 1) - (cidx == 2), cy_ = (cidx == 3) - (cidx == 4);
+              const int j = (x - cx_ + d.nx) % d.nx + d.nx * ((y - cy_ + d.ny) % d.ny);
+              return ((sl - dl + L) % L) * n + j;
+            };
+            float f0, f1;
+            nn_tile_f(w, [&](int row, int k) {
+              const int q = 16 * warp + row;
+              const int r = centre(q < 25 ? q : 24);
+              return patch_input(d, X, r / n, r % n, k, nn.x0, i, sl, xn, 0.0);
+            }, f0, f1);
+            if (t == 0) {
+              const int q0 = 16 * warp + g, q1 = q0 + 8;
+              if (q0 < 25) {
+                s.f25[q0] = f0;
+                s.gacc[q0] = (double)f0 - (double)fc[centre(q0)];
+              }
+              if (q1 < 25) {
+                s.f25[q1] = f1;
+                s.gacc[q1] = (double)f1 - (double)fc[centre(q1)];
+              }
+            }
           }
-          fill_patch(d, X, row >= 0 ? row / n : 0, row >= 0 ? row % n : 0, nn.x0, z, sub, i, sl, s.pxn[i], 0.0);
-          f = nn_patch_eval(s.w, z, h1, sub);
-          if (sub == 0) s.gacc[g] = (row >= 0) ? (double)f - (double)fc[row] : 0.0;
           __syncthreads();
           if (threadIdx.x == 0) {
             double dF = 0.0;
@@ -300,7 +275,14 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
           }
           __syncthreads();
           if (s.scal[0] != 0.0) {
-            if (row >= 0 && sub == 0) fc[row] = f;
+            if (threadIdx.x < 25) {
+              const int q = threadIdx.x;
+              const int dl = q / 5 - 2, cidx = q % 5;
+              const int cx_ = (cidx == 1) - (cidx == 2), cy_ = (cidx == 3) - (cidx == 4);
+              const int x = i % d.nx, y = i / d.nx;
+              const int j = (x - cx_ + d.nx) % d.nx + d.nx * ((y - cy_ + d.ny) % d.ny);
+              fc[((sl - dl + L) % L) * n + j] = s.f25[q];
+            }
             cn_stale = true;
           }
           __syncthreads();
@@ -335,29 +317,39 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
           cn_build_window(d, i, s.win);
           dF = cn_block_delta(d, s.cw, s.win, X, nn.x0, i, dx, h1c, h2c, o3c, h1p, h2p, o3p, s.red);
         } else {
-          // the 5 L patches containing site i: centres (l, i - c)
+          // the 5 L patches containing site i: patch q has centre (q / 5, i - c), c = q % 5; warp
+          // w takes the tiles w, w + 8, ... of 16 patches
+          auto centre = [&](int q) {
+            const int cidx = q % 5, sl = q / 5;
+            const int cx_ = (cidx == 1) - (cidx == 2), cy_ = (cidx == 3) - (cidx == 4);
+            const int j = (x - cx_ + d.nx) % d.nx + d.nx * ((y - cy_ + d.ny) % d.ny);
+            return sl * n + j;
+          };
           double pt = 0.0;
-          for (int base = 0; base < 5 * L; base += NN_GROUPS) {
-            const int q = base + g;
-            const bool on = q < 5 * L;
-            int row = 0;
-            if (on) {
-              const int cidx = q % 5, sl = q / 5;
-              const int cx_ = (cidx == 1) - (cidx == 2), cy_ = (cidx == 3) - (cidx == 4);
-              const int j = (x - cx_ + d.nx) % d.nx + d.nx * ((y - cy_ + d.ny) % d.ny);
-              row = sl * n + j;
-            }
-            fill_patch(d, X, row / n, row % n, nn.x0, z, sub, i, -1, 0.0, dx);
-            const float f = nn_patch_eval(s.w, z, h1, sub);
-            if (on && sub == 0) {
-              fnew[q] = f;
-              pt += (double)f - (double)fc[row];
+          for (int base = warp * 16; base < 5 * L; base += HQ_WARPS * 16) {
+            float f0, f1;
+            nn_tile_f(w, [&](int row, int k) {
+              const int q = base + row < 5 * L ? base + row : 5 * L - 1;
+              const int r = centre(q);
+              return patch_input(d, X, r / n, r % n, k, nn.x0, i, -1, 0.0, dx);
+            }, f0, f1);
+            if (t == 0) {
+              const int q0 = base + g, q1 = q0 + 8;
+              if (q0 < 5 * L) {
+                fnew[q0] = f0;
+                pt += (double)f0 - (double)fc[centre(q0)];
+              }
+              if (q1 < 5 * L) {
+                fnew[q1] = f1;
+                pt += (double)f1 - (double)fc[centre(q1)];
+              }
             }
           }
-          if (sub == 0) s.gacc[g] = pt;
+          pt = warp_sum_fixed(pt);
+          if (lane == 0) s.gacc[warp] = pt;
           __syncthreads();
           dF = 0.0;
-          for (int k = 0; k < NN_GROUPS; ++k) dF += s.gacc[k];
+          for (int k = 0; k < HQ_WARPS; ++k) dF += s.gacc[k];
         }
         if (threadIdx.x == 0) {
           const double prob = exp(fmin(2.0 * dF - dS, 709.0));
@@ -434,165 +426,270 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_decide_kernel(Dev d, NNState nn
 }
 
 // ------------------------------------------------------------------------ training
-// Mean squared error (1/B) sum_a (F(X_a) - y_a)^2 over a minibatch.  Forward: F_a per sample.
-// Backward: each CTA takes a fixed share of (sample, 32-patch tile) pairs; per tile the groups
-// store inputs, hidden activations and output gradients in shared memory, then every thread
-// accumulates the gradient entries it owns over the tile (fixed order: deterministic).  The
-// per-CTA partial gradients are summed in a fixed order by the Adam kernel.
-struct TrainSmem {
-  float* w;
-  float* z;    // [32][28]
-  float* h1;   // [32][64]
-  float* d1;   // [32][64] dL/da1
-  float* d2;   // [32][64] dL/da2
-  float* h2;   // [32][64]
-  float* dout; // [32]
-};
-
-__host__ __device__ inline size_t train_smem_bytes() {
-  return sizeof(float) * (NN_WPAD + NN_GROUPS * (NN_IN + 3) + 4 * NN_GROUPS * NN_H + NN_GROUPS);
-}
+// Mean squared error (1/B) sum_a (F(X_a) - y_a)^2 over a minibatch.  Forward: F_a per sample
+// (nn_batch_forward_kernel, the same tensor-core tiles as every other evaluation).  Backward:
+// nn_batch_backward_tc_kernel, per-CTA partial gradients summed in a fixed order by the Adam
+// kernel.
 
 __global__ void __launch_bounds__(HQ_THREADS) nn_batch_forward_kernel(Dev d, NNState nn, const double* Xs,
                                                                       const int* idx, double* Fb) {
   extern __shared__ __align__(16) char nraw[];
   const int a = blockIdx.x, n = d.n, NL = d.n * d.L;
   const NNSmem s = nn_carve(n, nraw);
-  load_weights(nn.wbf, s.w);
-  const double* X = Xs + (size_t)idx[a] * NL;
-  const int g = threadIdx.x / 8, sub = threadIdx.x % 8;
-  float* z = s.z + g * (NN_IN + 3);
-  float* h1 = s.h1 + g * NN_HP;
-  double part = 0.0;
-  for (int base = 0; base < NL; base += NN_GROUPS) {
-    const int row = base + g;
-    const bool on = row < NL;
-    fill_patch(d, X, on ? row / n : 0, on ? row % n : 0, nn.x0, z, sub, -1, -1, 0.0, 0.0);
-    const float f = nn_patch_eval(s.w, z, h1, sub);
-    if (on && sub == 0) part += (double)f;
-  }
-  if (sub == 0) s.gacc[g] = part;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double F = 0.0;
-    for (int k = 0; k < NN_GROUPS; ++k) F += s.gacc[k];
-    Fb[a] = F;
-  }
+  const NNFrags w = nn_build_frags(nn.wbf, s.frag, s.tcf);
+  const double F = fc_eval_all(d, s, w, Xs + (size_t)idx[a] * NL, nn.x0, nullptr);
+  if (threadIdx.x == 0) Fb[a] = F;
 }
 
-__global__ void __launch_bounds__(HQ_THREADS) nn_batch_backward_kernel(Dev d, NNState nn, const double* Xs,
-                                                                       const double* ys, const int* idx, int B,
-                                                                       const double* Fb, float* partials) {
+// Backward pass on the tensor cores (see hq_nn_tc.cuh): CTA k takes the 128-row chunks k, k +
+// grid, ... of the minibatch's rows (row R = sample a * L N + patch), warp w rows 16 w .. 16 w + 15
+// of a chunk.  partials[k] receives the CTA's gradient (every entry written once).
+__global__ void __launch_bounds__(HQ_THREADS) nn_batch_backward_tc_kernel(Dev d, NNState nn, const double* Xs,
+                                                                          const double* ys, const int* idx, int B,
+                                                                          const double* Fb, float* partials) {
   extern __shared__ __align__(16) char nraw[];
-  const int n = d.n, NL = d.n * d.L;
-  float* f0 = (float*)nraw;
-  TrainSmem s;
-  s.w = f0; f0 += NN_WPAD;
-  s.z = f0; f0 += NN_GROUPS * (NN_IN + 3);
-  s.h1 = f0; f0 += NN_GROUPS * NN_H;
-  s.d1 = f0; f0 += NN_GROUPS * NN_H;
-  s.d2 = f0; f0 += NN_GROUPS * NN_H;
-  s.h2 = f0; f0 += NN_GROUPS * NN_H;
-  s.dout = f0;
-  load_weights(nn.wbf, s.w);
-  const float* W1 = s.w + NN_W1;
-  const float* b1 = s.w + NN_B1;
-  const float* W2 = s.w + NN_W2;
-  const float* b2 = s.w + NN_B2;
-  const float* W3 = s.w + NN_W3;
-  const int g = threadIdx.x / 8, sub = threadIdx.x % 8, u0 = sub * 8;
-  float* z = s.z + g * (NN_IN + 3);
-  float* h1 = s.h1 + g * NN_H;
-  // gradient entries owned by this thread: W2 (16), W1 (<= 7), one of b1/b2/W3/b3
-  float gW2[16], gW1[7], gX = 0.f;
+  const int n = d.n, NL = d.n * d.L, rows = B * NL;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, g = lane >> 2, t = lane & 3;
+  uint2* frag = (uint2*)nraw;
+  float* tcf = (float*)(frag + TR_FRAGS);
+  float* colp = tcf + TC_FLOATS;              // [3][8 warps][64] column partials, then gb3 [8]
+  uint16_t* h1h = (uint16_t*)(colp + 3 * 8 * TC_H + 8);
+  uint16_t* h1l = h1h + TC_H * TR_LD;
+  uint16_t* d2h = h1l + TC_H * TR_LD;
+  uint16_t* d2l = d2h + TC_H * TR_LD;
+  uint16_t* zh = d2l + TC_H * TR_LD;
+  uint16_t* zl = zh + TC_K1 * TR_LD;
+  uint16_t* d1h = zl + TC_K1 * TR_LD;
+  uint16_t* d1l = d1h + TC_H * TR_LD;
+  const NNFrags w = nn_build_frags(nn.wbf, frag, tcf);
+  // W2^T fragments for d1 = d2 W2^T: B[k = u][n = v] = W2[v][u]
+  uint2* w2t = frag + TC_FRAGS;
+  for (int e = threadIdx.x; e < 4 * 8 * 32; e += HQ_THREADS) {
+    const int ln = e % 32, j = (e / 32) % 8, st = e / 256;
+    const int gg = ln >> 2, tt = ln & 3, v = 8 * j + gg, u = 16 * st + 2 * tt;
+    const uint16_t* row = nn.wbf + NN_W2 + v * NN_H;
+    w2t[e] = make_uint2(pack_bf16(row[u], row[u + 1]), pack_bf16(row[u + 8], row[u + 9]));
+  }
+  __syncthreads();
+  // owned accumulators: gW2 block (m-tile warp/2, n-tiles 4 (warp%2) ..), gW1 block (m-tile
+  // warp/4, n-tiles 2 (warp%4) ..), column partials of this lane's 16 columns
+  float gw2[4][4], gw1[2][4], cw3[16], cb2[16], cb1[16], cb3 = 0.f;
 #pragma unroll
-  for (int k = 0; k < 16; ++k) gW2[k] = 0.f;
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-  for (int k = 0; k < 7; ++k) gW1[k] = 0.f;
-  const int tiles_per_sample = (NL + NN_GROUPS - 1) / NN_GROUPS;
-  const int ntile = B * tiles_per_sample;
-  for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-    const int a = tile / tiles_per_sample, row = (tile % tiles_per_sample) * NN_GROUPS + g;
-    const bool on = row < NL;
-    const double* X = Xs + (size_t)idx[a] * NL;
-    const float dF = (float)(2.0 * (Fb[a] - ys[idx[a]]) / B);
-    fill_patch(d, X, on ? row / n : 0, on ? row % n : 0, nn.x0, z, sub, -1, -1, 0.0, 0.0);
-    // forward, keeping a1 / a2 signs, h1, h2
-    float a1[8], c2[8];
+    for (int e = 0; e < 4; ++e) gw2[a][e] = 0.f;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) a1[j] = b1[u0 + j];
-    for (int k = 0; k < NN_IN; ++k) {
-      const float zk = z[k];
+  for (int a = 0; a < 2; ++a)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) a1[j] = fmaf(zk, W1[k * NN_H + u0 + j], a1[j]);
+    for (int e = 0; e < 4; ++e) gw1[a][e] = 0.f;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) cw3[c] = cb2[c] = cb1[c] = 0.f;
+  const int nchunk = (rows + TR_ROWS - 1) / TR_ROWS;
+  for (int chunk = blockIdx.x; chunk < nchunk; chunk += gridDim.x) {
+    const int r0 = chunk * TR_ROWS + 16 * warp;
+    auto rowpos = [&](int row, int& a, int& pr) {
+      const int R = r0 + row < rows ? r0 + row : rows - 1;
+      a = R / NL;
+      pr = R % NL;
+    };
+    // forward of the warp's 16 rows, keeping what the backward pass needs
+    float acc1[8][4], acc2[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc1[j][e] = acc2[j][e] = 0.f;
+#pragma unroll
+    for (int st = 0; st < 2; ++st) {
+      uint32_t ahi[4], alo[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int row = g + 8 * (q & 1);
+        const int k = 16 * st + 2 * t + 8 * (q >> 1);
+        int a, pr;
+        rowpos(row, a, pr);
+        const double* X = Xs + (size_t)idx[a] * NL;
+        const float v0 = k < TC_IN ? patch_input(d, X, pr / n, pr % n, k, nn.x0, -1, -1, 0.0, 0.0) : 0.f;
+        const float v1 = k + 1 < TC_IN ? patch_input(d, X, pr / n, pr % n, k + 1, nn.x0, -1, -1, 0.0, 0.0) : 0.f;
+        split2(v0, v1, ahi[q], alo[q]);
+        // z^T staging (rows k >= 25 are zero)
+        zh[k * TR_LD + 16 * warp + row] = (uint16_t)(ahi[q] & 0xffffu);
+        zl[k * TR_LD + 16 * warp + row] = (uint16_t)(alo[q] & 0xffffu);
+        zh[(k + 1) * TR_LD + 16 * warp + row] = (uint16_t)(ahi[q] >> 16);
+        zl[(k + 1) * TR_LD + 16 * warp + row] = (uint16_t)(alo[q] >> 16);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint2 b = w.w1[(st * 8 + j) * 32 + lane];
+        mma_bf16(acc1[j], ahi, b);
+        mma_bf16(acc1[j], alo, b);
+      }
     }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) h1[u0 + j] = fmaxf(a1[j], 0.f);
-    __syncwarp();
-#pragma unroll
-    for (int j = 0; j < 8; ++j) c2[j] = b2[u0 + j];
-    for (int v = 0; v < NN_H; ++v) {
-      const float hv = h1[v];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) c2[j] = fmaf(hv, W2[v * NN_H + u0 + j], c2[j]);
-    }
-    const float dout = on ? dF : 0.f;
-    float* d2 = s.d2 + g * NN_H;
-    float* h2 = s.h2 + g * NN_H;
+    // a1 -> h1 (kept as hi/lo A fragments and staged transposed), masks in acc1's sign
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      h2[u0 + j] = fmaxf(c2[j], 0.f);
-      d2[u0 + j] = (c2[j] > 0.f) ? dout * W3[u0 + j] : 0.f;
+      const int v = 8 * j + 2 * t;
+      acc1[j][0] += w.b1[v];
+      acc1[j][1] += w.b1[v + 1];
+      acc1[j][2] += w.b1[v];
+      acc1[j][3] += w.b1[v + 1];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        uint16_t hh, hl;
+        split1(fmaxf(acc1[j][e], 0.f), hh, hl);
+        const int col = v + (e & 1), row = g + 8 * (e >> 1);
+        h1h[col * TR_LD + 16 * warp + row] = hh;
+        h1l[col * TR_LD + 16 * warp + row] = hl;
+      }
     }
-    if (sub == 0) s.dout[g] = dout;
-    __syncwarp();
-    // dL/da1 for this lane's 8 units: relu'(a1) sum_u W2[v][u] d2[u]
-    float* d1 = s.d1 + g * NN_H;
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+      uint32_t ahi[4], alo[4];
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int j = 2 * st + half;
+        split2(fmaxf(acc1[j][0], 0.f), fmaxf(acc1[j][1], 0.f), ahi[2 * half], alo[2 * half]);
+        split2(fmaxf(acc1[j][2], 0.f), fmaxf(acc1[j][3], 0.f), ahi[2 * half + 1], alo[2 * half + 1]);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint2 b = w.w2[(st * 8 + j) * 32 + lane];
+        mma_bf16(acc2[j], ahi, b);
+        mma_bf16(acc2[j], alo, b);
+      }
+    }
+    // output gradients of the two rows of this lane
+    float dout[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      int a, pr;
+      rowpos(g + 8 * h, a, pr);
+      dout[h] = (r0 + g + 8 * h < rows) ? (float)(2.0 * (Fb[a] - ys[idx[a]]) / B) : 0.f;
+    }
+    if (t == 0) cb3 += dout[0] + dout[1];
+    // d2 = relu'(a2) dout W3 (in acc2), gW3 and gb2 column sums, d2 staged transposed
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const int v = u0 + j;
-      float acc = 0.f;
-      for (int uu = 0; uu < NN_H; ++uu) acc = fmaf(W2[v * NN_H + uu], d2[uu], acc);
-      d1[v] = (a1[j] > 0.f) ? acc : 0.f;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int u = 8 * j + 2 * t + (e & 1), row = g + 8 * (e >> 1);
+        const float a2 = acc2[j][e] + w.b2[u];
+        const float dv = a2 > 0.f ? dout[e >> 1] * w.w3[u] : 0.f;
+        cw3[2 * j + (e & 1)] = fmaf(fmaxf(a2, 0.f), dout[e >> 1], cw3[2 * j + (e & 1)]);
+        cb2[2 * j + (e & 1)] += dv;
+        acc2[j][e] = dv;
+        uint16_t hh, hl;
+        split1(dv, hh, hl);
+        d2h[u * TR_LD + 16 * warp + row] = hh;
+        d2l[u * TR_LD + 16 * warp + row] = hl;
+      }
+    }
+    // d1 = relu'(a1) (d2 W2^T)
+    float acc3[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc3[j][e] = 0.f;
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+      uint32_t ahi[4], alo[4];
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int j = 2 * st + half;
+        split2(acc2[j][0], acc2[j][1], ahi[2 * half], alo[2 * half]);
+        split2(acc2[j][2], acc2[j][3], ahi[2 * half + 1], alo[2 * half + 1]);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint2 b = w2t[(st * 8 + j) * 32 + lane];
+        mma_bf16(acc3[j], ahi, b);
+        mma_bf16(acc3[j], alo, b);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int v = 8 * j + 2 * t + (e & 1), row = g + 8 * (e >> 1);
+        const float dv = acc1[j][e] > 0.f ? acc3[j][e] : 0.f;
+        cb1[2 * j + (e & 1)] += dv;
+        uint16_t hh, hl;
+        split1(dv, hh, hl);
+        d1h[v * TR_LD + 16 * warp + row] = hh;
+        d1l[v * TR_LD + 16 * warp + row] = hl;
+      }
     }
     __syncthreads();
-    // accumulate owned gradient entries over the tile's 32 patches
-    for (int p = 0; p < NN_GROUPS; ++p) {
-      const float* h1p = s.h1 + p * NN_H;
-      const float* d2p = s.d2 + p * NN_H;
-      const float* d1p = s.d1 + p * NN_H;
-      const float* zp = s.z + p * (NN_IN + 3);
+    // gW2 = h1^T d2 and gW1 = z^T d1 over the chunk's 128 rows
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int e = threadIdx.x + k * HQ_THREADS;  // W2 entry e = v * 64 + u
-        gW2[k] = fmaf(h1p[e / NN_H], d2p[e % NN_H], gW2[k]);
-      }
+    for (int ks = 0; ks < TR_ROWS / 16; ++ks) {
 #pragma unroll
-      for (int k = 0; k < 7; ++k) {
-        const int e = threadIdx.x + k * HQ_THREADS;  // W1 entry e = k_in * 64 + v
-        if (e < NN_IN * NN_H) gW1[k] = fmaf(zp[e / NN_H], d1p[e % NN_H], gW1[k]);
-      }
-      const int t = threadIdx.x;
-      if (t < NN_H) gX += d1p[t];                       // b1
-      else if (t < 2 * NN_H) gX += d2p[t - NN_H];       // b2
-      else if (t < 3 * NN_H) gX += s.h2[p * NN_H + t - 2 * NN_H] * s.dout[p];  // W3
-      else if (t == 3 * NN_H) gX += s.dout[p];          // b3
+      for (int a = 0; a < 4; ++a)
+        mma_tiles3(gw2[a], h1h, h1l, d2h, d2l, 16 * (warp / 2), 8 * (4 * (warp % 2) + a), 16 * ks);
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+        mma_tiles3(gw1[a], zh, zl, d1h, d1l, 16 * (warp / 4), 8 * (2 * (warp % 4) + a), 16 * ks);
     }
     __syncthreads();
   }
+  // column sums: over the 8 row groups of the warp, then over the warps (fixed order)
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+      cw3[c] += __shfl_xor_sync(HQ_FULL, cw3[c], o);
+      cb2[c] += __shfl_xor_sync(HQ_FULL, cb2[c], o);
+      cb1[c] += __shfl_xor_sync(HQ_FULL, cb1[c], o);
+    }
+  }
+#pragma unroll
+  for (int o = 4; o < 32; o <<= 1) cb3 += __shfl_xor_sync(HQ_FULL, cb3, o);
+  if (g == 0) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int u = 8 * j + 2 * t + e;
+        colp[(0 * 8 + warp) * TC_H + u] = cw3[2 * j + e];
+        colp[(1 * 8 + warp) * TC_H + u] = cb2[2 * j + e];
+        colp[(2 * 8 + warp) * TC_H + u] = cb1[2 * j + e];
+      }
+    if (t == 0) colp[3 * 8 * TC_H + warp] = cb3;
+  }
+  __syncthreads();
   float* out = partials + (size_t)blockIdx.x * NN_WPAD;
+  // gW2 [v][u] at NN_W2 + v * 64 + u: C rows = v (m-tile warp / 2), cols = u
 #pragma unroll
-  for (int k = 0; k < 16; ++k) out[NN_W2 + threadIdx.x + k * HQ_THREADS] = gW2[k];
-#pragma unroll
-  for (int k = 0; k < 7; ++k) {
-    const int e = threadIdx.x + k * HQ_THREADS;
-    if (e < NN_IN * NN_H) out[NN_W1 + e] = gW1[k];
+  for (int a = 0; a < 4; ++a) {
+    const int v0 = 16 * (warp / 2) + g, u0 = 8 * (4 * (warp % 2) + a) + 2 * t;
+    out[NN_W2 + v0 * NN_H + u0] = gw2[a][0];
+    out[NN_W2 + v0 * NN_H + u0 + 1] = gw2[a][1];
+    out[NN_W2 + (v0 + 8) * NN_H + u0] = gw2[a][2];
+    out[NN_W2 + (v0 + 8) * NN_H + u0 + 1] = gw2[a][3];
   }
-  const int t = threadIdx.x;
-  if (t < NN_H) out[NN_B1 + t] = gX;
-  else if (t < 2 * NN_H) out[NN_B2 + t - NN_H] = gX;
-  else if (t < 3 * NN_H) out[NN_W3 + t - 2 * NN_H] = gX;
-  else if (t == 3 * NN_H) out[NN_B3] = gX;
+  // gW1 [k][v] at NN_W1 + k * 64 + v for k < 25
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const int k0 = 16 * (warp / 4) + g, v0 = 8 * (2 * (warp % 4) + a) + 2 * t;
+    if (k0 < NN_IN) {
+      out[NN_W1 + k0 * NN_H + v0] = gw1[a][0];
+      out[NN_W1 + k0 * NN_H + v0 + 1] = gw1[a][1];
+    }
+    if (k0 + 8 < NN_IN) {
+      out[NN_W1 + (k0 + 8) * NN_H + v0] = gw1[a][2];
+      out[NN_W1 + (k0 + 8) * NN_H + v0 + 1] = gw1[a][3];
+    }
+  }
+  for (int e = threadIdx.x; e < 3 * TC_H + 1; e += HQ_THREADS) {
+    float acc = 0.f;
+    if (e < 3 * TC_H) {
+      const int which = e / TC_H, u = e % TC_H;
+      for (int ww = 0; ww < 8; ++ww) acc += colp[(which * 8 + ww) * TC_H + u];
+      out[(which == 0 ? NN_W3 : which == 1 ? NN_B2 : NN_B1) + u] = acc;
+    } else {
+      for (int ww = 0; ww < 8; ++ww) acc += colp[3 * 8 * TC_H + ww];
+      out[NN_B3] = acc;
+    }
+  }
 }
 
 // Sum of the per-CTA partials (fixed order) into grad; with lr > 0 an Adam step on the FP32
@@ -678,10 +775,18 @@ cudaError_t nn_launch_batch(const Dev& d, const NNState& nn, const double* Xs, c
   const size_t sf = nn_smem_bytes(d.n);
   smem_opt_in((const void*)nn_batch_forward_kernel, sf);
   nn_batch_forward_kernel<<<B, HQ_THREADS, sf, s>>>(d, nn, Xs, idx, nn.Fb);
-  const size_t sbk = train_smem_bytes();
-  smem_opt_in((const void*)nn_batch_backward_kernel, sbk);
-  nn_batch_backward_kernel<<<kNNTrainCtas, HQ_THREADS, sbk, s>>>(d, nn, Xs, ys, idx, B, nn.Fb, nn.partials);
-  nn_adam_kernel<<<(NN_NP + 255) / 256, 256, 0, s>>>(nn, nn.partials, kNNTrainCtas, lr, t_step);
+  const size_t sbk = nn_train_tc_smem_bytes();
+  smem_opt_in((const void*)nn_batch_backward_tc_kernel, sbk);
+  // one wave: one CTA per SM (the kernel takes a whole SM's registers), at most kNNTrainCtas
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = kNNTrainCtas;
+  }
+  const int grid = sms < kNNTrainCtas ? sms : kNNTrainCtas;
+  nn_batch_backward_tc_kernel<<<grid, HQ_THREADS, sbk, s>>>(d, nn, Xs, ys, idx, B, nn.Fb, nn.partials);
+  nn_adam_kernel<<<(NN_NP + 255) / 256, 256, 0, s>>>(nn, nn.partials, grid, lr, t_step);
   return cudaGetLastError();
 }
 

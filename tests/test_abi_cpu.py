@@ -115,3 +115,38 @@ def test_group_arena_rejects_empty_sets():
     assert lib.hq_group_arena_bytes(None, 3) == 0
     arr = (ctypes.c_void_p * 1)(None)
     assert lib.hq_group_arena_bytes(arr, 1) == 0          # null engine
+
+
+def test_noalloc_binding_rejects_bad_tensors_before_the_library():
+    """The no-allocation entry point trusts the sizes it is given, so the binding checks dtype,
+    shape, length and device on the host; none of these calls reaches the library."""
+    import torch
+    import paper_1905_07440_gb300 as hq
+    p = HolsteinParams(nx=4, ny=4, beta=1.0)
+    good = torch.zeros((3, p.n_slices, p.n_sites), dtype=torch.float64)
+    out = torch.zeros(3, dtype=torch.float64)
+    with pytest.raises(TypeError):
+        hq.logdet_noalloc(p, good.float(), out)
+    with pytest.raises(TypeError):
+        hq.logdet_noalloc(p, good, out.float())
+    with pytest.raises(ValueError, match="shape"):
+        hq.logdet_noalloc(p, torch.zeros((3, p.n_slices + 1, p.n_sites), dtype=torch.float64), out)
+    with pytest.raises(ValueError, match="shape"):
+        hq.logdet_noalloc(p, torch.zeros((p.n_slices, p.n_sites), dtype=torch.float64), out)
+    with pytest.raises(ValueError, match="chains"):
+        hq.logdet_noalloc(p, good, torch.zeros(2, dtype=torch.float64))
+    with pytest.raises(ValueError, match="CUDA"):
+        hq.logdet_noalloc(p, good, out)
+
+
+def test_backoff_parameters_are_validated_and_size_the_arena():
+    hq, _ = _lib()
+    p = HolsteinParams(nx=6, ny=6, beta=2.0, n_wrap=10)
+    assert hq.arena_bytes(p.with_(wrap_tol=-1.0), 1) == 0
+    assert hq.arena_bytes(p.with_(wrap_tol=float("inf")), 1) == 0
+    assert hq.arena_bytes(p.with_(n_wrap_min=11, wrap_tol=1e-8), 1) == 0
+    base = hq.arena_bytes(p, 4)
+    # the stack is sized for the smallest n_wrap the back-off can reach
+    assert hq.arena_bytes(p.with_(wrap_tol=1e-8, n_wrap_min=10), 4) == base
+    assert hq.arena_bytes(p.with_(wrap_tol=1e-8, n_wrap_min=2), 4) > base
+    assert hq.arena_bytes(p.with_(wrap_tol=1e-8), 4) >= hq.arena_bytes(p.with_(wrap_tol=1e-8, n_wrap_min=2), 4)

@@ -63,6 +63,32 @@ def test_group_equals_each_engine_alone(hq, idle):
     grp.close()
 
 
+def test_group_chains_match_the_oracle(hq):
+    """One chain of every engine of a group against the CPU oracle chain with that chain's
+    identity (Philox key = the engine's seed, chain word = its index, sweep counter from 0):
+    fields bit for bit, log|det M| and G to 1e-10, acceptance counts exact."""
+    from oracle import dqmc
+    engines = [make(hq, p, C) for p, C in SHAPES]
+    grp = hq.Group(engines)
+    grp.sweep(2)
+    for k, (p, C) in enumerate(SHAPES):
+        c = C - 1
+        X0 = initial_fields(p, C, seed=p.seed)[c]
+        ch = dqmc.OracleChain(p, X0, chain=c)
+        recs = [ch.sweep() for _ in range(2)]
+        eng = engines[k]
+        assert np.array_equal(eng.get_fields()[c], ch.X), k
+        _, ld = eng.log_weight()
+        assert abs(ld[c] - ch.logdet) <= 1e-10 * abs(ch.logdet), k
+        assert np.max(np.abs(eng.green(c) - ch.G)) < 1e-10, k
+        o = eng.observables()[c]
+        assert o["local_accepted"] == sum(r["local_accepted"] for r in recs), k
+        assert o["global_accepted"] == sum(r["global_accepted"] for r in recs), k
+        s = eng.series(hq.HQ_OBS_SCDW)[c]
+        assert np.max(np.abs(s - np.array([r["s_cdw"] for r in recs]))) < 1e-9, k
+    grp.close()
+
+
 def test_group_then_engine_calls_are_ordered(hq):
     """After a group sweep an engine's own sweep continues from the group's result."""
     engines = [make(hq, p, C) for p, C in SHAPES[:2]]

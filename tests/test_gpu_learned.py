@@ -85,13 +85,18 @@ def test_training_lowers_the_loss(hq):
     assert losses[-1] < 0.2 * losses[0], losses
 
 
-def test_cumulative_step_matches_oracle(hq):
+@pytest.mark.parametrize("split", [1, 2])
+def test_cumulative_step_matches_oracle(hq, split):
+    """Cumulative steps with the exact log|det M(X')| from one CTA per chain (split 1) or from
+    two halves joined by the two-sided formula (split 2) follow the oracle chain."""
     from oracle import nn
-    p = HolsteinParams(nx=4, ny=4, beta=1.0, seed=31)
+    p = HolsteinParams(nx=4, ny=4, beta=1.0, n_wrap=3, seed=31)
     C = 3
     X0 = initial_fields(p, C, seed=3)
     th = scaled_params(4, 2.0)
     eng = hq.Engine(p, C)
+    m = eng.set_logdet_split(split)
+    assert (m > 0) == (split == 2) and m % p.n_wrap == 0 and m < p.n_slices
     eng.attach_network(4, 8)
     eng.set_params(th)
     eng.set_fields(X0)
@@ -179,8 +184,10 @@ def test_trained_network_sampler_agrees_with_plain_and_accepts(hq):
     X0 = eng.get_fields()
     steps, burn = 60, 5
     res, rates = {}, {}
-    for kind, th in (("plain", None), ("trained", theta), ("untrained", scaled_params(6, 1.0))):
-        e = hq.Engine(p, C, max_series=steps)
+    for k, (kind, th) in enumerate((("plain", None), ("trained", theta), ("untrained", scaled_params(6, 1.0)))):
+        # a fresh Philox key per run: the training engine's key with counters from 0 again
+        # would replay the noise that produced X0 and couple the run to that trajectory
+        e = hq.Engine(p.with_(seed=p.seed + 101 * (k + 1)), C, max_series=steps)
         e.set_fields(X0)
         if th is None:
             e.sweep(steps)
@@ -233,16 +240,19 @@ def test_cumulative_window_matches_oracle(hq, window, sites):
         assert np.all(np.isfinite(d))
 
 
-def test_measured_cumulative_steps_match_oracle_measurements(hq):
+@pytest.mark.parametrize("split", [1, 2])
+def test_measured_cumulative_steps_match_oracle_measurements(hq, split):
     """Measured cumulative steps: the recorded density, double occupancy and S_CDW(pi,pi) of
-    each step are those of G_0 of the chain's fields after the step (the oracle's fresh G_0),
-    for accepted and rejected steps alike (a rejected step restores the saved G_0)."""
+    each step are those of G_m of the chain's fields after the step (the oracle's fresh G_m;
+    m = 0 with one CTA per chain, the split boundary with two halves), for accepted and
+    rejected steps alike (a rejected step restores the saved G_m)."""
     from oracle import dqmc, nn
-    p = HolsteinParams(nx=4, ny=4, beta=1.0, seed=43)
+    p = HolsteinParams(nx=4, ny=4, beta=1.0, n_wrap=4, seed=43)
     C, steps = 3, 4
     X0 = initial_fields(p, C, seed=8)
     th = scaled_params(7, 2.0)
     eng = hq.Engine(p, C, max_series=steps)
+    m = eng.set_logdet_split(split)
     eng.attach_network(4, 8)
     eng.set_params(th)
     eng.set_fields(X0)
@@ -257,7 +267,7 @@ def test_measured_cumulative_steps_match_oracle_measurements(hq):
         recs = []
         for k in range(steps):
             ch.step(k, 1)
-            recs.append(dqmc.measure_green(p, dqmc.green_at(p, expK, ch.X, 0)[0]))
+            recs.append(dqmc.measure_green(p, dqmc.green_at(p, expK, ch.X, m)[0]))
         if not np.array_equal(Xg[c], ch.X):
             assert ch.min_margin < 1e-4, ch.min_margin
             continue

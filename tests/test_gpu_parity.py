@@ -29,25 +29,26 @@ def hq():
     return mod
 
 
-def oracle_chains(p, X0, n_sweeps, flags=(True, True)):
+def oracle_chains(p, X0, n_sweeps, flags=(True, True), block_sites=0):
     from oracle import dqmc
     out = []
     for c in range(X0.shape[0]):
         ch = dqmc.OracleChain(p, X0[c], chain=c)
-        recs = [ch.sweep(do_local=flags[0], do_global=flags[1]) for _ in range(n_sweeps)]
+        recs = [ch.sweep(do_local=flags[0], do_global=flags[1], block_sites=block_sites) for _ in range(n_sweeps)]
         out.append((ch, recs))
     return out
 
 
-def check_against_oracle(hq, p, X0, n_sweeps, local=True, global_=True, max_series=8):
+def check_against_oracle(hq, p, X0, n_sweeps, local=True, global_=True, max_series=8, block_sites=0):
     eng = hq.Engine(p, X0.shape[0], max_series=max_series)
+    eng.set_block_sites(block_sites)
     eng.set_fields(X0)
     eng.sweep(n_sweeps, local=local, global_=global_, measure=True)
     Xg = eng.get_fields()
     lw, ld = eng.log_weight()
     obs = eng.observables()
     series = {k: eng.series(k) for k in range(hq.HQ_N_OBS)}
-    ref = oracle_chains(p, X0, n_sweeps, (local, global_))
+    ref = oracle_chains(p, X0, n_sweeps, (local, global_), block_sites)
     for c, (ch, recs) in enumerate(ref):
         assert np.array_equal(Xg[c], ch.X), f"chain {c}: fields differ"
         assert abs(ld[c] - ch.logdet) <= LD_RTOL * max(1.0, abs(ch.logdet))
@@ -58,6 +59,7 @@ def check_against_oracle(hq, p, X0, n_sweeps, local=True, global_=True, max_seri
             assert obs[c]["local_accepted"] == sum(r["local_accepted"] for r in recs)
         if global_:
             assert obs[c]["global_accepted"] == sum(r["global_accepted"] for r in recs)
+            assert obs[c]["global_proposed"] == n_sweeps * (block_sites or p.n_sites)
         for s, r in enumerate(recs):
             for k, name in ((hq.HQ_OBS_X_MEAN, "x_mean"), (hq.HQ_OBS_X2, "x2")):
                 assert abs(series[k][c, s] - r[name]) < OBS_ATOL

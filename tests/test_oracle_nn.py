@@ -109,3 +109,124 @@ def test_full_windows_equal_the_full_sweep():
     c.step(0, 1, local=True, block=False, window=2)
     moved = np.any(c.X != X0, axis=1)
     assert moved.sum() <= 2   # only the two slices of the window can change
+
+
+# ------------------------------------------------------------- cumulative accept pins
+
+def _path_log_ratio(ch, X_start, log_pi):
+    """Replays the recorded inner moves of the last step and returns (X', log of the reverse
+    path's probability over the forward path's).  Each move is a Metropolis move with a
+    symmetric proposal on its own weight pi_j (log_pi(kind, X)); a rejected move contributes
+    the same rejection factor to both paths, an accepted move a -> b contributes
+    min(1, pi(a)/pi(b)) / min(1, pi(b)/pi(a)).  Also checks every recorded decision against
+    u < min(1, pi(b)/pi(a)) computed from the full weights."""
+    X = X_start.copy()
+    lr = 0.0
+    for m in ch.moves:
+        assert np.array_equal(m["before"], X)
+        b = X.copy()
+        if m["kind"] == "local":
+            b[m["where"]] = m["value"]
+        else:
+            b[:, m["where"]] += m["value"]
+        d = log_pi(m["kind"], b) - log_pi(m["kind"], X)
+        fwd, rev = min(1.0, np.exp(d)), min(1.0, np.exp(-d))
+        if abs(m["u"] - fwd) > 1e-9 * max(fwd, 1e-300):
+            assert (m["u"] < fwd) == m["accepted"], (m["kind"], m["u"], fwd)
+        if m["accepted"]:
+            lr += np.log(rev) - np.log(fwd)
+            X = b
+    return X, lr
+
+
+@pytest.mark.parametrize("with_cnn", [False, True])
+def test_cumulative_accept_equals_the_explicit_path_probability_ratio(with_cnn):
+    """Paper, cumulative update: p_c = [W(X')/W(X)] [P(X' -> X) / P(X -> X')] for the
+    proposal made of network-driven moves.  On a 2x2, L = 4 lattice, for each recorded step
+    (forward and reverse visiting orders) the oracle's p_c must equal W(X')/W(X) from fresh
+    determinants and the phonon action, times the ratio of the reverse path's to the forward
+    path's acceptance probabilities, each computed from the full learned weights
+    exp(-dtau S_ph + 2 F) (not the incremental changes the sampler uses), to 1e-12 in log."""
+    import math
+    from oracle import cnn, dqmc
+    p = HolsteinParams(nx=2, ny=2, beta=0.4, seed=123)
+    th = nn.init_params(8)
+    th[-nn.N_H - 1:] *= 30.0
+    th = nn.to_bfloat16(th.astype(np.float32))
+    act = nn.EffectiveAction(p, th)
+    cth = cnn_act = None
+    if with_cnn:
+        cth = nn.to_bfloat16(cnn.init_params(3, out_scale=30.0).astype(np.float32))
+        cnn_act = cnn.CnnAction(p, cth)
+    expK, _ = dqmc.kinetic_propagators(p)
+
+    def log_pi(kind, X):
+        F = cnn_act.F(X) if (kind == "block" and cnn_act is not None) else act.F(X)
+        return -dqmc.phonon_action(p, X) + 2.0 * F
+
+    def log_w(X):
+        return 2.0 * dqmc.log_det_M(p, expK, X) - dqmc.phonon_action(p, X)
+
+    X0 = random_fields(p, 1, seed=4, offset=-1.4)[0]
+    ch = nn.CumulativeChain(p, X0, th, chain=3, cnn_theta=cth, record=True)
+    dirs = set()
+    n_acc_moves = 0
+    for k in range(8):
+        Xs = ch.X.copy()
+        pc, accepted = ch.step(k, 1)
+        dirs.add(ch.last_forward)
+        Xp, lr = _path_log_ratio(ch, Xs, log_pi)
+        n_acc_moves += sum(m["accepted"] for m in ch.moves)
+        expected = log_w(Xp) - log_w(Xs) + lr
+        assert abs(math.log(pc) - expected) < 1e-12 * max(1.0, abs(expected)), (k, math.log(pc), expected)
+        assert np.array_equal(ch.X, Xp if accepted else Xs)
+    assert dirs == {True, False}
+    assert n_acc_moves > 20
+
+
+def _free_phonon_sampler(p, L, N):
+    """Exact samples of X at g = 0: each site's time column is Gaussian with the circulant
+    precision of dtau S_ph."""
+    A = np.zeros((L, L))
+    for l in range(L):
+        A[l, l] = 2.0 * p.mass / p.dtau + p.dtau * p.mass * p.omega ** 2
+        A[l, (l + 1) % L] -= p.mass / p.dtau
+        A[l, (l - 1) % L] -= p.mass / p.dtau
+    chol = np.linalg.cholesky(np.linalg.inv(A))
+    return lambda rng, n: np.einsum("ab,nbi->nai", chol, rng.standard_normal((n, L, N)))
+
+
+def test_cumulative_sampler_reproduces_the_free_phonon_closed_form():
+    """g = 0: log|det M| does not depend on X, so the cumulative sampler with any network must
+    sample exp(-dtau S_ph), whose <X^2> is the closed form (1/L) sum_q 1/[(2M/dtau)(1 - cos
+    2 pi q/L) + dtau M Omega^2].  The network chosen here biases the inner moves strongly: the
+    inner chain alone would sample exp(-dtau S_ph + 2F), whose <X^2> (importance-reweighted
+    exact samples) lies many error bars away, so only a correct cumulative accept passes."""
+    import math
+    from oracle import autocorr
+    from tests import closed_forms as cf
+    p = HolsteinParams(nx=2, ny=2, beta=0.8, g=0.0, mu=0.0, seed=5)
+    L, N = p.n_slices, p.n_sites
+    ref = cf.free_phonon_x2(L, p.dtau, p.mass, p.omega)
+    th = nn.to_bfloat16(nn.init_params(2).astype(np.float32))
+    draw = _free_phonon_sampler(p, L, N)
+    series, acc, steps = [], 0, 450
+    for c in range(4):
+        ch = nn.CumulativeChain(p, draw(np.random.default_rng(100 + c), 1)[0], th, chain=c)
+        s = []
+        for k in range(steps):
+            acc += ch.step(k, 1)[1]
+            s.append(float(np.mean(ch.X ** 2)))
+        series.append(np.array(s))
+    tau = float(np.mean([autocorr.tau_int(x)[0] for x in series]))
+    allx = np.concatenate(series)
+    err = float(np.std(allx)) / math.sqrt(allx.size / (2.0 * tau))
+    assert 0.3 < acc / (4 * steps) < 0.9
+    assert abs(allx.mean() - ref) < 3.0 * err, (allx.mean(), ref, err, tau)
+    # the inner chain's own distribution is far from the closed form
+    act = nn.EffectiveAction(p, th)
+    S = draw(np.random.default_rng(0), 20000)
+    F = np.array([act.F(x) for x in S])
+    w = np.exp(2.0 * (F - F.max()))
+    biased = float(np.sum(w * np.mean(S ** 2, axis=(1, 2))) / np.sum(w))
+    assert abs(biased - ref) > 10.0 * err, (biased, ref, err)

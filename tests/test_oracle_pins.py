@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 from oracle import dqmc, philox, autocorr
-from workloads import HolsteinParams, random_fields, uniform_fields
+from workloads import HolsteinParams, initial_fields, random_fields, uniform_fields
 from tests import closed_forms as cf
 from tests import fock
 
@@ -273,3 +273,27 @@ def test_tau_int_white_noise_and_ar1():
             x[k] = rho * x[k - 1] + e[k]
         ref = 0.5 * (1 + rho) / (1 - rho)
         assert abs(autocorr.tau_int(x)[0] - ref) < 0.1 * ref
+
+
+def test_stabilisation_backoff_halves_n_wrap_down_to_the_floor():
+    """Back-off reading: a sweep whose largest wrap error exceeds wrap_tol halves n_wrap for the
+    next sweeps, down to n_wrap_min, where the chain is reported unstable; a tolerance above the
+    rounding-level wrap error changes nothing.  Every sweep stays consistent: G after the sweep
+    equals a fresh G at the current n_wrap."""
+    p = HolsteinParams(nx=4, ny=4, beta=1.6, n_wrap=8, n_wrap_min=2, wrap_tol=1e-300, seed=7)  # L = 16
+    X0 = initial_fields(p, 1, seed=3)[0]
+    ch = dqmc.OracleChain(p, X0)
+    seq = []
+    for _ in range(4):
+        r = ch.sweep()
+        assert r["max_wrap_error"] > 0.0
+        seq.append(ch.n_wrap)
+    assert seq == [4, 2, 2, 2]
+    assert ch.wrap_exceeded == 4 and ch.unstable
+    expK, _ = dqmc.kinetic_propagators(p)
+    G, ld = dqmc.green_at(p, expK, ch.X, 0, ch.n_wrap)
+    assert np.max(np.abs(G - ch.G)) < 1e-10 and abs(ld - ch.logdet) < 1e-10 * abs(ld)
+    loose = dqmc.OracleChain(p.with_(wrap_tol=1e-6), X0)
+    for _ in range(3):
+        loose.sweep()
+    assert loose.n_wrap == 8 and loose.wrap_exceeded == 0 and not loose.unstable

@@ -1,6 +1,6 @@
 """Serving scheduler: admission by HBM budget, continuous batching, release of empty pools
 (CPU, with a fake backend whose 'sweeps' are counters), and on the GPU the same results for
-a request alone and in a mix."""
+a request alone and in a mix, and a served request's chain against the CPU oracle."""
 import numpy as np
 import pytest
 
@@ -184,3 +184,48 @@ def test_learned_requests_alone_equal_in_the_mix():
         assert np.array_equal(alone[0].X, r.X), r.rid
         if r.sampler == "learned":
             assert alone[0].obs["cumulative_accepted"] == r.obs["cumulative_accepted"]
+
+
+@pytest.mark.gpu
+def test_served_requests_match_the_oracle():
+    """A plain and a learned request served in a mix with other requests end on the oracle
+    chain with the request's identity (key = its seed, chain word = chain_id, counter from 0):
+    plain fields bit for bit; learned fields bit for bit unless a decision was closer than the
+    FP32 network can resolve (|u - p|/p < 1e-4)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle import dqmc, nn
+    from paper_1905_07440_gb300.serving import GpuBackend
+    th = nn.init_params(4)
+    th[-nn.N_H - 1:] *= 2.0
+    shapes = [HolsteinParams(nx=4, ny=4, beta=1.0), HolsteinParams(nx=6, ny=4, beta=0.8, g=1.0, mu=-1.0)]
+    reqs = []
+    for k in range(8):
+        p = shapes[k % 2].with_(seed=700 + k)
+        kind = "learned" if (k % 4 == 0 and p.nx >= 4 and p.ny >= 4) else "plain"
+        reqs.append(Request(rid=k, params=p, X0=initial_fields(p, 1, seed=90 + k)[0], sweeps=2 + k % 2,
+                            sampler=kind, theta=th if kind == "learned" else None, chain_id=40 + k,
+                            arrival=0.001 * k))
+    done = {r.rid: r for r in Server(GpuBackend(), hbm_budget=8 << 30, slots_per_pool=3).run(reqs)}
+    assert len(done) == 8
+    thb = nn.to_bfloat16(th.astype(np.float32))
+    checked = {"plain": 0, "learned": 0}
+    for k in (0, 1, 3, 4):
+        r = done[k]
+        X0 = initial_fields(r.params, 1, seed=90 + k)[0]
+        if r.sampler == "plain":
+            ch = dqmc.OracleChain(r.params, X0, chain=r.chain_id)
+            recs = [ch.sweep() for _ in range(r.sweeps)]
+            assert np.array_equal(r.X, ch.X), k
+            assert r.obs["local_accepted"] == sum(x["local_accepted"] for x in recs)
+            checked["plain"] += 1
+        else:
+            ch = nn.CumulativeChain(r.params, X0, thb, chain=r.chain_id)
+            acc = sum(ch.step(j, 1)[1] for j in range(r.sweeps))
+            if np.array_equal(r.X, ch.X):
+                assert r.obs["cumulative_accepted"] == acc
+                checked["learned"] += 1
+            else:
+                assert ch.min_margin < 1e-4, ch.min_margin
+    assert checked["plain"] >= 2 and checked["learned"] >= 1, checked

@@ -5,7 +5,8 @@ framework whose memory pool owns the GPU, or they must not allocate once running
 serving loop).  This entry point takes only their input and output buffers and keeps its
 scratch in a static device array inside the library.  The test drives it through the C ABI
 on caller-owned tensors and compares it with the engine's log|det M| (hq_log_weight) on the
-same fields, on two calls in a row (the second reuses the scratch the first left behind).
+same fields, on two calls in a row (the second reuses the scratch the first left behind), and
+with the CPU oracle's log|det M| directly.
 The file sorts last so that a run stopping at the first failure has run every other test.
 """
 import numpy as np
@@ -51,6 +52,26 @@ def test_noalloc_logdet_matches_engine_on_two_calls(hq):
         ref = engine_logdet(hq, p, X)
         assert np.all(np.isfinite(got))
         assert np.max(np.abs(got - ref) / np.abs(ref)) < LD_RTOL
+
+
+def test_noalloc_logdet_matches_the_oracle(hq):
+    """Small lattices against the oracle's stabilised log|det M| (scipy pivoted QR), including
+    a ragged n_wrap and non-unit t, M, Omega; two calls in a row on the shared scratch."""
+    import torch
+    from oracle import dqmc
+    cases = [HolsteinParams(nx=4, ny=4, beta=1.0), HolsteinParams(nx=6, ny=4, beta=1.3, n_wrap=4, t=0.8,
+                                                                   mass=1.3, omega=0.5, g=1.0, mu=-3.0)]
+    for p in cases:
+        X = random_fields(p, 3, seed=41, offset=-1.0)
+        Xd = torch.from_numpy(X).cuda()
+        out = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
+        hq.logdet_noalloc(p, Xd, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        expK, _ = dqmc.kinetic_propagators(p)
+        for c in range(3):
+            ref = dqmc.log_det_M(p, expK, X[c])
+            assert abs(got[c] - ref) <= LD_RTOL * abs(ref), (p, c, got[c], ref)
 
 
 def test_noalloc_rejects_sizes_beyond_the_scratch(hq):

@@ -34,6 +34,8 @@ class HolsteinParams:
     dx_global: float = 1.0
     seed: int = DEFAULT_SEED
     block_method: int = 0  # engine's block-move algorithm (0 flop model, 1 per slice, 2 chunks)
+    n_wrap_min: int = 0    # stabilisation back-off floor (0: 1)
+    wrap_tol: float = 0.0  # stabilisation back-off threshold on |G_wrapped - G_fresh| (0: off)
 
     @property
     def n_sites(self) -> int:
