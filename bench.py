@@ -517,6 +517,15 @@ def series_stats(hq, eng, first, names):
     return out
 
 
+def start_fields(p, chains, amplitude, seed):
+    """Starting fields of the headline runs: the charge-ordered pattern (amplitude > 0; beta = 16
+    is deep in the ordered phase, where a disordered start coarsens domains for hundreds of
+    steps) or the mean field with the free-phonon spread (amplitude 0)."""
+    if amplitude > 0:
+        return workloads.ordered_fields(p, chains, amplitude, seed=seed)
+    return workloads.initial_fields(p, chains, seed=seed) - p.g / (p.mass * p.omega ** 2)
+
+
 def run_headline(args):
     """Learned vs plain at 16x16, beta = 16 (L = 160), 64 chains per GPU (see the module doc)."""
     rank, world, local_rank = dist_env()
@@ -559,22 +568,31 @@ def run_headline(args):
     with torch.cuda.stream(stream):
         peak = hq.fp64_peak_tflops(20, stream.cuda_stream, kind=hq.HQ_PROBE_DFMA)
         dgemm = measure_dgemm(dev)
-        # ---- 1. training data: plain sampler at 8x8 (same beta and couplings), fresh Philox key
+        # ---- 1. training data: plain local sweeps on the deployment lattice (one chain per SM), from
+        # the ordered start, fresh Philox key; the exact log|det M| comes with every local sweep
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
         t0 = time.perf_counter()
-        tr = hq.Engine(small.with_(seed=small.seed + 7), args.train_chains, first_chain=first, device=dev, stream=stream)
-        tr.set_fields(workloads.initial_fields(small, args.train_chains, seed=workloads.DEFAULT_SEED + 5000 + first) + x0)
-        tr.sweep(args.train_warmup)
+        tp = big.with_(seed=big.seed + 7)
+        tr = hq.Engine(tp, sms, first_chain=first, device=dev, stream=stream)
+        tr.set_fields(start_fields(big, sms, args.start_amplitude, workloads.DEFAULT_SEED + 5000 + first))
+        tr.sweep(args.train_warmup, global_=False)
         Xs, ys = [], []
         for _ in range(args.train_snapshots):
-            tr.sweep(1)
+            tr.sweep(1, global_=False)
             Xs.append(tr.get_fields())
             ys.append(tr.log_weight()[1])
         tr.close()
         t_data = time.perf_counter() - t0
-        Xtr, ytr = np.concatenate(Xs), np.concatenate(ys)
-        ytr = ytr - ytr.mean()
+        # chains split 75/25 into training and held-out test configurations
+        ntr = (3 * sms) // 4
+        Xall, yall = np.stack(Xs, axis=1), np.stack(ys, axis=1)
+        Xtr, ytr = Xall[:ntr].reshape((-1,) + Xall.shape[2:]), yall[:ntr].reshape(-1)
+        Xte, yte = Xall[ntr:].reshape((-1,) + Xall.shape[2:]), yall[ntr:].reshape(-1)
+        del Xall
+        ymu = ytr.mean()
+        ytr, yte = ytr - ymu, yte - ymu
         # ---- 2. network training on the tensor cores (lr halved every third of the epochs)
-        net = hq.Engine(small, 1, device=dev, stream=stream)
+        net = hq.Engine(big, 1, device=dev, stream=stream)
         net.attach_network(64, Xtr.shape[0])
         net.set_params(hq.init_network(args.nn_seed))
         Xd, yd = torch.from_numpy(Xtr).to(dev), torch.from_numpy(ytr).to(dev)
@@ -586,6 +604,13 @@ def run_headline(args):
             losses.extend(net.nn_train(Xd, yd, epochs=ep, batch=64, lr=args.lr * 0.5 ** k, seed=args.nn_seed + k))
         torch.cuda.synchronize(dev)
         t_train = time.perf_counter() - t1
+        test_mse, nt = 0.0, 0
+        for a0 in range(0, Xte.shape[0], 64):
+            nb = min(64, Xte.shape[0] - a0)
+            _, l = net.nn_gradient(torch.from_numpy(Xte[a0:a0 + nb]).to(dev), torch.from_numpy(yte[a0:a0 + nb]).to(dev))
+            test_mse += l * nb
+            nt += nb
+        test_rms = math.sqrt(test_mse / nt)
         theta = net.get_params()
         net.close()
         del Xd, yd
@@ -596,8 +621,11 @@ def run_headline(args):
         lrn.set_params(theta)
         lrn.set_inner_window(W)
         split_m = lrn.set_logdet_split(0)
-        lrn.set_fields(workloads.initial_fields(big, C, seed=workloads.DEFAULT_SEED + first) + x0)
-        lrn.cumulative(args.relax + Wm, 1, measure=True)
+        lrn.set_fields(start_fields(big, C, args.start_amplitude, workloads.DEFAULT_SEED + first))
+        blk = args.inner_block_sites > 0
+        if blk:
+            lrn.set_inner_sites(args.inner_block_sites)
+        lrn.cumulative(args.relax + Wm, 1, global_=blk, measure=True)
         flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
         torch.cuda.synchronize(dev)
         lrn.set_timing(True)
@@ -616,7 +644,7 @@ def run_headline(args):
             flush.fill_(1.0)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            lrn.cumulative(1, 1, measure=True)
+            lrn.cumulative(1, 1, global_=blk, measure=True)
             b.record(stream)
             evs.append((a, b))
         torch.cuda.synchronize(dev)
@@ -626,7 +654,7 @@ def run_headline(args):
         lrn.set_timing(False)
         t_dev = replicas.max_over_ranks(sum(a.elapsed_time(b) for a, b in evs) / 1e3, dev)
         step_rate = C * world * K / t_dev
-        lrn.cumulative(args.tau_steps, 1, measure=True)
+        lrn.cumulative(args.tau_steps, 1, global_=blk, measure=True)
         stats = series_stats(hq, lrn, args.relax + Wm, names)
         st = lrn.learned_stats()
         acc = sum(x["cumulative_accepted"] for x in st) / max(1, sum(x["cumulative_proposed"] for x in st))
@@ -638,7 +666,7 @@ def run_headline(args):
         te = time.perf_counter()
         for _ in range(args.e2e_steps):
             lrn.set_fields(Xh)
-            lrn.cumulative(1, 1, measure=True)
+            lrn.cumulative(1, 1, global_=blk, measure=True)
             lrn.get_fields(Xh)
             obs = lrn.observables()
         t_e2e = replicas.max_over_ranks(time.perf_counter() - te, dev)
@@ -701,9 +729,14 @@ def run_headline(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 (determinants); bf16 operands / fp32 accumulation "
                                                           "(network)", "data": "synthetic",
         "config": {"workload": f"16x16 beta=16 L=160 {C} chains: learned (patch network, window {W}) vs plain",
+                   "learned_moves": (f"local moves on a window of {W} slices" + (
+                       f" + block moves on {args.inner_block_sites} sites" if blk else ", no block moves")
+                                     + " per cumulative step"),
                    "lattice": "16x16", "beta": big.beta, "dtau": big.dtau, "L": big.n_slices, "chains_per_rank": C,
                    "n_wrap": big.n_wrap, "delay_k": big.delay_k, "parallelism": f"replicas x{world}",
                    "logdet_split_boundary": split_m,
+                   "start": (f"charge-ordered: -g/(M Omega^2) + {args.start_amplitude} (-1)^(x+y) + N(0, 1/(2 M Omega))"
+                             if args.start_amplitude > 0 else "mean field + N(0, 1/(M Omega^2))"),
                    "l2": "flushed (512 MB write) before every timed step; flush outside the events"},
         "learned": {"chain_steps_per_s": step_rate, "tau_int_steps": tau, "indep_samples_per_s": indep,
                     "cumulative_acceptance": acc, "observables": stats, "relax_steps": args.relax + Wm,
@@ -716,7 +749,10 @@ def run_headline(args):
                   "phases_ms": {k: v[0] for k, v in ph.items() if v[1]},
                   "block_acceptance": sum(o["global_accepted"] for o in pobs) / max(1, sum(o["global_proposed"] for o in pobs))},
         "gain_lower_bound": {k: indep[k] / plain_bound for k in indep},
-        "training": {"lattice": "8x8", "samples": int(Xtr.shape[0]), "data_s": t_data, "train_s": t_train,
+        "training": {"lattice": "16x16", "source": f"plain local sweeps, {sms} chains from the start state, "
+                                                    f"{args.train_warmup} warm-up sweeps, one snapshot per sweep",
+                     "samples": int(Xtr.shape[0]), "test_samples": int(Xte.shape[0]), "data_s": t_data,
+                     "train_s": t_train, "test_rms": test_rms, "test_target_sd": float(yte.std()),
                      "epochs": args.epochs, "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
                      "target_variance": float(np.var(ytr))},
         "e2e": {"value": e2e, "unit": "independent samples/s (S_CDW, tau_int-corrected)",
@@ -962,8 +998,8 @@ def run_learned(args):
     return 0
 
 
-SERVING_SIDES = (4, 6, 8)
-SERVING_BETAS = (1.0, 2.0, 4.0)
+SERVING_SIDES = (6, 8, 10, 12, 16)
+SERVING_BETAS = (4.0, 8.0, 12.0)
 SERVING_LAMBDAS = (0.15, 0.25, 0.35)
 
 
@@ -975,16 +1011,16 @@ def serving_params(side, beta, lam, seed):
 
 
 def run_serving(args):
-    """Continuous-batching service under Poisson arrivals.
-
-    Each request asks for args.req_sweeps sweeps (plain) or cumulative steps (learned) of one
-    chain with its own lattice side, beta, lambda, seed, chain word and initial fields; side,
-    beta, lambda and the sampler are drawn uniformly (the sizes are scaled down from 6..16 and
-    beta 4..12 so that a request takes well under a second to a few seconds).  Learned requests
-    carry a small seeded network (the cumulative accept keeps them exact whatever it is).
-    Reported: served chain-sweeps/s, request latency (arrival to result on the host)
-    percentiles, queueing delay, and the latency of the same kinds served alone on an idle GPU.
-    """
+    """Continuous-batching service under Poisson arrivals, on the serving workload's shape: lattice
+    side in {6, 8, 10, 12, 16}, beta in {4, 8, 12}, lambda in {0.15, 0.25, 0.35} (45 kinds), learned
+    or plain sampler per request, each drawn uniformly.  Stated reductions: args.duration seconds of
+    arrivals at args.rate per second (not 1000 requests), args.req_sweeps sweeps or cumulative steps
+    per request (not 500), plain block moves on a run of args.serve_block_sites sites per sweep (a
+    full sweep at 16x16, beta = 12 is about a minute of block moves).  Learned requests carry a small
+    seeded network (the cumulative accept keeps them exact whatever it is).  Reported: served
+    chain-sweeps/s, latency (arrival to result on the host) percentiles overall and per kind, queueing
+    delay, and one request of each (side, beta, sampler) served alone on an idle GPU against the same
+    kinds in the mix."""
     import numpy as np
     import torch
     import paper_1905_07440_gb300 as hq
@@ -1003,18 +1039,21 @@ def run_serving(args):
         lam = float(rng.choice(SERVING_LAMBDAS))
         sampler = "learned" if rng.random() < args.learned_frac else "plain"
         p = serving_params(side, beta, lam, workloads.BATCHED.seed + 7919 * k)
-        r = Request(rid=k, params=p, X0=workloads.initial_fields(p, 1, seed=10_000 + k)[0], sweeps=args.req_sweeps,
-                    sampler=sampler, theta=theta if sampler == "learned" else None, chain_id=k, arrival=t)
-        r.kind = (side, beta, sampler)
+        r = Request(rid=k, params=p, X0=workloads.initial_fields(p, 1, seed=10_000 + k)[0] - p.g / (p.mass * p.omega ** 2),
+                    sweeps=args.req_sweeps, sampler=sampler, theta=theta if sampler == "learned" else None,
+                    chain_id=k, arrival=t)
+        r.kind = (side, beta, lam, sampler)
         reqs.append(r)
-    backend = GpuBackend()
+
+    def backend():
+        return GpuBackend(block_sites=args.serve_block_sites, window=args.serve_window)
 
     def server():
-        return Server(backend, args.hbm_budget, args.slots, max_pools=args.max_pools)
+        return Server(backend(), args.hbm_budget, args.slots, max_pools=args.max_pools)
 
     # warm-up: one request of each lattice side and sampler (kernel loading, allocator)
-    warm = [Request(rid=-1, params=serving_params(s_, 1.0, 0.25, 1), X0=workloads.initial_fields(
-        serving_params(s_, 1.0, 0.25, 1), 1)[0], sweeps=1, sampler=sm, theta=theta)
+    warm = [Request(rid=-1, params=serving_params(s_, 4.0, 0.25, 1), X0=workloads.initial_fields(
+        serving_params(s_, 4.0, 0.25, 1), 1)[0], sweeps=1, sampler=sm, theta=theta)
         for s_ in SERVING_SIDES for sm in ("plain", "learned")]
     server().run(warm)
     torch.cuda.synchronize()
@@ -1026,7 +1065,7 @@ def run_serving(args):
             peak["bytes"] = max(peak["bytes"], self.used)
             peak["pools"] = max(peak["pools"], len(self.pools))
 
-    srv = Tracking(backend, args.hbm_budget, args.slots, max_pools=args.max_pools)
+    srv = Tracking(backend(), args.hbm_budget, args.slots, max_pools=args.max_pools)
     sampler = ClockSampler()
     sampler.start()
     t0 = time.perf_counter()
@@ -1036,37 +1075,47 @@ def run_serving(args):
     pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
     lat = np.array([r.done - r.arrival for r in done]) * 1e3
     wait = np.array([r.admitted - r.arrival for r in done]) * 1e3
+    kinds = {}
+    for r in done:
+        kinds.setdefault(r.kind, []).append((r.done - r.arrival) * 1e3)
+    by_kind = {f"{s_}x{s_} beta={b:g} lambda={l:g} {sm}": {"n": len(v), "p50": pct(np.array(v), 50),
+                                                          "max": float(max(v))}
+               for (s_, b, l, sm), v in sorted(kinds.items())}
     by_side = {}
     for side in SERVING_SIDES:
         lk = np.array([r.done - r.arrival for r in done if r.kind[0] == side]) * 1e3
         by_side[f"{side}x{side}"] = {"n": int(lk.size), "p50": pct(lk, 50), "p99": pct(lk, 99)}
-    # the same kinds alone (one request at a time, idle GPU) against the mix
+    # one request of each (side, beta, sampler) alone (lambda = 0.25) against the same kinds in the mix
     alone = {}
     for side in SERVING_SIDES:
-        for beta in (SERVING_BETAS[0], SERVING_BETAS[-1]):
-            ts = []
-            for j in range(3):
-                p = serving_params(side, beta, 0.25, 123 + j)
-                r = Request(rid=j, params=p, X0=workloads.initial_fields(p, 1, seed=j)[0], sweeps=args.req_sweeps)
+        for beta in SERVING_BETAS:
+            for sm in ("plain", "learned"):
+                p = serving_params(side, beta, 0.25, 123)
+                r = Request(rid=0, params=p, X0=workloads.initial_fields(p, 1, seed=5)[0] - p.g / (p.mass * p.omega ** 2),
+                            sweeps=args.req_sweeps, sampler=sm, theta=theta if sm == "learned" else None)
                 a = time.perf_counter()
                 server().run([r])
-                ts.append((time.perf_counter() - a) * 1e3)
-            mixed = np.array([r.done - r.arrival for r in done if r.kind == (side, beta, "plain")]) * 1e3
-            alone[f"{side}x{side} beta={beta:g} plain"] = {"alone_ms": float(np.median(ts)), "mix_p50_ms": pct(mixed, 50),
-                                                           "mix_n": int(mixed.size)}
+                mixed = np.array([x.done - x.arrival for x in done if x.kind[0] == side and x.kind[1] == beta
+                                  and x.kind[3] == sm]) * 1e3
+                alone[f"{side}x{side} beta={beta:g} {sm}"] = {"alone_ms": (time.perf_counter() - a) * 1e3,
+                                                               "mix_p50_ms": pct(mixed, 50), "mix_n": int(mixed.size)}
     served = sum(r.sweeps for r in done)
     n_learned = sum(1 for r in done if r.sampler == "learned")
     line = {"metric": METRIC, "mode": "serving", "value": served / wall, "unit": "chain-sweeps/s (served)",
-            "higher_is_better": True, "dtype": "f64 (learned requests: bf16-weight/fp32 network)", "data": "synthetic",
-            "config": {"workload": "Poisson arrivals; side in %s, beta in %s, lambda in %s, learned fraction %g"
-                                   % (SERVING_SIDES, SERVING_BETAS, SERVING_LAMBDAS, args.learned_frac),
+            "higher_is_better": True, "dtype": "f64 (learned requests: bf16-operand/fp32 network)", "data": "synthetic",
+            "config": {"workload": "Poisson arrivals; side in %s, beta in %s, lambda in %s (45 kinds), learned "
+                                   "fraction %g" % (SERVING_SIDES, SERVING_BETAS, SERVING_LAMBDAS, args.learned_frac),
                        "rate_per_s": args.rate, "duration_s": args.duration, "sweeps_per_request": args.req_sweeps,
-                       "slots_per_pool": args.slots, "max_pools": args.max_pools, "hbm_budget_bytes": args.hbm_budget},
-            "requests": len(done), "learned_requests": n_learned, "wall_s": wall, "requests_per_s": len(done) / wall,
+                       "plain_block_sites": args.serve_block_sites, "learned_window": args.serve_window,
+                       "slots_per_pool": args.slots, "max_pools": args.max_pools, "hbm_budget_bytes": args.hbm_budget,
+                       "reductions": "request count (duration x rate, not 1000), sweeps per request (not 500), "
+                                     "plain block moves on a run of sites"},
+            "requests": len(done), "learned_requests": n_learned, "kinds_served": len(kinds), "wall_s": wall,
+            "requests_per_s": len(done) / wall,
             "latency_ms": {"p50": pct(lat, 50), "p90": pct(lat, 90), "p99": pct(lat, 99), "max": float(lat.max())},
             "queue_ms": {"p50": pct(wait, 50), "p99": pct(wait, 99)}, "latency_by_side_ms": by_side,
-            "alone_vs_mix": alone, "peak_pool_bytes": int(peak["bytes"]), "peak_pools": peak["pools"],
-            "clocks": clocks}
+            "latency_by_kind_ms": by_kind, "alone_vs_mix": alone, "peak_pool_bytes": int(peak["bytes"]),
+            "peak_pools": peak["pools"], "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -1373,6 +1422,218 @@ def run_largest_learned(args):
     return 0
 
 
+def run_training(args):
+    """Training protocol of the learned-proposal workload (paper, Training: tens of thousands of
+    configurations of the conventional sampler with a train/test split).  Per temperature
+    (beta = 8 and 16, 8x8, the headline couplings): 256 plain chains from the ordered start,
+    args.train_warmup sweeps, then one snapshot (fields, exact log|det M|) per sweep; chains
+    0..191 give the training set, 192..255 the held-out test set (75/25 by chain, so no test
+    configuration is correlated with a training one).  Reported: the test-set RMS of F against
+    log|det M| (both centred by the training mean), and on deployment lattices (12x12 at beta = 8,
+    16x16 at beta = 16) the RMS of the centred differences over configurations of the plain
+    sampler there (local sweeps from the ordered start), against the spread of log|det M|."""
+    import numpy as np
+    import torch
+    import paper_1905_07440_gb300 as hq
+    dev = torch.device("cuda", 0)
+    out = {"mode": "training protocol", "config": {"snapshots": {}, "epochs": args.epochs, "batch": 64,
+                                                   "lr": args.lr, "split": "chains 0-191 train, 192-255 test"}}
+    for beta, snaps, deploy in ((8.0, args.train_snapshots_b8, workloads.MEDIUM),
+                                (16.0, args.train_snapshots_b16, workloads.LARGEST)):
+        small = workloads.LARGEST.with_(nx=8, ny=8, beta=beta)
+        t0 = time.perf_counter()
+        tr = hq.Engine(small.with_(seed=small.seed + 7), 256)
+        tr.set_fields(start_fields(small, 256, args.start_amplitude, workloads.DEFAULT_SEED + 5000))
+        tr.sweep(args.train_warmup)
+        X = torch.empty((snaps, 256, small.n_slices, small.n_sites), dtype=torch.float64, device=dev)
+        Y = np.empty((snaps, 256))
+        for k in range(snaps):
+            tr.sweep(1)
+            X[k] = torch.from_numpy(tr.get_fields()).to(dev)
+            Y[k] = tr.log_weight()[1]
+        tr.close()
+        t_data = time.perf_counter() - t0
+        Xtr = X[:, :192].reshape(-1, small.n_slices, small.n_sites).contiguous()
+        Xte = X[:, 192:].reshape(-1, small.n_slices, small.n_sites).contiguous()
+        del X
+        ytr, yte = Y[:, :192].reshape(-1), Y[:, 192:].reshape(-1)
+        mu = ytr.mean()
+        ytr_d = torch.from_numpy(ytr - mu).to(dev)
+        yte_d = torch.from_numpy(yte - mu).to(dev)
+        net = hq.Engine(small, 1)
+        B = 2048
+        net.attach_network(B, Xtr.shape[0])
+        net.set_params(hq.init_network(args.nn_seed))
+        t1 = time.perf_counter()
+        losses = []
+        for k in range(3):
+            ep = args.epochs // 3 + (args.epochs % 3 if k == 2 else 0)
+            losses.extend(net.nn_train(Xtr, ytr_d, epochs=ep, batch=64, lr=args.lr * 0.5 ** k, seed=args.nn_seed + k))
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t1
+
+        def mse(Xs, ys):
+            tot, n = 0.0, 0
+            for a in range(0, Xs.shape[0], B):
+                nb = min(B, Xs.shape[0] - a)
+                _, l = net.nn_gradient(Xs[a:a + nb], ys[a:a + nb])
+                tot += l * nb
+                n += nb
+            return tot / n
+
+        train_mse, test_mse = mse(Xtr, ytr_d), mse(Xte, yte_d)
+        theta = net.get_params()
+        net.close()
+        del Xtr, Xte
+        # deployment lattice: configurations of the exact plain sampler there (local sweeps from the
+        # ordered start), F of the network trained at 8x8 against their log|det M|
+        dp = deploy
+        e = hq.Engine(dp.with_(seed=dp.seed + 77), 64, max_series=0)
+        e.attach_network(4, 8)
+        e.set_params(theta)
+        e.set_fields(start_fields(dp, 64, args.start_amplitude, workloads.DEFAULT_SEED + 77))
+        e.sweep(args.deploy_relax, global_=False)
+        Fs, Ls = [], []
+        for _ in range(args.deploy_samples):
+            e.sweep(args.deploy_gap, global_=False)
+            Fs.append(e.nn_eval())
+            Ls.append(e.log_weight()[1])
+        e.close()
+        Fs, Ls = np.concatenate(Fs), np.concatenate(Ls)
+        dlt = (Fs - Fs.mean()) - (Ls - Ls.mean())
+        key = f"8x8 beta={beta:g}"
+        out["config"]["snapshots"][key] = snaps
+        out[key] = {"train_samples": int(ytr.size), "test_samples": int(yte.size), "data_s": t_data,
+                    "train_s": t_train, "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+                    "train_rms": math.sqrt(train_mse), "test_rms": math.sqrt(test_mse),
+                    "target_sd_train": float(ytr.std()), "target_sd_test": float(yte.std()),
+                    "deployment": {"lattice": f"{dp.nx}x{dp.ny} beta={dp.beta:g}", "configurations": int(Fs.size),
+                                   "rms_centred": float(np.sqrt(np.mean(dlt ** 2))),
+                                   "logdet_sd": float(Ls.std())}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_sections(args):
+    """Section rooflines from the per-section cycle counters of a -DHQ_SECTION_TIMING build (its
+    own library variant): the local phase's wrap and delayed-update flush, and the block moves' QR,
+    Q formation, T update and products, on the plain 8x8, beta = 8 workload with one chain per SM
+    (152 chains), so that a CTA's cycles are its SM's.  Flops per section: wrap 4 N^2 (nx + ny) +
+    2 N^2 per slice, flush 2 N^2 per accepted local move."""
+    import numpy as np
+    import torch
+    from paper_1905_07440_gb300 import build
+    lib = build.build(extra=("-DHQ_SECTION_TIMING",), variant="timing")
+    import paper_1905_07440_gb300 as hq
+    hq.load_library(lib)
+    dev = torch.device("cuda", 0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    p = workloads.BATCHED
+    C = args.chains or sms
+    peak = hq.fp64_peak_tflops(20, kind=hq.HQ_PROBE_DFMA)
+    eng = hq.Engine(p, C, max_series=args.steps + 4)
+    eng.set_fields(workloads.ordered_fields(p, C, args.start_amplitude, seed=workloads.DEFAULT_SEED))
+    eng.sweep(2)
+    torch.cuda.synchronize()
+    hq.section_cycles()
+    o0 = eng.observables()
+    clocks = ClockSampler()
+    clocks.start()
+    eng.sweep(args.steps, local=True, global_=False)
+    torch.cuda.synchronize()
+    cyc_local = hq.section_cycles()
+    eng.sweep(1, local=False, global_=True)
+    torch.cuda.synchronize()
+    cyc_block = hq.section_cycles()
+    clk = clocks.stop()
+    o1 = eng.observables()
+    acc = sum(b["local_accepted"] - a["local_accepted"] for a, b in zip(o0, o1))
+    hz = (clk["sm_mhz"] or 2070.0) * 1e6
+    n, L = p.n_sites, p.n_slices
+    per_sm = peak / sms
+    fl_wrap = args.steps * C * L * (4.0 * n * n * (p.nx + p.ny) + 2.0 * n * n)
+    fl_flush = 2.0 * n * n * acc
+
+    def roof(fl, cycles):
+        t = cycles / hz
+        return {"tflops_per_sm": fl / t / 1e12 if t else None, "frac_of_per_sm_peak": fl / t / 1e12 / per_sm if t else None,
+                "sm_seconds": t, "gflop": fl / 1e9}
+    out = {"mode": "section rooflines", "config": {"workload": "plain 8x8 beta=8 L=80", "chains": C, "sms": sms,
+                                                   "local_sweeps": args.steps, "clock_mhz": hz / 1e6},
+           "peak_tflops_dfma": peak, "wrap": roof(fl_wrap, cyc_local.get("wrap", 0)),
+           "flush": roof(fl_flush, cyc_local.get("flush", 0)), "local_accepted": acc,
+           "local_sections_cycles": cyc_local, "block_sections_cycles": cyc_block, "clocks": clk}
+    # block moves: one move per site per chain; per chunk of m slices QR 4/3 N^3, Q 4/3 N^3, T update N^3
+    q = math.ceil(L / p.n_wrap)
+    moves = C * n
+    out["block_qr"] = roof(moves * q * (4.0 / 3.0) * n ** 3, cyc_block.get("qr", 0))
+    out["block_form_q"] = roof(moves * q * (4.0 / 3.0) * n ** 3, cyc_block.get("form_q", 0))
+    out["block_t_update"] = roof(moves * (q - 1) * float(n) ** 3, cyc_block.get("t_update", 0))
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_agreement(args):
+    """Learned vs plain means from the same fields, every run with a fresh Philox key.  Per beta in
+    args.betas on an args.side x args.side lattice (headline couplings): 256 plain chains from the mean
+    field + N(0, 1/(M Omega^2)), args.relax sweeps, 16 snapshots two sweeps apart (training data), the
+    network trained on the tensor cores; then from the final fields a plain run, a learned run (local
+    moves at every slice) and a second plain run of args.tau_steps sweeps or steps each.  Reported per
+    observable: mean and error over the chains' means, tau_int, the second-half minus first-half
+    difference, and the z-scores learned - plain and plain2 - plain."""
+    import numpy as np
+    import torch
+    import paper_1905_07440_gb300 as hq
+    names = ((hq.HQ_OBS_X2, "x2"), (hq.HQ_OBS_DOUBLE_OCC, "double_occ"), (hq.HQ_OBS_SCDW, "s_cdw"))
+    out = {"mode": "agreement", "config": {"lattice": f"{args.side}x{args.side}", "chains": 256,
+                                           "warmup_sweeps": args.relax + 32, "measured": args.tau_steps,
+                                           "learned_window": args.agree_window}}
+    for beta in (float(b) for b in args.betas.split(",")):
+        p = workloads.HolsteinParams(nx=args.side, ny=args.side, beta=beta)
+        x0 = -p.g / (p.mass * p.omega ** 2)
+        A = hq.Engine(p, 256)
+        A.set_fields(workloads.initial_fields(p, 256) + x0)
+        A.sweep(args.relax)
+        Xs, ys = [], []
+        for _ in range(16):
+            A.sweep(2)
+            Xs.append(A.get_fields())
+            ys.append(A.log_weight()[1])
+        Xeq = A.get_fields()
+        A.close()
+        Xtr, ytr = np.concatenate(Xs), np.concatenate(ys)
+        ytr = ytr - ytr.mean()
+        net = hq.Engine(p, 1)
+        net.attach_network(64, Xtr.shape[0])
+        net.set_params(hq.init_network(args.nn_seed))
+        Xd, yd = torch.from_numpy(Xtr).cuda(), torch.from_numpy(ytr).cuda()
+        for k in range(3):
+            net.nn_train(Xd, yd, epochs=args.epochs // 3, batch=64, lr=args.lr * 0.5 ** k, seed=args.nn_seed + k)
+        theta = net.get_params()
+        net.close()
+        row = {}
+        for kind, seed in (("plain", 777), ("learned", 888), ("plain2", 999)):
+            m = hq.Engine(p.with_(seed=seed), 256, max_series=args.tau_steps)
+            m.set_fields(Xeq)
+            if kind == "learned":
+                m.attach_network(4, 8)
+                m.set_params(theta)
+                m.set_inner_window(args.agree_window)
+                m.cumulative(args.tau_steps, 1, measure=True)
+                st = m.learned_stats()
+                row["acceptance"] = sum(x["cumulative_accepted"] for x in st) / sum(x["cumulative_proposed"] for x in st)
+            else:
+                m.sweep(args.tau_steps)
+            row[kind] = series_stats(hq, m, 0, names)
+            m.close()
+        for a, b in (("learned", "plain"), ("plain2", "plain")):
+            row[f"z_{a}_vs_{b}"] = {k: (row[a][k]["mean"] - row[b][k]["mean"]) / math.hypot(row[a][k]["err"], row[b][k]["err"])
+                                    for _, k in names}
+        out[f"beta={beta:g}"] = row
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_peaks():
     """FP64 pipe evidence: DFMA and DMMA probes of the library, cuBLAS DGEMM/SGEMM via torch."""
     import torch
@@ -1412,7 +1673,19 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default="headline")
     ap.add_argument("--relax", type=int, default=200, help="headline: learned steps before the measured series")
+    ap.add_argument("--side", type=int, default=6, help="agreement mode: lattice side")
+    ap.add_argument("--betas", default="2,3,4", help="agreement mode: comma-separated beta values")
+    ap.add_argument("--agree-window", type=int, default=0, help="agreement mode: learned window (0: every slice)")
+    ap.add_argument("--inner-block-sites", type=int, default=0,
+                    help="headline: block moves per cumulative step on this many sites (0: none)")
+    ap.add_argument("--start-amplitude", type=float, default=0.9,
+                    help="headline: staggered amplitude of the ordered start (0: mean-field start)")
     ap.add_argument("--train-chains", type=int, default=256, help="headline: plain chains for training data")
+    ap.add_argument("--train-snapshots-b8", type=int, default=392, help="training mode: sweeps of snapshots, beta 8")
+    ap.add_argument("--train-snapshots-b16", type=int, default=200, help="training mode: sweeps of snapshots, beta 16")
+    ap.add_argument("--deploy-relax", type=int, default=10, help="training mode: local sweeps before deployment")
+    ap.add_argument("--deploy-samples", type=int, default=8, help="training mode: deployment snapshots")
+    ap.add_argument("--deploy-gap", type=int, default=1, help="training mode: local sweeps between snapshots")
     ap.add_argument("--cpu-steps", type=int, default=2, help="headline: oracle steps per core in the CPU baseline")
     ap.add_argument("--e2e-steps", type=int, default=5, help="headline: steps through host buffers")
     ap.add_argument("--plain-block-sites", type=int, default=16, help="headline: block-move sites timed per plain sweep")
@@ -1425,8 +1698,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--nn-seed", type=int, default=1)
-    ap.add_argument("--train-warmup", type=int, default=24)
-    ap.add_argument("--train-snapshots", type=int, default=32)
+    ap.add_argument("--train-warmup", type=int, default=8)
+    ap.add_argument("--train-snapshots", type=int, default=24)
     ap.add_argument("--tau-steps", type=int, default=240)
     ap.add_argument("--cnn", action="store_true", help="learned mode: convolutional action for block moves")
     ap.add_argument("--deploy", choices=("largest", "medium"), default="largest",
@@ -1437,9 +1710,11 @@ def main():
     ap.add_argument("--plain-full", action="store_true",
                     help="largest-learned mode: also time one full plain sweep (minutes at 16x16)")
     ap.add_argument("--cnn-lr", type=float, default=3e-3)
-    ap.add_argument("--rate", type=float, default=40.0, help="serving mode: requests per second")
+    ap.add_argument("--rate", type=float, default=20.0, help="serving mode: requests per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serving mode: seconds of arrivals")
-    ap.add_argument("--req-sweeps", type=int, default=10, help="serving mode: sweeps per request")
+    ap.add_argument("--req-sweeps", type=int, default=2, help="serving mode: sweeps per request")
+    ap.add_argument("--serve-block-sites", type=int, default=8, help="serving mode: plain block-move sites per sweep")
+    ap.add_argument("--serve-window", type=int, default=32, help="serving mode: learned window (slices)")
     ap.add_argument("--slots", type=int, default=16, help="serving mode: chain slots per pool")
     ap.add_argument("--max-pools", type=int, default=32, help="serving mode: live pools (streams)")
     ap.add_argument("--learned-frac", type=float, default=0.5, help="serving mode: share of learned requests")
@@ -1456,6 +1731,12 @@ def main():
         sys.exit(run_largest_learned(args))
     if args.workload == "serving":
         sys.exit(run_serving(args))
+    if args.workload == "training":
+        sys.exit(run_training(args))
+    if args.workload == "sections":
+        sys.exit(run_sections(args))
+    if args.workload == "agreement":
+        sys.exit(run_agreement(args))
     if args.peaks:
         sys.exit(run_peaks())
     if args.workload == "autotune":

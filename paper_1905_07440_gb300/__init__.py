@@ -572,7 +572,7 @@ def tau_int(series, c=6.0):
 
 
 SECTIONS = ("dl", "kin", "prepivot", "qr", "form_q", "t_update", "logdet", "move", "wait", "prop_prep",
-            "prop_seq", "wrap", "restab_prod", "restab_qr", "restab_green", "measure")
+            "prop_seq", "wrap", "restab_prod", "restab_qr", "restab_green", "measure", "flush")
 
 
 def wait_probe(limit_seconds=0.05, stream=None):

@@ -31,14 +31,18 @@ def _stale(obj, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose=False, extra=()):
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose=False, extra=(), variant=None):
+    """Compile and link the library; with `variant` (e.g. "timing" with extra=("-DHQ_SECTION_TIMING",))
+    into its own build directory and libholstein_dqmc_<variant>.so, leaving the default build alone."""
+    build_dir = BUILD if variant is None else BUILD + "_" + variant
+    lib = LIB if variant is None else os.path.join(HERE, f"libholstein_dqmc_{variant}.so")
+    os.makedirs(build_dir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "holstein_dqmc.h"))
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(build_dir, src.replace(".cu", ".o"))
         if _stale(o, [s] + headers):
             jobs.append([nvcc(), *ARCH, *FLAGS, *extra, "-c", s, "-o", o])
 
@@ -54,10 +58,10 @@ def build(verbose=False, extra=()):
         for out in ex.map(run, jobs):
             if verbose and out.strip():
                 print(out)
-    objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
-    if _stale(LIB, objs):
-        run([nvcc(), *ARCH, "-shared", "-o", LIB, *objs])
-    return LIB
+    objs = [os.path.join(build_dir, s.replace(".cu", ".o")) for s in SOURCES]
+    if _stale(lib, objs):
+        run([nvcc(), *ARCH, "-shared", "-o", lib, *objs])
+    return lib
 
 
 if __name__ == "__main__":

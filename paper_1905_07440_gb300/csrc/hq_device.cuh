@@ -21,7 +21,7 @@ namespace hq {
 enum {
   SEC_DL = 0, SEC_KIN, SEC_PREPIVOT, SEC_QR, SEC_FORMQ, SEC_TUPD, SEC_LOGDET, SEC_MOVE, SEC_WAIT,
   SEC_PROP_PREP, SEC_PROP_SEQ, SEC_WRAP, SEC_RESTAB_PROD, SEC_RESTAB_QR, SEC_RESTAB_GREEN, SEC_MEASURE,
-  SEC_COUNT
+  SEC_FLUSH, SEC_COUNT
 };
 #ifdef HQ_SECTION_TIMING
 static __device__ unsigned long long g_section_cycles[SEC_COUNT];  // per translation unit
@@ -517,6 +517,7 @@ __device__ inline double lu_logdet(double* A, int ld, int n, int* piv, int* sint
       if (lane == 0) {
         sint[0] = bi;
         piv[j] = bi;
+        red[0] = 1.0 / aj[bi];  // reciprocal of the pivot, once for the CTA
       }
     }
     __syncthreads();
@@ -530,7 +531,7 @@ __device__ inline double lu_logdet(double* A, int ld, int n, int* piv, int* sint
       }
       __syncthreads();
     }
-    const double rp = 1.0 / aj[j];
+    const double rp = red[0];
     for (int r = j + 1 + tid; r < n; r += HQ_THREADS) aj[r] *= rp;
     __syncthreads();
     const int m = n - j - 1;
@@ -540,13 +541,21 @@ __device__ inline double lu_logdet(double* A, int ld, int n, int* piv, int* sint
     }
     __syncthreads();
   }
+  __syncthreads();  // red[0] is read above; block_sum reuses red
   double a = 0.0;
   for (int j = tid; j < n; j += HQ_THREADS) a += log(fabs(A[(size_t)j * ld + j]));
   return block_sum(a, red);
 }
 
-// Y <- A^-1 Y for the LU factors from lu_logdet (n right-hand sides, one warp per column).
-__device__ inline void lu_solve(const double* A, int ld, int n, const int* piv, double* Y) {
+// rd[j] = 1 / U_jj of the LU factors (one division per diagonal entry, not per use).
+__device__ __forceinline__ void lu_diag_recip(const double* A, int ld, int n, double* rd) {
+  for (int j = threadIdx.x; j < n; j += HQ_THREADS) rd[j] = 1.0 / A[(size_t)j * ld + j];
+  __syncthreads();
+}
+
+// Y <- A^-1 Y for the LU factors from lu_logdet (n right-hand sides, one warp per column);
+// rd: the reciprocals of U's diagonal (lu_diag_recip).
+__device__ inline void lu_solve(const double* A, int ld, int n, const int* piv, const double* rd, double* Y) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int c = warp; c < n; c += HQ_WARPS) {
     double* y = Y + (size_t)c * ld;
@@ -565,7 +574,7 @@ __device__ inline void lu_solve(const double* A, int ld, int n, const int* piv, 
     }
     for (int j = n - 1; j >= 0; --j) {
       const double* uj = A + (size_t)j * ld;
-      const double yj = y[j] / uj[j];
+      const double yj = y[j] * rd[j];
       __syncwarp();
       if (lane == 0) y[j] = yj;
       for (int r = lane; r < j; r += 32) y[r] = fma(-uj[r], yj, y[r]);

@@ -35,12 +35,12 @@ int section_cycles(unsigned long long* out, int n) {
 
 struct Smem {
   double *ex, *exi, *ey, *eyi;
-  double *dl, *u2, *xn, *dlt, *es, *dcorr, *tau, *norm2, *rinv, *vs, *dv;
+  double *dl, *u2, *xn, *dlt, *es, *dcorr, *tau, *norm2, *rinv, *vs, *dv, *rd;
   double *red, *scal;
   int *perm, *piv, *sint;
 };
 
-static constexpr int kSmemVecs = 12;  // vs takes two
+static constexpr int kSmemVecs = 13;  // vs takes two
 
 __host__ __device__ inline size_t smem_layout_bytes(int nx, int ny, int n) {
   return (size_t)(2 * nx * nx + 2 * ny * ny + kSmemVecs * n + 32 + 16) * sizeof(double) +
@@ -68,6 +68,7 @@ __device__ inline Smem carve(const Dev& d, double* base) {
   s.rinv = p; p += n;
   s.vs = p; p += 2 * n;
   s.dv = p; p += n;
+  s.rd = p; p += n;
   s.red = p; p += 32;
   s.scal = p; p += 16;
   int* q = reinterpret_cast<int*>(p);
@@ -99,12 +100,13 @@ __device__ double finish_logdet(const Dev& d, int c, const Smem& sm, const doubl
   HQ_TIC(ld);
   double* A = chain_work(d, c, WK_M1);
   double* Y = chain_work(d, c, WK_M2);
+  for (int i = threadIdx.x; i < n; i += HQ_THREADS) sm.rinv[i] = 1.0 / fmax(sm.dv[i], 1.0);
+  __syncthreads();
   for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
     const int i = idx % n, col = idx / n;
-    const double D = sm.dv[i];
-    const double db = fmax(D, 1.0), ds = fmin(D, 1.0);
-    const double ut = U[(size_t)i * n + col] / db;
-    A[(size_t)col * n + i] = ut + ds * Tc[(size_t)col * n + i];
+    const double ds = fmin(sm.dv[i], 1.0);
+    const double ut = U[(size_t)i * n + col] * sm.rinv[i];
+    A[(size_t)col * n + i] = fma(ds, Tc[(size_t)col * n + i], ut);
     if (G0) Y[(size_t)col * n + i] = ut;
   }
   double lsum = 0.0;
@@ -112,7 +114,8 @@ __device__ double finish_logdet(const Dev& d, int c, const Smem& sm, const doubl
   const double lb = block_sum(lsum, sm.red);
   const double la = lu_logdet(A, n, n, sm.piv, sm.sint, sm.red);
   if (G0) {
-    lu_solve(A, n, n, sm.piv, Y);
+    lu_diag_recip(A, n, n, sm.rd);
+    lu_solve(A, n, n, sm.piv, sm.rd, Y);
     for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
       const int r = idx % n, col = idx / n;
       G0[(size_t)col * n + r] = Y[(size_t)r * n + col];
@@ -297,39 +300,50 @@ __device__ double green_two_sided(const Dev& d, int c, const Smem& sm, int l, do
     const double* UL = d.stU + b * n * n;
     const double* TL = d.stT + b * n * n;
     const double* DL = d.stD + b * n;
-    gemm_nn<true, false>(n, UR, UL, M1, n);   // UR^T UL
+    // reciprocals of the large parts DRb = max(DR, 1), DLb = max(DL, 1) (one division each)
+    double* rdr = sm.rinv;
+    double* rdl = sm.norm2;
+    for (int i = threadIdx.x; i < n; i += HQ_THREADS) {
+      rdr[i] = 1.0 / fmax(DR[i], 1.0);
+      rdl[i] = 1.0 / fmax(DL[i], 1.0);
+    }
+    gemm_nn<true, false>(n, UR, UL, M1, n);   // UR^T UL (ends with a barrier)
     gemm_nn<false, true>(n, TR, TL, M2, n);   // TR TL^T
     for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
       const int i = idx % n, j = idx / n;
-      const double drb = fmax(DR[i], 1.0), drs = fmin(DR[i], 1.0);
-      const double dlb = fmax(DL[j], 1.0), dls = fmin(DL[j], 1.0);
+      const double drs = fmin(DR[i], 1.0), dls = fmin(DL[j], 1.0);
       const size_t o = (size_t)j * n + i;
-      M2[o] = M1[o] / (drb * dlb) + drs * M2[o] * dls;
-      M3[o] = UR[(size_t)i * n + j] / drb;
+      M2[o] = fma(M1[o] * rdr[i], rdl[j], drs * M2[o] * dls);
+      M3[o] = UR[(size_t)i * n + j] * rdr[i];
     }
     for (int i = threadIdx.x; i < n; i += HQ_THREADS) lsum += log(fmax(DR[i], 1.0)) + log(fmax(DL[i], 1.0));
     __syncthreads();
     la = lu_logdet(M2, n, n, sm.piv, sm.sint, sm.red);
-    lu_solve(M2, n, n, sm.piv, M3);
+    lu_diag_recip(M2, n, n, sm.rd);
+    lu_solve(M2, n, n, sm.piv, sm.rd, M3);
     // M1 <- UL DLb^-1, Gf = M1 M3
     for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
       const int j = idx / n;
-      M1[idx] = UL[idx] / fmax(DL[j], 1.0);
+      M1[idx] = UL[idx] * rdl[j];
     }
     __syncthreads();
     gemm_nn<false, false>(n, M1, M3, Gf, n);
   } else {
+    double* rdr = sm.rinv;
+    for (int i = threadIdx.x; i < n; i += HQ_THREADS) rdr[i] = 1.0 / fmax(DR[i], 1.0);
+    __syncthreads();
     for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
       const int i = idx % n, j = idx / n;
-      const double drb = fmax(DR[i], 1.0), drs = fmin(DR[i], 1.0);
-      const double ut = UR[(size_t)i * n + j] / drb;
-      M2[(size_t)j * n + i] = ut + drs * TR[(size_t)j * n + i];
+      const double drs = fmin(DR[i], 1.0);
+      const double ut = UR[(size_t)i * n + j] * rdr[i];
+      M2[(size_t)j * n + i] = fma(drs, TR[(size_t)j * n + i], ut);
       Gf[(size_t)j * n + i] = ut;
     }
     for (int i = threadIdx.x; i < n; i += HQ_THREADS) lsum += log(fmax(DR[i], 1.0));
     __syncthreads();
     la = lu_logdet(M2, n, n, sm.piv, sm.sint, sm.red);
-    lu_solve(M2, n, n, sm.piv, Gf);
+    lu_diag_recip(M2, n, n, sm.rd);
+    lu_solve(M2, n, n, sm.piv, sm.rd, Gf);
   }
   return block_sum(lsum, sm.red) + la;
 }
@@ -365,6 +379,37 @@ __device__ void measure_green(const Dev& d, int c, const Smem& sm, const double*
     acc[ACC_DOCC] += sm_m2 / n;
     acc[ACC_SCDW] += (4.0 * sm_sm * sm_sm + 2.0 * sm_g - 2.0 * conn) / n;
     acc[ACC_COUNT] += 1.0;
+  }
+}
+
+// Flush of the delayed updates: G += A B^T (n x n, rank kk; A, B [kk][n]) as a register-tiled
+// contraction, 4 x 4 entries of G per thread (8 loads per 16 FMAs instead of 2 per FMA); every
+// entry still accumulates its kk products in order m = 0 .. kk-1 onto G, so the result does not
+// depend on the tiling.
+__device__ inline void flush_delayed(double* G, const double* A, const double* B, int n, int kk) {
+  const int tiles = n >> 2;  // n is a multiple of 4
+  for (int t = threadIdx.x; t < tiles * tiles; t += HQ_THREADS) {
+    const int r0 = (t % tiles) * 4, c0 = (t / tiles) * 4;
+    double acc[4][4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) acc[a][b] = G[(size_t)(c0 + b) * n + r0 + a];
+    for (int m = 0; m < kk; ++m) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = A[m * n + r0 + a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = B[m * n + c0 + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) G[(size_t)(c0 + b) * n + r0 + a] = acc[a][b];
   }
 }
 
@@ -457,13 +502,9 @@ __device__ void local_chunk_body(const Dev& d, int c, int s0, int s1, int measur
         ++kk;
         if (kk == k) {
           __syncthreads();
-          // flush: G += A B^T, an n x n x k FP64 contraction
-          for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
-            const int r = idx % n, col = idx / n;
-            double v = G[(size_t)col * n + r];
-            for (int m = 0; m < kk; ++m) v = fma(A[m * n + r], B[m * n + col], v);
-            G[(size_t)col * n + r] = v;
-          }
+          HQ_TIC(fl);
+          flush_delayed(G, A, B, n, kk);
+          HQ_TOC(fl, SEC_FLUSH);
           __syncthreads();
           for (int r = threadIdx.x; r < n; r += HQ_THREADS) sm.dcorr[r] = 0.0;
           kk = 0;
@@ -472,21 +513,23 @@ __device__ void local_chunk_body(const Dev& d, int c, int s0, int s1, int measur
       }
     }
     if (kk > 0) {
-      for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
-        const int r = idx % n, col = idx / n;
-        double v = G[(size_t)col * n + r];
-        for (int m = 0; m < kk; ++m) v = fma(A[m * n + r], B[m * n + col], v);
-        G[(size_t)col * n + r] = v;
-      }
+      HQ_TIC(fl);
+      flush_delayed(G, A, B, n, kk);
+      HQ_TOC(fl, SEC_FLUSH);
     }
     HQ_TOC(seq, SEC_PROP_SEQ);
     HQ_TIC(wr);
     // wrap: G_l = exp(-dtau K) D_l G_{l-1} D_l^-1 exp(dtau K), D_l = exp(-dtau V_l)
-    for (int r = threadIdx.x; r < n; r += HQ_THREADS) sm.dl[r] = exp(-d.dtau * (d.g * X[(size_t)s * n + r] - d.mu));
+    // (the proposal buffer u2 is free once the slice's moves are done: it takes 1 / D_l)
+    for (int r = threadIdx.x; r < n; r += HQ_THREADS) {
+      const double e = exp(-d.dtau * (d.g * X[(size_t)s * n + r] - d.mu));
+      sm.dl[r] = e;
+      sm.u2[r] = 1.0 / e;
+    }
     __syncthreads();
     for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
       const int r = idx % n, col = idx / n;
-      G[(size_t)col * n + r] = (sm.dl[r] * G[(size_t)col * n + r]) / sm.dl[col];
+      G[(size_t)col * n + r] = (sm.dl[r] * G[(size_t)col * n + r]) * sm.u2[col];
     }
     __syncthreads();
     kin_rows<LMAX, KIN_PLAIN>(G, n, n, sm.ex, sm.ey, d.nx, d.ny);
@@ -860,7 +903,7 @@ __device__ void block_move(const Dev& d, const Smem& sm, int c, int site) {
 // every worker stops taking tasks.  sched = [counter, abort, ..., progress[C] at
 // kSchedHeader], zeroed before the launch.
 template <int LMAX>
-__global__ void __launch_bounds__(HQ_THREADS) global_phase_kernel(Dev d) {
+__global__ void __launch_bounds__(HQ_THREADS, 2) global_phase_kernel(Dev d) {
   extern __shared__ double smraw[];
   __shared__ int s_task;
   const Smem sm = carve(d, smraw);

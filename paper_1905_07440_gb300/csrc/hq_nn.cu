@@ -37,6 +37,7 @@ struct NNSmem {
   uint2* frag;   // [TC_FRAGS] weight fragments of the tensor-core layers
   float* tcf;    // [TC_FLOATS] b1, b2, W3, b3
   float* f25;    // [32] f of the patches of a local move
+  int* nbr;      // [n][5] cross neighbours of every site: self, +x, -x, +y, -y
   double* red;   // [HQ_WARPS]
   double* pu2;   // [n] proposal uniforms (local)
   double* pxn;   // [n] proposed values
@@ -49,7 +50,7 @@ struct NNSmem {
 
 __host__ __device__ inline size_t nn_smem_bytes(int n, bool with_cnn = false) {
   size_t b = sizeof(uint2) * TC_FRAGS + sizeof(double) * (HQ_WARPS + 3 * (size_t)n + NN_GROUPS + 8) +
-             sizeof(float) * (TC_FLOATS + 32);
+             sizeof(float) * (TC_FLOATS + 32) + sizeof(int) * 5 * (size_t)n;
   if (with_cnn) b += sizeof(float) * CN_WPAD + sizeof(int) * (4 + 3 * CN_WIN + 2 * (size_t)n);
   return b;
 }
@@ -67,6 +68,7 @@ __device__ inline NNSmem nn_carve(int n, char* base, bool with_cnn = false) {
   float* f = (float*)p;
   s.tcf = f; f += TC_FLOATS;
   s.f25 = f; f += 32;
+  s.nbr = (int*)f; f += 5 * n;
   s.cw = nullptr;
   if (with_cnn) {
     s.cw = f; f += CN_WPAD;
@@ -165,7 +167,15 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
   const int c = blockIdx.x, n = d.n, L = d.L, NL = n * L;
   if (!d.active[c]) return;
   const NNSmem s = nn_carve(n, nraw, use_cnn != 0);
-  const NNFrags w = nn_build_frags(nn.wbf, s.frag, s.tcf);
+  for (int r = threadIdx.x; r < n; r += HQ_THREADS) {
+    const int x = r % d.nx, y = r / d.nx;
+    s.nbr[5 * r + 0] = r;
+    s.nbr[5 * r + 1] = (x + 1) % d.nx + d.nx * y;
+    s.nbr[5 * r + 2] = (x - 1 + d.nx) % d.nx + d.nx * y;
+    s.nbr[5 * r + 3] = x + d.nx * ((y + 1) % d.ny);
+    s.nbr[5 * r + 4] = x + d.nx * ((y - 1 + d.ny) % d.ny);
+  }
+  const NNFrags w = nn_build_frags(nn.wbf, s.frag, s.tcf);  // (ends with a barrier)
   if (use_cnn) cn_load_weights(cn.wbf, s.cw);
   double* X = d.X + (size_t)c * NL;
   float* fc = nn.fcache + (size_t)c * NL;
@@ -184,6 +194,7 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
   const uint32_t key0 = id[0], key1 = id[1], chain = id[2], step = id[3];
   long long nl_acc = 0, nb_acc = 0;
   double path = 0.0;                   // thread 0
+  int any_local = 0;                   // thread 0: a local move was accepted in this part
   bool fc_stale = false, cn_stale = false;  // uniform over the CTA
   const double kfac = d.mass / (2.0 * d.dtau), pfac = 0.5 * d.dtau * d.mass * (d.omega * d.omega);
   double du1, du2;
@@ -211,6 +222,7 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
     for (int part = 0; part < 2; ++part) {
     const bool local_part = (part == 0) == fwd;
     if (local_part && do_local) {
+      any_local = 0;
       if (fc_stale) {
         fc_eval_all(d, s, w, X, nn.x0, fc);
         fc_stale = false;
@@ -229,65 +241,64 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
           s.pds[i] = kfac * kin + pfac * (xn * xn - xo * xo);
         }
         __syncthreads();
-        for (int i0 = 0; i0 < n; ++i0) {
-          const int i = fwd ? i0 : n - 1 - i0;
-          // the 25 patches containing (sl, i): patch q has centre (sl - dl, i - c), q = 5 (dl + 2) + c;
-          // warps 0 and 1 evaluate q = 0..15 and 16..31 (q >= 25: padding)
-          if (warp < 2) {
+        // The moves of the slice run in warp 0 alone: a move's 25 patches are two tensor-core
+        // tiles, its change of F a fixed-order warp sum, and the decision, the field and the
+        // patch cache are updated without a CTA barrier (the other warps wait for the slice).
+        if (warp == 0) {
+          for (int i0 = 0; i0 < n; ++i0) {
+            const int i = fwd ? i0 : n - 1 - i0;
             const double xn = s.pxn[i];
-            const int x = i % d.nx, y = i / d.nx;
-            auto centre = [&](int q) {
-              const int dl = q / 5 - 2, cidx = q % 5;
-              const int cx_ = (cidx == 1) - (cidx == 2), cy_ = (cidx == 3) - (cidx == 4);
-              const int j = (x - cx_ + d.nx) % d.nx + d.nx * ((y - cy_ + d.ny) % d.ny);
-              return ((sl - dl + L) % L) * n + j;
+            // patch q = 5 (dl + 2) + c contains (sl, i): centre slice sl - dl, centre site the
+            // neighbour of i opposite to c (q >= 25: padding rows)
+            auto cslice = [&](int q) {
+              const int v = sl - (q / 5 - 2);
+              return v < 0 ? v + L : (v >= L ? v - L : v);
             };
-            float f0, f1;
-            nn_tile_f(w, [&](int row, int k) {
-              const int q = 16 * warp + row;
-              const int r = centre(q < 25 ? q : 24);
-              return patch_input(d, X, r / n, r % n, k, nn.x0, i, sl, xn, 0.0);
-            }, f0, f1);
-            if (t == 0) {
-              const int q0 = 16 * warp + g, q1 = q0 + 8;
-              if (q0 < 25) {
-                s.f25[q0] = f0;
-                s.gacc[q0] = (double)f0 - (double)fc[centre(q0)];
+            auto csite = [&](int q) {
+              const int c = q % 5;
+              return s.nbr[5 * i + (c == 0 ? 0 : (c & 1) ? c + 1 : c - 1)];
+            };
+            auto zv = [&](int q, int k) -> float {
+              q = q < 25 ? q : 24;
+              int ll = sl - (q / 5 - 2) + (k / 5 - 2);
+              ll = ll < 0 ? ll + L : (ll >= L ? ll - L : ll);
+              const int site = s.nbr[5 * csite(q) + k % 5];
+              const double v = (ll == sl && site == i) ? xn : X[(size_t)ll * n + site];
+              return (float)(v - nn.x0);
+            };
+            float fv[4];
+            nn_tile_f(w, [&](int row, int k) { return zv(row, k); }, fv[0], fv[1]);
+            nn_tile_f(w, [&](int row, int k) { return zv(16 + row, k); }, fv[2], fv[3]);
+            const int qs[4] = {g, g + 8, 16 + g, 24 + g};
+            double part = 0.0;
+            if (t == 0)
+              for (int a = 0; a < 4; ++a)
+                if (qs[a] < 25) part += (double)fv[a] - (double)fc[(size_t)cslice(qs[a]) * n + csite(qs[a])];
+            const double dF = warp_sum_fixed(part);
+            int acc = 0;
+            if (lane == 0) {
+              const double prob = exp(fmin(2.0 * dF - s.pds[i], 709.0));
+              acc = s.pu2[i] < prob;
+              if (acc) {
+                X[(size_t)sl * n + i] = xn;
+                path += dF;
+                any_local = 1;
               }
-              if (q1 < 25) {
-                s.f25[q1] = f1;
-                s.gacc[q1] = (double)f1 - (double)fc[centre(q1)];
-              }
+              nl_acc += acc;
             }
+            acc = __shfl_sync(HQ_FULL, acc, 0);
+            if (acc && t == 0)
+              for (int a = 0; a < 4; ++a)
+                if (qs[a] < 25) fc[(size_t)cslice(qs[a]) * n + csite(qs[a])] = fv[a];
+            __syncwarp();
           }
-          __syncthreads();
-          if (threadIdx.x == 0) {
-            double dF = 0.0;
-            for (int k = 0; k < 25; ++k) dF += s.gacc[k];
-            const double prob = exp(fmin(2.0 * dF - s.pds[i], 709.0));
-            const int acc = s.pu2[i] < prob;
-            s.scal[0] = acc;
-            if (acc) {
-              X[(size_t)sl * n + i] = s.pxn[i];
-              path += dF;
-            }
-            nl_acc += acc;
-          }
-          __syncthreads();
-          if (s.scal[0] != 0.0) {
-            if (threadIdx.x < 25) {
-              const int q = threadIdx.x;
-              const int dl = q / 5 - 2, cidx = q % 5;
-              const int cx_ = (cidx == 1) - (cidx == 2), cy_ = (cidx == 3) - (cidx == 4);
-              const int x = i % d.nx, y = i / d.nx;
-              const int j = (x - cx_ + d.nx) % d.nx + d.nx * ((y - cy_ + d.ny) % d.ny);
-              fc[((sl - dl + L) % L) * n + j] = s.f25[q];
-            }
-            cn_stale = true;
-          }
-          __syncthreads();
         }
+        __syncthreads();
       }
+      if (threadIdx.x == 0) s.scal[3] = any_local;
+      __syncthreads();
+      if (s.scal[3] != 0.0) cn_stale = true;
+      __syncthreads();
     }
     if (!local_part && do_block) {
       if (use_cnn && cn_stale) {

@@ -198,11 +198,15 @@ class Server:
 class GpuBackend:
     """Engines of the C ABI, each pool on a CUDA stream of its own."""
 
-    def __init__(self, device=0, nn_batch=4):
+    def __init__(self, device=0, nn_batch=4, block_sites=0, window=0):
+        """block_sites > 0: plain pools take their block moves on a run of that many sites per
+        sweep (hq_set_block_sites); window > 0: learned pools take their local moves on that
+        many slices per step (hq_set_inner_window)."""
         import torch
         import paper_1905_07440_gb300 as hq
         self.torch, self.hq, self.device = torch, hq, torch.device("cuda", device)
         self.nn_batch = nn_batch
+        self.block_sites, self.window = block_sites, window
         self._free_streams = []
         self._in_use = set()
 
@@ -233,7 +237,10 @@ class GpuBackend:
         if sampler == "learned":
             eng.attach_network(self.nn_batch, self.nn_batch)
             eng.set_params(theta)
+            eng.set_inner_window(self.window)
             nbytes += eng.nn_arena.numel()
+        else:
+            eng.set_block_sites(self.block_sites)
         for k in range(slots):
             eng.set_active(k, False)
         eng._done_event = None

@@ -89,6 +89,19 @@ def initial_fields(params: HolsteinParams, n_chains: int, seed: int = DEFAULT_SE
     return X
 
 
+def ordered_fields(params: HolsteinParams, n_chains: int, amplitude: float, seed: int = DEFAULT_SEED):
+    """Charge-ordered start for low temperatures: X(i, l) = -g/(M Omega^2) + amplitude (-1)^(x+y)
+    plus i.i.d. N(0, 1/(2 M Omega)) (the oscillator's zero-point spread); chain c uses seed + c."""
+    L, N = params.n_slices, params.n_sites
+    x0 = -params.g / (params.mass * params.omega ** 2)
+    stag = np.array([1.0 if ((i % params.nx) + (i // params.nx)) % 2 == 0 else -1.0 for i in range(N)])
+    sd = 1.0 / math.sqrt(2.0 * params.mass * params.omega)
+    X = np.empty((n_chains, L, N), dtype=np.float64)
+    for c in range(n_chains):
+        X[c] = x0 + amplitude * stag[None, :] + np.random.default_rng(seed + c).normal(0.0, sd, size=(L, N))
+    return X
+
+
 def random_fields(params: HolsteinParams, n_chains: int, seed: int, scale: float = 1.0,
                   offset: float = 0.0):
     """Generic seeded test fields: offset + scale * N(0, 1) of shape [chain][L][N]."""
