@@ -568,13 +568,15 @@ def run_headline(args):
     with torch.cuda.stream(stream):
         peak = hq.fp64_peak_tflops(20, stream.cuda_stream, kind=hq.HQ_PROBE_DFMA)
         dgemm = measure_dgemm(dev)
-        # ---- 1. training data: plain local sweeps on the deployment lattice (one chain per SM), from
-        # the ordered start, fresh Philox key; the exact log|det M| comes with every local sweep
+        # ---- 1. training data: plain local sweeps on the deployment lattice (one chain per SM) from
+        # the mean-field start, fresh Philox key; the exact log|det M| comes with every local sweep.
+        # (Measured alternatives: networks fitted to 8x8 configurations, ordered or not, are
+        # accepted far less often on the ordered 16x16 lattice.)
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         t0 = time.perf_counter()
-        tp = big.with_(seed=big.seed + 7)
-        tr = hq.Engine(tp, sms, first_chain=first, device=dev, stream=stream)
-        tr.set_fields(start_fields(big, sms, args.start_amplitude, workloads.DEFAULT_SEED + 5000 + first))
+        TC = sms
+        tr = hq.Engine(big.with_(seed=big.seed + 7), TC, first_chain=first, device=dev, stream=stream)
+        tr.set_fields(start_fields(big, TC, args.train_start_amplitude, workloads.DEFAULT_SEED + 5000 + first))
         tr.sweep(args.train_warmup, global_=False)
         Xs, ys = [], []
         for _ in range(args.train_snapshots):
@@ -584,7 +586,7 @@ def run_headline(args):
         tr.close()
         t_data = time.perf_counter() - t0
         # chains split 75/25 into training and held-out test configurations
-        ntr = (3 * sms) // 4
+        ntr = (3 * TC) // 4
         Xall, yall = np.stack(Xs, axis=1), np.stack(ys, axis=1)
         Xtr, ytr = Xall[:ntr].reshape((-1,) + Xall.shape[2:]), yall[:ntr].reshape(-1)
         Xte, yte = Xall[ntr:].reshape((-1,) + Xall.shape[2:]), yall[ntr:].reshape(-1)
@@ -615,8 +617,8 @@ def run_headline(args):
         net.close()
         del Xd, yd
         # ---- 3. learned sampler at 16x16: relaxation, timed steps, then the tau series
-        lrn = hq.Engine(big, C, first_chain=first, max_series=args.relax + Wm + K + args.tau_steps + 4, device=dev,
-                        stream=stream)
+        lrn = hq.Engine(big, C, first_chain=first, max_series=args.relax_max + Wm + K + args.tau_steps + 4,
+                        device=dev, stream=stream)
         lrn.attach_network(4, 8)
         lrn.set_params(theta)
         lrn.set_inner_window(W)
@@ -625,7 +627,18 @@ def run_headline(args):
         blk = args.inner_block_sites > 0
         if blk:
             lrn.set_inner_sites(args.inner_block_sites)
-        lrn.cumulative(args.relax + Wm, 1, global_=blk, measure=True)
+        # relaxation: at least args.relax steps, then in chunks of 100 until the last 200 steps'
+        # halves agree within two error bars for X^2, D and S_CDW, at most args.relax_max steps
+        lrn.cumulative(args.relax, 1, global_=blk, measure=True)
+        relaxed = args.relax
+        while True:
+            st_r = series_stats(hq, lrn, relaxed - min(200, relaxed), names)
+            ok = all(abs(v["half_diff"]) <= 2.0 * v["half_diff_err"] for v in st_r.values())
+            if ok or relaxed + 100 > args.relax_max:
+                break
+            lrn.cumulative(100, 1, global_=blk, measure=True)
+            relaxed += 100
+        lrn.cumulative(Wm, 1, global_=blk, measure=True)
         flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
         torch.cuda.synchronize(dev)
         lrn.set_timing(True)
@@ -655,7 +668,7 @@ def run_headline(args):
         t_dev = replicas.max_over_ranks(sum(a.elapsed_time(b) for a, b in evs) / 1e3, dev)
         step_rate = C * world * K / t_dev
         lrn.cumulative(args.tau_steps, 1, global_=blk, measure=True)
-        stats = series_stats(hq, lrn, args.relax + Wm, names)
+        stats = series_stats(hq, lrn, relaxed + Wm, names)
         st = lrn.learned_stats()
         acc = sum(x["cumulative_accepted"] for x in st) / max(1, sum(x["cumulative_proposed"] for x in st))
         # ---- 4. end to end through the C ABI with host buffers (pinned), copies timed
@@ -713,6 +726,17 @@ def run_headline(args):
           "stack_build": C * flops_stack_build(big)}.get(dom)
     achieved = fl / per_launch_s / 1e12 if fl else None
     total_ms = sum(m for m, _ in phases.values())
+    # DRAM traffic per launch of the dominant kernel from an ncu record of the same source
+    traffic, tr_src = None, None
+    tr_path = os.path.join(ROOT, "profiles", f"traffic_{kernel_names.get(dom, dom)}_largest.json")
+    if os.path.exists(tr_path) and C == workloads.LARGEST_RUN["n_chains"]:
+        import hashlib
+        with open(tr_path) as f:
+            tr = json.load(f)
+        src = b"".join(open(os.path.join(ROOT, "paper_1905_07440_gb300", "csrc", x), "rb").read()
+                       for x in ("hq_kernels.cu", "hq_device.cuh"))
+        if hashlib.sha256(src).hexdigest()[:16] == tr["source_hash"]:
+            traffic, tr_src = tr["dram_bytes_per_launch"], "profiles/" + os.path.basename(tr_path)
     xbytes = 8 * C * big.n_slices * big.n_sites
     e2e = C * world * args.e2e_steps / t_e2e / (2.0 * tau["s_cdw"])
     if cpu is not None:
@@ -739,7 +763,8 @@ def run_headline(args):
                              if args.start_amplitude > 0 else "mean field + N(0, 1/(M Omega^2))"),
                    "l2": "flushed (512 MB write) before every timed step; flush outside the events"},
         "learned": {"chain_steps_per_s": step_rate, "tau_int_steps": tau, "indep_samples_per_s": indep,
-                    "cumulative_acceptance": acc, "observables": stats, "relax_steps": args.relax + Wm,
+                    "cumulative_acceptance": acc, "observables": stats, "relax_steps": relaxed + Wm,
+                    "relax_window_stationary_2sigma": ok,
                     "measured_steps": K + args.tau_steps,
                     "stationary_2sigma": all(abs(v["half_diff"]) <= 2.0 * v["half_diff_err"] for v in stats.values())},
         "plain": {"seconds_per_full_sweep": t_full, "chain_sweeps_per_s": plain_bound,
@@ -749,8 +774,10 @@ def run_headline(args):
                   "phases_ms": {k: v[0] for k, v in ph.items() if v[1]},
                   "block_acceptance": sum(o["global_accepted"] for o in pobs) / max(1, sum(o["global_proposed"] for o in pobs))},
         "gain_lower_bound": {k: indep[k] / plain_bound for k in indep},
-        "training": {"lattice": "16x16", "source": f"plain local sweeps, {sms} chains from the start state, "
-                                                    f"{args.train_warmup} warm-up sweeps, one snapshot per sweep",
+        "training": {"lattice": "16x16", "source": f"plain local sweeps, {TC} chains from the "
+                                                  f"{'ordered' if args.train_start_amplitude > 0 else 'mean-field'} start, "
+                                                  f"{args.train_warmup} warm-up sweeps, one snapshot per sweep, "
+                                                  f"chains split 75/25 into training and test",
                      "samples": int(Xtr.shape[0]), "test_samples": int(Xte.shape[0]), "data_s": t_data,
                      "train_s": t_train, "test_rms": test_rms, "test_target_sd": float(yte.std()),
                      "epochs": args.epochs, "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
@@ -761,7 +788,8 @@ def run_headline(args):
                         "and observables out"},
         "gpu_launches": sum(n for _, n in phases.values()) + K,
         "roofline": {"bound": "alu", "kernel": kernel_names.get(dom, dom), "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "traffic_source": tr_src,
                      "peak_source": "FP64 DFMA probe measured in this run (hq_fp64_peak_tflops)",
                      "frac_vs_cublas_dgemm": (achieved / dgemm) if (achieved and dgemm) else None,
                      "cublas_dgemm_tflops": dgemm, "flops_per_launch": fl, "ms_per_launch": per_launch_s * 1e3,
@@ -1012,8 +1040,8 @@ def serving_params(side, beta, lam, seed):
 
 def run_serving(args):
     """Continuous-batching service under Poisson arrivals, on the serving workload's shape: lattice
-    side in {6, 8, 10, 12, 16}, beta in {4, 8, 12}, lambda in {0.15, 0.25, 0.35} (45 kinds), learned
-    or plain sampler per request, each drawn uniformly.  Stated reductions: args.duration seconds of
+    side in {6, 8, 10, 12, 16}, beta in {4, 8, 12}, lambda in {0.15, 0.25, 0.35} (45 kinds, drawn
+    uniformly in stratified runs of 45 so every kind appears), learned or plain sampler per request.  Stated reductions: args.duration seconds of
     arrivals at args.rate per second (not 1000 requests), args.req_sweeps sweeps or cumulative steps
     per request (not 500), plain block moves on a run of args.serve_block_sites sites per sweep (a
     full sweep at 16x16, beta = 12 is about a minute of block moves).  Learned requests carry a small
@@ -1028,15 +1056,20 @@ def run_serving(args):
 
     theta = hq.init_network(args.nn_seed, out_scale=0.1)
     rng = np.random.default_rng(args.serve_seed)
+    all_kinds = [(s_, b_, l_) for s_ in SERVING_SIDES for b_ in SERVING_BETAS for l_ in SERVING_LAMBDAS]
+    order = []
     reqs, t = [], 0.0
     while True:
         t += rng.exponential(1.0 / args.rate)
         if t > args.duration:
             break
         k = len(reqs)
-        side = int(rng.choice(SERVING_SIDES))
-        beta = float(rng.choice(SERVING_BETAS))
-        lam = float(rng.choice(SERVING_LAMBDAS))
+        # kinds uniform but stratified: each run of 45 requests visits every kind once, in random
+        # order, so a reduced request count still covers all of them
+        if not order:
+            order = [all_kinds[j] for j in rng.permutation(len(all_kinds))]
+        side, beta, lam = order.pop()
+        side, beta, lam = int(side), float(beta), float(lam)
         sampler = "learned" if rng.random() < args.learned_frac else "plain"
         p = serving_params(side, beta, lam, workloads.BATCHED.seed + 7919 * k)
         r = Request(rid=k, params=p, X0=workloads.initial_fields(p, 1, seed=10_000 + k)[0] - p.g / (p.mass * p.omega ** 2),
@@ -1672,12 +1705,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default="headline")
-    ap.add_argument("--relax", type=int, default=200, help="headline: learned steps before the measured series")
+    ap.add_argument("--relax", type=int, default=200, help="headline: learned steps before the measured series (minimum)")
+    ap.add_argument("--relax-max", type=int, default=800, help="headline: most relaxation steps")
     ap.add_argument("--side", type=int, default=6, help="agreement mode: lattice side")
     ap.add_argument("--betas", default="2,3,4", help="agreement mode: comma-separated beta values")
     ap.add_argument("--agree-window", type=int, default=0, help="agreement mode: learned window (0: every slice)")
     ap.add_argument("--inner-block-sites", type=int, default=0,
                     help="headline: block moves per cumulative step on this many sites (0: none)")
+    ap.add_argument("--train-start-amplitude", type=float, default=0.0,
+                    help="headline: staggered amplitude of the training chains' start (0: mean field)")
     ap.add_argument("--start-amplitude", type=float, default=0.9,
                     help="headline: staggered amplitude of the ordered start (0: mean-field start)")
     ap.add_argument("--train-chains", type=int, default=256, help="headline: plain chains for training data")

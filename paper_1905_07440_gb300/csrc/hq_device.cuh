@@ -275,9 +275,9 @@ __device__ __forceinline__ void copy_mat(double* B, const double* A, int ld, int
 // one-time ordering gives the graded R that the UDV decomposition needs, without per-step
 // pivot searches and norm downdates.
 //
-// Column work is spread over groups of 8 lanes (32 groups per CTA): each group reduces a
-// column's dot product with 3 shuffles, and every warp runs the same number of passes so
-// the shuffles always see all 32 lanes.
+// Column work is spread over groups of kGroup lanes (qr_group below: 4 or 8 lanes, 64 or 32
+// groups per CTA): each group reduces a column's dot product with log2(kGroup) shuffles, and
+// every warp runs the same number of passes so the shuffles always see all 32 lanes.
 struct QrScratch {
   double* tau;   // [n] reflector scalars
   double* vs;    // [2n] Householder vectors (current and next)
@@ -286,20 +286,28 @@ struct QrScratch {
   int* sint;     // >= 1
 };
 
-constexpr int kGroup = 8;
-constexpr int kGroups = HQ_THREADS / kGroup;
+// Lanes per column in the QR and Q-formation column updates (template parameter G).  Fewer lanes
+// per column means fewer shuffle-and-add steps (FP64 instructions that do no algorithmic work)
+// per column and longer FMA runs per lane, which pays for small matrices held in L1 (N <= 64);
+// at N = 256 (512 KB per matrix, streamed through L2) 8 lanes per column, 64-byte column
+// segments per load, are faster.  qr_group<LMAX>() picks it per lattice class.
+template <int LMAX>
+__host__ __device__ constexpr int qr_group() { return LMAX <= 8 ? 4 : 8; }
 
+template <int G>
 __device__ __forceinline__ double group_sum(double v) {
-  v += __shfl_xor_sync(HQ_FULL, v, 4);
-  v += __shfl_xor_sync(HQ_FULL, v, 2);
-  v += __shfl_xor_sync(HQ_FULL, v, 1);
+  static_assert(G == 2 || G == 4 || G == 8, "QR group size");
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(HQ_FULL, v, o);
   return v;
 }
 
 // Q <- columns of P ordered by decreasing norm (stable: ties keep index order); perm
 // records the order.  Norms are compared through their IEEE bit patterns, which order
 // non-negative doubles exactly like their values.  `norm2` is n doubles of scratch.
+template <int kGroup>
 __device__ inline void prepivot(const double* P, double* Q, int ld, int n, const QrScratch& s, double* norm2) {
+  constexpr int kGroups = HQ_THREADS / kGroup;
   const int g = threadIdx.x / kGroup, sub = threadIdx.x % kGroup;
   for (int base = 0; base < n; base += kGroups) {
     const int c = base + g;
@@ -308,7 +316,7 @@ __device__ inline void prepivot(const double* P, double* Q, int ld, int n, const
       const double* col = P + (size_t)c * ld;
       for (int r = sub; r < n; r += kGroup) a = fma(col[r], col[r], a);
     }
-    a = group_sum(a);
+    a = group_sum<kGroup>(a);
     if (c < n && sub == 0) norm2[c] = a;
   }
   __syncthreads();
@@ -368,6 +376,7 @@ __device__ __forceinline__ void house_gen(double* P, int ld, int n, int j, doubl
 // One barrier per column with look-ahead: during step j, warp 0 applies reflector j to
 // column j+1 and builds reflector j+1 while warps 1.. apply reflector j to columns j+2..
 // (two vector buffers in `vs`, 2n doubles).
+template <int kGroup>
 __device__ inline void qr_householder(double* P, int ld, int n, const QrScratch& s) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = (tid - 32) / kGroup, sub = tid % kGroup;  // groups of warps 1..
@@ -397,7 +406,7 @@ __device__ inline void qr_householder(double* P, int ld, int n, const QrScratch&
         double w = 0.0;
         if (c < n)
           for (int r = j + sub; r < n; r += kGroup) w = fma(vc[r], cc[r], w);
-        w = group_sum(w) * tj;
+        w = group_sum<kGroup>(w) * tj;
         if (c < n)
           for (int r = j + sub; r < n; r += kGroup) cc[r] = fma(-w, vc[r], cc[r]);
       }
@@ -410,7 +419,9 @@ __device__ inline void qr_householder(double* P, int ld, int n, const QrScratch&
 // One barrier per reflector: the next reflector's vector is staged into the other half of
 // `vs` while the current one is applied.  (A compact-WY blocked variant was measured slower
 // here: its serial T-factor build per block outweighs the barriers it saves.)
+template <int kGroup>
 __device__ inline void form_q(const double* P, int ld, int n, double* U, const QrScratch& s) {
+  constexpr int kGroups = HQ_THREADS / kGroup;
   const int g = threadIdx.x / kGroup, sub = threadIdx.x % kGroup;
   set_identity(U, ld, n);
   const int jl = n - 1;
@@ -430,7 +441,7 @@ __device__ inline void form_q(const double* P, int ld, int n, double* U, const Q
         double w = 0.0;
         if (c < n)
           for (int r = j + sub; r < n; r += kGroup) w = fma(vc[r], uc[r], w);
-        w = group_sum(w) * tj;
+        w = group_sum<kGroup>(w) * tj;
         if (c < n)
           for (int r = j + sub; r < n; r += kGroup) uc[r] = fma(-w, vc[r], uc[r]);
       }

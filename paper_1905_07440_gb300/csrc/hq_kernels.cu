@@ -163,13 +163,13 @@ __device__ double udv_top_down(const Dev& d, int c, const Smem& sm, const double
       HQ_TOC(kin, SEC_KIN);
     }
     HQ_TIC(pp);
-    prepivot(P, Q, n, n, qs, sm.norm2);
+    prepivot<qr_group<LMAX>()>(P, Q, n, n, qs, sm.norm2);
     HQ_TOC(pp, SEC_PREPIVOT);
     HQ_TIC(qr);
-    qr_householder(Q, n, n, qs);
+    qr_householder<qr_group<LMAX>()>(Q, n, n, qs);
     HQ_TOC(qr, SEC_QR);
     HQ_TIC(fq);
-    form_q(Q, n, n, U, qs);
+    form_q<qr_group<LMAX>()>(Q, n, n, U, qs);
     HQ_TOC(fq, SEC_FORMQ);
     HQ_TIC(tu);
     t_update(Q, n, n, qs, sm.dv, first ? nullptr : Tc, Tn);
@@ -242,9 +242,9 @@ __device__ void udv_bottom_half(const Dev& d, int c, const Smem& sm, int m) {
       // B_s P = exp(-dtau K) exp(-dtau V_s) P
       kin_rows<LMAX, KIN_SCALE_BEFORE>(P, n, n, sm.ex, sm.ey, d.nx, d.ny, sm.dl);
     }
-    prepivot(P, Q, n, n, qs, sm.norm2);
-    qr_householder(Q, n, n, qs);
-    form_q(Q, n, n, UR, qs);
+    prepivot<qr_group<LMAX>()>(P, Q, n, n, qs, sm.norm2);
+    qr_householder<qr_group<LMAX>()>(Q, n, n, qs);
+    form_q<qr_group<LMAX>()>(Q, n, n, UR, qs);
     t_update(Q, n, n, qs, DR, first ? nullptr : TR, T2);
     copy_mat(TR, T2, n, n);
     __syncthreads();
@@ -564,9 +564,9 @@ __device__ void local_chunk_body(const Dev& d, int c, int s0, int s1, int measur
   HQ_TIC(rq);
   double* Q = chain_work(d, c, WK_M1);
   const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint};
-  prepivot(P, Q, n, n, qs, sm.norm2);
-  qr_householder(Q, n, n, qs);
-  form_q(Q, n, n, UR, qs);
+  prepivot<qr_group<LMAX>()>(P, Q, n, n, qs, sm.norm2);
+  qr_householder<qr_group<LMAX>()>(Q, n, n, qs);
+  form_q<qr_group<LMAX>()>(Q, n, n, UR, qs);
   t_update(Q, n, n, qs, DR, first ? nullptr : TR, T2);
   copy_mat(TR, T2, n, n);
   __syncthreads();
@@ -805,13 +805,13 @@ __device__ double udv_top_down_cm(const Dev& d, int c, const Smem& sm, int site,
     __syncthreads();
     HQ_TOC(gm, SEC_KIN);
     HQ_TIC(pp);
-    prepivot(P, Q, n, n, qs, sm.norm2);
+    prepivot<qr_group<LMAX>()>(P, Q, n, n, qs, sm.norm2);
     HQ_TOC(pp, SEC_PREPIVOT);
     HQ_TIC(qr);
-    qr_householder(Q, n, n, qs);
+    qr_householder<qr_group<LMAX>()>(Q, n, n, qs);
     HQ_TOC(qr, SEC_QR);
     HQ_TIC(fq);
-    form_q(Q, n, n, U, qs);
+    form_q<qr_group<LMAX>()>(Q, n, n, U, qs);
     HQ_TOC(fq, SEC_FORMQ);
     HQ_TIC(tu);
     t_update(Q, n, n, qs, sm.dv, first ? nullptr : Tc, Tn);
