@@ -1602,6 +1602,31 @@ def run_sections(args):
     out["block_qr"] = roof(moves * q * (4.0 / 3.0) * n ** 3, cyc_block.get("qr", 0))
     out["block_form_q"] = roof(moves * q * (4.0 / 3.0) * n ** 3, cyc_block.get("form_q", 0))
     out["block_t_update"] = roof(moves * (q - 1) * float(n) ** 3, cyc_block.get("t_update", 0))
+    eng.close()
+    # the same sections in the largest lattice's full top-down product (16x16, beta = 16: the
+    # stack build, whose chunks are those of the two-half log-det), one chain per SM
+    pl = workloads.LARGEST
+    big = hq.Engine(pl, C)
+    Xl = workloads.ordered_fields(pl, C, args.start_amplitude, seed=workloads.DEFAULT_SEED)
+    big.set_fields(Xl)
+    torch.cuda.synchronize()
+    hq.section_cycles()
+    clocks = ClockSampler()
+    clocks.start()
+    big.set_fields(Xl)
+    torch.cuda.synchronize()
+    cyc_big = hq.section_cycles()
+    clk_big = clocks.stop()
+    big.close()
+    nb, chunks = pl.n_sites, chunk_sizes_top_down(pl)
+    slices = sum(chunks)
+    out["largest_stack_build"] = {
+        "workload": "16x16 beta=16 L=160 stack build, one chain per SM", "chains": C, "clocks": clk_big,
+        "kin": roof(C * slices * (2.0 * nb * nb * (pl.nx + pl.ny) + nb * nb), cyc_big.get("kin", 0)),
+        "qr": roof(C * len(chunks) * (4.0 / 3.0) * nb ** 3, cyc_big.get("qr", 0)),
+        "form_q": roof(C * len(chunks) * (4.0 / 3.0) * nb ** 3, cyc_big.get("form_q", 0)),
+        "t_update": roof(C * (len(chunks) - 1) * float(nb) ** 3, cyc_big.get("t_update", 0)),
+        "sections_cycles": cyc_big}
     print(json.dumps(out), flush=True)
     return 0
 
