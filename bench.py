@@ -1609,11 +1609,13 @@ def run_sections(args):
     big = hq.Engine(pl, C)
     Xl = workloads.ordered_fields(pl, C, args.start_amplitude, seed=workloads.DEFAULT_SEED)
     big.set_fields(Xl)
+    big.log_weight()  # the stack build runs on the first use of new fields
     torch.cuda.synchronize()
     hq.section_cycles()
     clocks = ClockSampler()
     clocks.start()
     big.set_fields(Xl)
+    big.log_weight()
     torch.cuda.synchronize()
     cyc_big = hq.section_cycles()
     clk_big = clocks.stop()

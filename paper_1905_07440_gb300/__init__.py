@@ -590,7 +590,9 @@ def section_cycles():
     """{section: cycles} from a -DHQ_SECTION_TIMING build (empty otherwise); clears them."""
     out = (ctypes.c_uint64 * len(SECTIONS))()
     n = load_library().hq_get_section_cycles(out, len(SECTIONS))
-    return {SECTIONS[i]: int(out[i]) for i in range(max(n, 0))}
+    if n < 0:
+        raise HQError(f"hq_get_section_cycles failed ({n})")
+    return {SECTIONS[i]: int(out[i]) for i in range(n)}
 
 
 HQ_PROBE_DFMA = 0

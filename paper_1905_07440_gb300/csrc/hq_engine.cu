@@ -924,7 +924,7 @@ constexpr int kNNParamsPad = (HQ_NN_PARAMS + 3) & ~3;
 constexpr int kCnnParamsPad = (HQ_CNN_PARAMS + 3) & ~3;
 
 struct NNLayout {
-  size_t wbf, master, grad, am, av, partials, fcache, fnew, X0, ld0, F0, F1, pc, Fb, loss, idx, counters, dFpath, G0;
+  size_t wbf, master, grad, am, av, partials, fcache, fnew, X0, ld0, F0, F1, pc, Fb, loss, idx, counters, dFpath, G0, xf, xb;
   size_t cwbf, cmaster, cgrad, cam, cav, cpartials, h1c, h2c, o3c, h1p, h2p, o3p, tr, cFb, cF;
   int train_ctas;
   size_t total;
@@ -954,6 +954,8 @@ NNLayout nn_layout(const hq::Dev& d, int max_batch, int max_samples) {
   l.counters = take(8 * C * hq::kNNCounters);
   l.dFpath = take(8 * C);
   l.G0 = take(8 * C * (size_t)d.n * d.n);
+  l.xf = take(4 * C * NL);
+  l.xb = take(4 * (size_t)max_batch * NL);
   // convolutional action
   const size_t PC = kCnnParamsPad, CH = hq::kCnnC;
   l.train_ctas = max_batch < hq::kCnnTrainCtas ? max_batch : hq::kCnnTrainCtas;
@@ -1024,6 +1026,8 @@ int hq_nn_attach(hq_engine* e, void* arena, size_t bytes, int max_batch, int max
   nn.counters = (long long*)(a + l.counters);
   nn.dFpath = (double*)(a + l.dFpath);
   nn.G0 = (double*)(a + l.G0);
+  nn.xf = (float*)(a + l.xf);
+  nn.xb = (float*)(a + l.xb);
   nn.x0 = -e->p.g / (e->p.mass * e->p.omega * e->p.omega);
   hq::CnnState& cn = e->cn;
   cn.on = 0;

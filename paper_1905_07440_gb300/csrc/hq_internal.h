@@ -114,6 +114,8 @@ struct NNState {
   long long* counters;  // [C][kNNCounters]
   double* dFpath;       // [C] sum of the accepted inner moves' network changes (cumulative step)
   double* G0;           // [C][N*N] G_0 of the step's starting fields (measured steps)
+  float* xf;            // [C][L N] network inputs (float)(X - x0) of the current fields
+  float* xb;            // [max batch][L N] network inputs of a training minibatch
   double x0;            // input shift -g/(M Omega^2)
 };
 

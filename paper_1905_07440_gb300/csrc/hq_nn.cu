@@ -37,6 +37,7 @@ struct NNSmem {
   uint2* frag;   // [TC_FRAGS] weight fragments of the tensor-core layers
   float* tcf;    // [TC_FLOATS] b1, b2, W3, b3
   float* f25;    // [32] f of the patches of a local move
+  float* pxf;    // [n] network inputs of the proposed values (local moves)
   int* nbr;      // [n][5] cross neighbours of every site: self, +x, -x, +y, -y
   double* red;   // [HQ_WARPS]
   double* pu2;   // [n] proposal uniforms (local)
@@ -50,7 +51,7 @@ struct NNSmem {
 
 __host__ __device__ inline size_t nn_smem_bytes(int n, bool with_cnn = false) {
   size_t b = sizeof(uint2) * TC_FRAGS + sizeof(double) * (HQ_WARPS + 3 * (size_t)n + NN_GROUPS + 8) +
-             sizeof(float) * (TC_FLOATS + 32) + sizeof(int) * 5 * (size_t)n;
+             sizeof(float) * (TC_FLOATS + 32 + (size_t)n) + sizeof(int) * 5 * (size_t)n;
   if (with_cnn) b += sizeof(float) * CN_WPAD + sizeof(int) * (4 + 3 * CN_WIN + 2 * (size_t)n);
   return b;
 }
@@ -68,6 +69,7 @@ __device__ inline NNSmem nn_carve(int n, char* base, bool with_cnn = false) {
   float* f = (float*)p;
   s.tcf = f; f += TC_FLOATS;
   s.f25 = f; f += 32;
+  s.pxf = f; f += n;
   s.nbr = (int*)f; f += 5 * n;
   s.cw = nullptr;
   if (with_cnn) {
@@ -80,22 +82,28 @@ __device__ inline NNSmem nn_carve(int n, char* base, bool with_cnn = false) {
   return s;
 }
 
-// Input k of the patch centred at (l, i): X at slice l + dl, cross site c (k = 5 (dl + 2) + c),
-// minus the mean field x0.  Optional change: points of site `cs` get + cdx on every slice (block
-// move), or, if cl >= 0, only the point (cl, cs) is set to cx (local move).
-__device__ __forceinline__ float patch_input(const Dev& d, const double* X, int l, int i, int k, double x0, int cs,
-                                             int cl, double cx, double cdx) {
-  const int n = d.n, L = d.L, x = i % d.nx, y = i / d.nx;
+// Position ll * n + j of input k of the patch centred at (l, i): slice ll = l + dl, site j =
+// cross point c of i (k = 5 (dl + 2) + c; c = 0 the site itself, then +x, -x, +y, -y).
+__device__ __forceinline__ int patch_pos(const Dev& d, int l, int i, int k) {
+  const int L = d.L, x = i % d.nx, y = i / d.nx;
   const int dl = k / 5 - 2, cidx = k % 5;
   const int cx_ = (cidx == 1) - (cidx == 2), cy_ = (cidx == 3) - (cidx == 4);
   const int ll = (l + dl + L) % L;
   const int j = (x + cx_ + d.nx) % d.nx + d.nx * ((y + cy_ + d.ny) % d.ny);
-  double v = X[(size_t)ll * n + j];
-  if (j == cs) {
-    if (cl < 0) v = v + cdx;
-    else if (ll == cl) v = cx;
-  }
-  return (float)(v - x0);
+  return ll * d.n + j;
+}
+
+// Network input of a field value: the value minus the mean field x0, rounded to float.  Every
+// kernel forms inputs through this one expression, so a value gives the same input bits
+// wherever it is formed.
+__device__ __forceinline__ float net_input(double v, double x0) { return (float)(v - x0); }
+
+// xf[k] = net_input(X[k]) for the L N values of a configuration (all threads; ends with a
+// barrier).  Each value enters 25 patches: converting it once keeps the FP64 pipe (which does
+// the subtraction and the rounding) out of the patch loops.
+__device__ inline void to_inputs(const double* X, double x0, float* xf, int NL) {
+  for (int k = threadIdx.x; k < NL; k += HQ_THREADS) xf[k] = net_input(X[k], x0);
+  __syncthreads();
 }
 
 // Warp sum in a fixed order (every lane gets the same bits).
@@ -107,8 +115,7 @@ __device__ __forceinline__ double warp_sum_fixed(double v) {
 
 // F of one configuration by the whole CTA: warp w takes the tiles of 16 patch rows w, w + 8, ...
 // (fixed order); the patch values go to fc when fc != nullptr.  Returns F in every thread.
-__device__ inline double fc_eval_all(const Dev& d, const NNSmem& s, const NNFrags& w, const double* X, double x0,
-                                     float* fc) {
+__device__ inline double fc_eval_all(const Dev& d, const NNSmem& s, const NNFrags& w, const float* xf, float* fc) {
   const int n = d.n, NL = d.n * d.L;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, g = lane >> 2, t = lane & 3;
   double part = 0.0;
@@ -116,7 +123,7 @@ __device__ inline double fc_eval_all(const Dev& d, const NNSmem& s, const NNFrag
     float f0, f1;
     nn_tile_f(w, [&](int row, int k) {
       const int r = base + row < NL ? base + row : NL - 1;
-      return patch_input(d, X, r / n, r % n, k, x0, -1, -1, 0.0, 0.0);
+      return xf[patch_pos(d, r / n, r % n, k)];
     }, f0, f1);
     if (t == 0) {
       if (base + g < NL) {
@@ -145,7 +152,9 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_eval_kernel(Dev d, NNState nn, 
   const int c = blockIdx.x, n = d.n, NL = d.n * d.L;
   const NNSmem s = nn_carve(n, nraw);
   const NNFrags w = nn_build_frags(nn.wbf, s.frag, s.tcf);
-  const double F = fc_eval_all(d, s, w, Xall + (size_t)c * NL, nn.x0, write_cache ? nn.fcache + (size_t)c * NL : nullptr);
+  float* xf = nn.xf + (size_t)c * NL;
+  to_inputs(Xall + (size_t)c * NL, nn.x0, xf, NL);
+  const double F = fc_eval_all(d, s, w, xf, write_cache ? nn.fcache + (size_t)c * NL : nullptr);
   if (threadIdx.x == 0) Fout[c] = F;
 }
 
@@ -178,6 +187,8 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
   const NNFrags w = nn_build_frags(nn.wbf, s.frag, s.tcf);  // (ends with a barrier)
   if (use_cnn) cn_load_weights(cn.wbf, s.cw);
   double* X = d.X + (size_t)c * NL;
+  float* xf = nn.xf + (size_t)c * NL;  // inputs of the current fields, kept with X below
+  to_inputs(X, nn.x0, xf, NL);
   float* fc = nn.fcache + (size_t)c * NL;
   float* fnew = nn.fnew + (size_t)c * 5 * L;
   float *h1c = nullptr, *h2c = nullptr, *o3c = nullptr, *h1p = nullptr, *h2p = nullptr, *o3p = nullptr;
@@ -224,7 +235,7 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
     if (local_part && do_local) {
       any_local = 0;
       if (fc_stale) {
-        fc_eval_all(d, s, w, X, nn.x0, fc);
+        fc_eval_all(d, s, w, xf, fc);
         fc_stale = false;
       }
       for (int sl0 = 0; sl0 < W; ++sl0) {
@@ -238,6 +249,7 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
           const double kin = (xp - xn) * (xp - xn) + (xn - xm) * (xn - xm) - (xp - xo) * (xp - xo) - (xo - xm) * (xo - xm);
           s.pu2[i] = u2;
           s.pxn[i] = xn;
+          s.pxf[i] = net_input(xn, nn.x0);
           s.pds[i] = kfac * kin + pfac * (xn * xn - xo * xo);
         }
         __syncthreads();
@@ -263,8 +275,7 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
               int ll = sl - (q / 5 - 2) + (k / 5 - 2);
               ll = ll < 0 ? ll + L : (ll >= L ? ll - L : ll);
               const int site = s.nbr[5 * csite(q) + k % 5];
-              const double v = (ll == sl && site == i) ? xn : X[(size_t)ll * n + site];
-              return (float)(v - nn.x0);
+              return (ll == sl && site == i) ? s.pxf[i] : xf[(size_t)ll * n + site];
             };
             float fv[4];
             nn_tile_f(w, [&](int row, int k) { return zv(row, k); }, fv[0], fv[1]);
@@ -281,6 +292,7 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
               acc = s.pu2[i] < prob;
               if (acc) {
                 X[(size_t)sl * n + i] = xn;
+                xf[(size_t)sl * n + i] = s.pxf[i];
                 path += dF;
                 any_local = 1;
               }
@@ -342,7 +354,8 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
             nn_tile_f(w, [&](int row, int k) {
               const int q = base + row < 5 * L ? base + row : 5 * L - 1;
               const int r = centre(q);
-              return patch_input(d, X, r / n, r % n, k, nn.x0, i, -1, 0.0, dx);
+              const int pos = patch_pos(d, r / n, r % n, k);
+              return pos % n == i ? net_input(X[pos] + dx, nn.x0) : xf[pos];
             }, f0, f1);
             if (t == 0) {
               const int q0 = base + g, q1 = q0 + 8;
@@ -371,7 +384,11 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_inner_kernel(Dev d, NNState nn,
         }
         __syncthreads();
         if (s.scal[0] != 0.0) {
-          for (int sl = threadIdx.x; sl < L; sl += HQ_THREADS) X[(size_t)sl * n + i] = X[(size_t)sl * n + i] + dx;
+          for (int sl = threadIdx.x; sl < L; sl += HQ_THREADS) {
+            const double v = X[(size_t)sl * n + i] + dx;
+            X[(size_t)sl * n + i] = v;
+            xf[(size_t)sl * n + i] = net_input(v, nn.x0);
+          }
           if (use_cnn) {
             cn_block_commit(d, s.win, h1c, h2c, o3c, h1p, h2p, o3p);
             fc_stale = true;
@@ -448,14 +465,17 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_batch_forward_kernel(Dev d, NNS
   const int a = blockIdx.x, n = d.n, NL = d.n * d.L;
   const NNSmem s = nn_carve(n, nraw);
   const NNFrags w = nn_build_frags(nn.wbf, s.frag, s.tcf);
-  const double F = fc_eval_all(d, s, w, Xs + (size_t)idx[a] * NL, nn.x0, nullptr);
+  float* xa = nn.xb + (size_t)a * NL;  // read again by the backward pass
+  to_inputs(Xs + (size_t)idx[a] * NL, nn.x0, xa, NL);
+  const double F = fc_eval_all(d, s, w, xa, nullptr);
   if (threadIdx.x == 0) Fb[a] = F;
 }
 
 // Backward pass on the tensor cores (see hq_nn_tc.cuh): CTA k takes the 128-row chunks k, k +
 // grid, ... of the minibatch's rows (row R = sample a * L N + patch), warp w rows 16 w .. 16 w + 15
-// of a chunk.  partials[k] receives the CTA's gradient (every entry written once).
-__global__ void __launch_bounds__(HQ_THREADS) nn_batch_backward_tc_kernel(Dev d, NNState nn, const double* Xs,
+// of a chunk.  Inputs come from nn.xb, written by the forward kernel.  partials[k] receives the
+// CTA's gradient (every entry written once).
+__global__ void __launch_bounds__(HQ_THREADS) nn_batch_backward_tc_kernel(Dev d, NNState nn,
                                                                           const double* ys, const int* idx, int B,
                                                                           const double* Fb, float* partials) {
   extern __shared__ __align__(16) char nraw[];
@@ -518,9 +538,9 @@ __global__ void __launch_bounds__(HQ_THREADS) nn_batch_backward_tc_kernel(Dev d,
         const int k = 16 * st + 2 * t + 8 * (q >> 1);
         int a, pr;
         rowpos(row, a, pr);
-        const double* X = Xs + (size_t)idx[a] * NL;
-        const float v0 = k < TC_IN ? patch_input(d, X, pr / n, pr % n, k, nn.x0, -1, -1, 0.0, 0.0) : 0.f;
-        const float v1 = k + 1 < TC_IN ? patch_input(d, X, pr / n, pr % n, k + 1, nn.x0, -1, -1, 0.0, 0.0) : 0.f;
+        const float* xa = nn.xb + (size_t)a * NL;  // the minibatch inputs of the forward kernel
+        const float v0 = k < TC_IN ? xa[patch_pos(d, pr / n, pr % n, k)] : 0.f;
+        const float v1 = k + 1 < TC_IN ? xa[patch_pos(d, pr / n, pr % n, k + 1)] : 0.f;
         split2(v0, v1, ahi[q], alo[q]);
         // z^T staging (rows k >= 25 are zero)
         zh[k * TR_LD + 16 * warp + row] = (uint16_t)(ahi[q] & 0xffffu);
@@ -796,7 +816,7 @@ cudaError_t nn_launch_batch(const Dev& d, const NNState& nn, const double* Xs, c
       sms = kNNTrainCtas;
   }
   const int grid = sms < kNNTrainCtas ? sms : kNNTrainCtas;
-  nn_batch_backward_tc_kernel<<<grid, HQ_THREADS, sbk, s>>>(d, nn, Xs, ys, idx, B, nn.Fb, nn.partials);
+  nn_batch_backward_tc_kernel<<<grid, HQ_THREADS, sbk, s>>>(d, nn, ys, idx, B, nn.Fb, nn.partials);
   nn_adam_kernel<<<(NN_NP + 255) / 256, 256, 0, s>>>(nn, nn.partials, grid, lr, t_step);
   return cudaGetLastError();
 }
