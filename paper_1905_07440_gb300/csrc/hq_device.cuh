@@ -275,6 +275,10 @@ __device__ __forceinline__ void copy_mat(double* B, const double* A, int ld, int
 // one-time ordering gives the graded R that the UDV decomposition needs, without per-step
 // pivot searches and norm downdates.
 //
+constexpr int kQb = 16;         // panel width of the blocked QR and Q formation
+constexpr int kQbLd = kQb + 2;  // row stride (doubles) of a panel's copy in shared memory: rows
+                                // stay 16-byte aligned and consecutive rows start 4 banks apart
+
 // Column work is spread over groups of kGroup lanes (qr_group below: 4 or 8 lanes, 64 or 32
 // groups per CTA): each group reduces a column's dot product with log2(kGroup) shuffles, and
 // every warp runs the same number of passes so the shuffles always see all 32 lanes.
@@ -284,6 +288,8 @@ struct QrScratch {
   double* rinv;  // [n] 1 / D
   int* perm;     // [n] perm[j] = original column placed at position j
   int* sint;     // >= 1
+  double* wv;    // [n][kQbLd] panel of reflector vectors (blocked variants only)
+  double* ws;    // [kQb][kQb] strict upper part of V^T V (blocked variants only)
 };
 
 // Lanes per column in the QR and Q-formation column updates (template parameter G).  Fewer lanes
@@ -448,6 +454,190 @@ __device__ inline void form_q(const double* P, int ld, int n, double* U, const Q
     }
     __syncthreads();
   }
+}
+
+// ------------------------------------------------ blocked QR and Q formation (16-wide class)
+// At N up to 256 a column-by-column QR or Q formation sweeps a matrix of up to 512 KB once per
+// column, and those sweeps run out of L1 and L2.  The blocked variants take the columns in panels
+// of kQb.  A panel is factored column by column (qr_panel: the look-ahead scheme of
+// qr_householder restricted to the panel), and its kQb reflectors then reach the rest of the
+// matrix at once in the compact WY form H_j0 ... H_j1-1 = I - V T V^T (Schreiber and Van Loan,
+// SIAM J. Sci. Stat. Comput. 10 (1989)).  T is never formed.  Its inverse is diag(1/tau) + S,
+// with S the strict upper part of V^T V (the "UT transform": Joffrain, Low, Quintana-Orti, van
+// de Geijn and Van Zee, ACM TOMS 32 (2006)), so each column's small triangular product becomes
+// a substitution without divisions.  The factorisation is the unblocked one up to rounding:
+// R above the diagonal, the unit-lower reflector vectors below it, and tau.  So the T update
+// and every other reader of the QR see the same layout.
+
+__host__ __device__ constexpr bool qr_blocked_class(int lmax) { return lmax > 8; }
+
+// Panel factorisation of columns j0 .. j1 - 1 (rows j .. n - 1 for column j).  Columns from
+// j1 on are not touched.
+template <int kGroup>
+__device__ inline void qr_panel(double* P, int ld, int n, int j0, int j1, const QrScratch& s) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = (tid - 32) / kGroup, sub = tid % kGroup;
+  constexpr int kTailGroups = (HQ_THREADS - 32) / kGroup;
+  if (warp == 0) house_gen(P, ld, n, j0, s.vs + (j0 & 1) * n, s.tau);
+  __syncthreads();
+  for (int j = j0; j < j1; ++j) {
+    const double* vc = s.vs + (j & 1) * n;
+    double* vn = s.vs + ((j + 1) & 1) * n;
+    const double tj = s.tau[j];
+    if (warp == 0) {
+      if (j + 1 < j1) {
+        double* cc = P + (size_t)(j + 1) * ld;
+        if (tj != 0.0) {
+          double w = 0.0;
+          for (int r = j + lane; r < n; r += 32) w = fma(vc[r], cc[r], w);
+          w = warp_sum(w) * tj;
+          for (int r = j + lane; r < n; r += 32) cc[r] = fma(-w, vc[r], cc[r]);
+          __syncwarp();
+        }
+        house_gen(P, ld, n, j + 1, vn, s.tau);
+      }
+    } else if (tj != 0.0) {
+      for (int base = j + 2; base < j1; base += kTailGroups) {
+        const int c = base + g;
+        double* cc = P + (size_t)c * ld;
+        double w = 0.0;
+        if (c < j1)
+          for (int r = j + sub; r < n; r += kGroup) w = fma(vc[r], cc[r], w);
+        w = group_sum<kGroup>(w) * tj;
+        if (c < j1)
+          for (int r = j + sub; r < n; r += kGroup) cc[r] = fma(-w, vc[r], cc[r]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// The reflectors of columns j0 .. j1 - 1 of P (j1 - j0 <= kQb; unit leading entries implied,
+// tau[j0 ..]) applied at once to columns c0 .. n - 1, rows j0 .. n - 1, of A (A may be P when
+// c0 >= j1):
+//   kTrans:  A <- (H_j0 ... H_j1-1)^T A = A - V T^T (V^T A)   (trailing update of the QR)
+//   !kTrans: A <- H_j0 ... H_j1-1 A     = A - V T (V^T A)     (Q formation)
+// With W = V^T A, Z = T^T W is the forward substitution Z_k = tau_k (W_k - sum_{m<k} S_mk Z_m)
+// and Z = T W the backward one Z_k = tau_k (W_k - sum_{m>k} S_km Z_m).  A column of A belongs to
+// a group of 4 lanes (64 groups, more columns in further passes): each lane takes every fourth
+// row, keeps kQb partial sums, and the group adds them with two shuffle steps.  V is copied to
+// shared memory (s.wv, zero-padded to kQb columns) and read as 16-byte pairs.
+template <bool kTrans>
+__device__ __noinline__ void wy_apply(const double* P, int ld, int n, int j0, int j1, const QrScratch& s, double* A,
+                                int c0) {
+  const int kb = j1 - j0, nr = n - j0;
+  double* V = s.wv;
+  double* S = s.ws;
+  for (int idx = threadIdx.x; idx < nr * kQb; idx += HQ_THREADS) {
+    const int rr = idx / kQb, k = idx % kQb;
+    double v = 0.0;
+    if (k < kb) v = rr > k ? P[(size_t)(j0 + k) * ld + j0 + rr] : (rr == k ? 1.0 : 0.0);
+    V[rr * kQbLd + k] = v;
+  }
+  __syncthreads();
+  // S_ab = v_a . v_b for a < b: pair q = b (b - 1) / 2 + a per group of 8 lanes and pass
+  {
+    constexpr int kPairs = kQb * (kQb - 1) / 2;
+    const int g8 = threadIdx.x >> 3, sub8 = threadIdx.x & 7;
+    for (int base = 0; base < kPairs; base += HQ_THREADS / 8) {
+      const int q = base + g8;
+      int b = 1;
+      while (b * (b + 1) / 2 <= q) ++b;
+      const int a = q - b * (b - 1) / 2;
+      double acc = 0.0;
+      if (q < kPairs && b < kb)
+        for (int rr = b + sub8; rr < nr; rr += 8) acc = fma(V[rr * kQbLd + a], V[rr * kQbLd + b], acc);
+      acc = group_sum<8>(acc);
+      if (q < kPairs && sub8 == 0) S[a * kQb + b] = acc;
+    }
+  }
+  __syncthreads();
+  const int g4 = threadIdx.x >> 2, sub = threadIdx.x & 3;
+  const int ncols = n - c0;
+  for (int base = 0; base < ncols; base += HQ_THREADS / 4) {
+    const bool on = base + g4 < ncols;
+    double* ac = A + (size_t)(c0 + (on ? base + g4 : 0)) * ld + j0;
+    double w[kQb];
+#pragma unroll
+    for (int k = 0; k < kQb; ++k) w[k] = 0.0;
+    if (on)
+      for (int rr = sub; rr < nr; rr += 4) {
+        const double a = ac[rr];
+        const double2* vr = reinterpret_cast<const double2*>(V + rr * kQbLd);
+#pragma unroll
+        for (int k2 = 0; k2 < kQb / 2; ++k2) {
+          const double2 v = vr[k2];
+          w[2 * k2] = fma(v.x, a, w[2 * k2]);
+          w[2 * k2 + 1] = fma(v.y, a, w[2 * k2 + 1]);
+        }
+      }
+#pragma unroll
+    for (int k = 0; k < kQb; ++k) w[k] = group_sum<4>(w[k]);
+    if (kTrans) {
+#pragma unroll
+      for (int k = 0; k < kQb; ++k) {
+        double z = w[k];
+#pragma unroll
+        for (int m = 0; m < k; ++m) z = fma(-S[m * kQb + k], w[m], z);
+        w[k] = (k < kb ? s.tau[j0 + k] : 0.0) * z;
+      }
+    } else {
+#pragma unroll
+      for (int k = kQb - 1; k >= 0; --k) {
+        double z = w[k];
+#pragma unroll
+        for (int m = k + 1; m < kQb; ++m) z = fma(-S[k * kQb + m], w[m], z);
+        w[k] = (k < kb ? s.tau[j0 + k] : 0.0) * z;
+      }
+    }
+    if (on)
+      for (int rr = sub; rr < nr; rr += 4) {
+        const double2* vr = reinterpret_cast<const double2*>(V + rr * kQbLd);
+        double a = ac[rr];
+#pragma unroll
+        for (int k2 = 0; k2 < kQb / 2; ++k2) {
+          const double2 v = vr[k2];
+          a = fma(-v.x, w[2 * k2], a);
+          a = fma(-v.y, w[2 * k2 + 1], a);
+        }
+        ac[rr] = a;
+      }
+  }
+  __syncthreads();
+}
+
+template <int kGroup>
+__device__ inline void qr_blocked(double* P, int ld, int n, const QrScratch& s) {
+  for (int j0 = 0; j0 < n; j0 += kQb) {
+    const int j1 = j0 + kQb < n ? j0 + kQb : n;
+    qr_panel<kGroup>(P, ld, n, j0, j1, s);
+    if (j1 < n) wy_apply<true>(P, ld, n, j0, j1, s, P, j1);
+  }
+}
+
+// U <- H_0 ... H_{n-1}: the panels' block reflectors applied to the identity, last panel first
+// (columns below a panel's first are still unit vectors there and need no update).
+__device__ inline void form_q_blocked(const double* P, int ld, int n, double* U, const QrScratch& s) {
+  set_identity(U, ld, n);
+  __syncthreads();
+  for (int j0 = ((n - 1) / kQb) * kQb; j0 >= 0; j0 -= kQb) {
+    const int j1 = j0 + kQb < n ? j0 + kQb : n;
+    wy_apply<false>(P, ld, n, j0, j1, s, U, j0);
+  }
+}
+
+// The QR and the Q formation of a lattice class: blocked for the 16-wide class, column by
+// column (with qr_group<LMAX>() lanes per column) below it.
+template <int LMAX>
+__device__ inline void qr_factor(double* P, int ld, int n, const QrScratch& s) {
+  if constexpr (qr_blocked_class(LMAX)) qr_blocked<qr_group<LMAX>()>(P, ld, n, s);
+  else qr_householder<qr_group<LMAX>()>(P, ld, n, s);
+}
+
+template <int LMAX>
+__device__ inline void qr_form_q(const double* P, int ld, int n, double* U, const QrScratch& s) {
+  if constexpr (qr_blocked_class(LMAX)) form_q_blocked(P, ld, n, U, s);
+  else form_q<qr_group<LMAX>()>(P, ld, n, U, s);
 }
 
 // D[j] = |R_jj| and Tout = T' Tprev with T'(j, perm[c]) = R(j, c) / D[j] for c >= j

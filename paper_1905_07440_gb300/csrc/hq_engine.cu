@@ -1459,7 +1459,10 @@ int hq_group_create(hq_engine* const* engines, int n_engines, void* device_arena
     devs[e] = d;
     const int lm = hq::lmax_class(d.nx, d.ny);
     g->lmax = lm > g->lmax ? lm : g->lmax;
-    const size_t sb = hq::smem_bytes(d);
+  }
+  // every engine's chains run in the group's class, whose QR may need more shared memory
+  for (int e = 0; e < n_engines; ++e) {
+    const size_t sb = hq::smem_bytes_class(engines[e]->d, g->lmax);
     g->sb = sb > g->sb ? sb : g->sb;
   }
   // task table: every chain, longest estimated sweep first (longest-processing-time order)

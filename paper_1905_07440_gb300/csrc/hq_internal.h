@@ -146,6 +146,8 @@ struct CnnState {
 };
 
 size_t smem_bytes(const Dev& d);
+// shared memory of a chain of d in a kernel of class lmax (group launches: the group's class)
+size_t smem_bytes_class(const Dev& d, int lmax);
 
 // Raise a kernel's dynamic shared memory limit to the device maximum (once per kernel and
 // device) when it needs more than the default 48 KB.

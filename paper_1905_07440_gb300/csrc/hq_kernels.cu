@@ -37,18 +37,37 @@ struct Smem {
   double *ex, *exi, *ey, *eyi;
   double *dl, *u2, *xn, *dlt, *es, *dcorr, *tau, *norm2, *rinv, *vs, *dv, *rd;
   double *red, *scal;
+  double *wv, *ws;  // blocked QR scratch (16-wide class only, else nullptr)
   int *perm, *piv, *sint;
 };
 
 static constexpr int kSmemVecs = 13;  // vs takes two
 
-__host__ __device__ inline size_t smem_layout_bytes(int nx, int ny, int n) {
-  return (size_t)(2 * nx * nx + 2 * ny * ny + kSmemVecs * n + 32 + 16) * sizeof(double) +
-         (size_t)(2 * n + 8) * sizeof(int);
+// Kernel template class of a lattice: the largest side rounded up to 2, 4, 8 or 16.
+static inline int lmax_of(int nx, int ny) {
+  const int m = nx > ny ? nx : ny;
+  return m <= 2 ? 2 : m <= 4 ? 4 : m <= 8 ? 8 : 16;
 }
 
-size_t smem_bytes(const Dev& d) { return smem_layout_bytes(d.nx, d.ny, d.n); }
+// doubles of the blocked QR scratch: the panel copy (n rows of kQbLd) and S (kQb x kQb)
+__host__ __device__ inline size_t smem_qr_doubles(bool blocked, int n) {
+  return blocked ? (size_t)n * kQbLd + kQb * kQb : 0;
+}
 
+// Shared memory of one chain's CTA in a kernel instantiated for class LMAX (`blocked` =
+// qr_blocked_class(LMAX)): the layout of carve<LMAX>.
+__host__ __device__ inline size_t smem_layout_bytes(int nx, int ny, int n, bool blocked) {
+  return (size_t)(2 * nx * nx + 2 * ny * ny + kSmemVecs * n + 32 + 16) * sizeof(double) +
+         smem_qr_doubles(blocked, n) * sizeof(double) + (size_t)(2 * n + 8) * sizeof(int);
+}
+
+size_t smem_bytes(const Dev& d) {
+  return smem_layout_bytes(d.nx, d.ny, d.n, qr_blocked_class(lmax_of(d.nx, d.ny)));
+}
+
+size_t smem_bytes_class(const Dev& d, int lmax) { return smem_layout_bytes(d.nx, d.ny, d.n, qr_blocked_class(lmax)); }
+
+template <int LMAX>
 __device__ inline Smem carve(const Dev& d, double* base) {
   Smem s;
   double* p = base;
@@ -71,6 +90,13 @@ __device__ inline Smem carve(const Dev& d, double* base) {
   s.rd = p; p += n;
   s.red = p; p += 32;
   s.scal = p; p += 16;
+  // 16-byte aligned: every count above is even (nx, ny and n are even)
+  s.wv = nullptr;
+  s.ws = nullptr;
+  if (qr_blocked_class(LMAX)) {
+    s.wv = p; p += (size_t)n * kQbLd;
+    s.ws = p; p += kQb * kQb;
+  }
   int* q = reinterpret_cast<int*>(p);
   s.perm = q; q += n;
   s.piv = q; q += n;
@@ -142,7 +168,7 @@ __device__ double udv_top_down(const Dev& d, int c, const Smem& sm, const double
   double* Tc = chain_work(d, c, WK_T);
   double* Tn = chain_work(d, c, WK_T2);
   double* Q = chain_work(d, c, WK_M1);
-  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint};
+  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint, sm.wv, sm.ws};
   int hi = L, lo = ((L - 1) / nw) * nw;
   bool first = true;
   while (true) {
@@ -166,10 +192,10 @@ __device__ double udv_top_down(const Dev& d, int c, const Smem& sm, const double
     prepivot<qr_group<LMAX>()>(P, Q, n, n, qs, sm.norm2);
     HQ_TOC(pp, SEC_PREPIVOT);
     HQ_TIC(qr);
-    qr_householder<qr_group<LMAX>()>(Q, n, n, qs);
+    qr_factor<LMAX>(Q, n, n, qs);
     HQ_TOC(qr, SEC_QR);
     HQ_TIC(fq);
-    form_q<qr_group<LMAX>()>(Q, n, n, U, qs);
+    qr_form_q<LMAX>(Q, n, n, U, qs);
     HQ_TOC(fq, SEC_FORMQ);
     HQ_TIC(tu);
     t_update(Q, n, n, qs, sm.dv, first ? nullptr : Tc, Tn);
@@ -194,7 +220,7 @@ __device__ double udv_top_down(const Dev& d, int c, const Smem& sm, const double
 template <int LMAX>
 __device__ void stack_build_body(const Dev& d, int c, double* smraw) {
   if (!d.active[c]) return;
-  const Smem sm = carve(d, smraw);
+  const Smem sm = carve<LMAX>(d, smraw);
   load_kinetic(d, sm);
   const double* X = d.X + (size_t)c * d.L * d.n;
   double* G = d.G + (size_t)c * d.n * d.n;
@@ -207,7 +233,7 @@ __device__ void stack_build_body(const Dev& d, int c, double* smraw) {
 
 template <int LMAX>
 __global__ void __launch_bounds__(HQ_THREADS) stack_build_kernel(Dev d) {
-  extern __shared__ double smraw[];
+  extern __shared__ __align__(16) double smraw[];
   stack_build_body<LMAX>(d, blockIdx.x, smraw);
 }
 
@@ -229,7 +255,7 @@ __device__ void udv_bottom_half(const Dev& d, int c, const Smem& sm, int m) {
   double* P = chain_work(d, c, WK_M2);
   double* Q = chain_work(d, c, WK_M3);
   double* T2 = d.G + (size_t)c * n * n;
-  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint};
+  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint, sm.wv, sm.ws};
   for (int s0 = 0; s0 < m; s0 += nw) {
     const int s1 = s0 + nw < m ? s0 + nw : m;
     const bool first = (s0 == 0);
@@ -243,8 +269,8 @@ __device__ void udv_bottom_half(const Dev& d, int c, const Smem& sm, int m) {
       kin_rows<LMAX, KIN_SCALE_BEFORE>(P, n, n, sm.ex, sm.ey, d.nx, d.ny, sm.dl);
     }
     prepivot<qr_group<LMAX>()>(P, Q, n, n, qs, sm.norm2);
-    qr_householder<qr_group<LMAX>()>(Q, n, n, qs);
-    form_q<qr_group<LMAX>()>(Q, n, n, UR, qs);
+    qr_factor<LMAX>(Q, n, n, qs);
+    qr_form_q<LMAX>(Q, n, n, UR, qs);
     t_update(Q, n, n, qs, DR, first ? nullptr : TR, T2);
     copy_mat(TR, T2, n, n);
     __syncthreads();
@@ -253,11 +279,11 @@ __device__ void udv_bottom_half(const Dev& d, int c, const Smem& sm, int m) {
 
 template <int LMAX>
 __global__ void __launch_bounds__(HQ_THREADS) split_halves_kernel(Dev d, int m) {
-  extern __shared__ double smraw[];
+  extern __shared__ __align__(16) double smraw[];
   const int C = d.n_chains;
   const int c = blockIdx.x % C;
   if (!d.active[c]) return;
-  const Smem sm = carve(d, smraw);
+  const Smem sm = carve<LMAX>(d, smraw);
   load_kinetic(d, sm);
   if (blockIdx.x < C) {
     udv_top_down<LMAX>(d, c, sm, d.X + (size_t)c * d.L * d.n, -1, 0.0, true, nullptr, m);
@@ -270,10 +296,10 @@ __device__ double green_two_sided(const Dev& d, int c, const Smem& sm, int l, do
 
 template <int LMAX>
 __global__ void __launch_bounds__(HQ_THREADS) split_join_kernel(Dev d, int m) {
-  extern __shared__ double smraw[];
+  extern __shared__ __align__(16) double smraw[];
   const int c = blockIdx.x;
   if (!d.active[c]) return;
-  const Smem sm = carve(d, smraw);
+  const Smem sm = carve<LMAX>(d, smraw);
   const double ld = green_two_sided(d, c, sm, m, d.G + (size_t)c * d.n * d.n);
   if (threadIdx.x == 0) {
     d.logdet[c] = ld;
@@ -417,7 +443,7 @@ template <int LMAX>
 __device__ void local_chunk_body(const Dev& d, int c, int s0, int s1, int measure, double* smraw) {
   if (!d.active[c]) return;
   const int n = d.n, L = d.L, k = d.k;
-  const Smem sm = carve(d, smraw);
+  const Smem sm = carve<LMAX>(d, smraw);
   load_kinetic(d, sm);
   double* X = d.X + (size_t)c * L * n;
   double* G = d.G + (size_t)c * n * n;
@@ -563,10 +589,10 @@ __device__ void local_chunk_body(const Dev& d, int c, int s0, int s1, int measur
   HQ_TOC(rp, SEC_RESTAB_PROD);
   HQ_TIC(rq);
   double* Q = chain_work(d, c, WK_M1);
-  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint};
+  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint, sm.wv, sm.ws};
   prepivot<qr_group<LMAX>()>(P, Q, n, n, qs, sm.norm2);
-  qr_householder<qr_group<LMAX>()>(Q, n, n, qs);
-  form_q<qr_group<LMAX>()>(Q, n, n, UR, qs);
+  qr_factor<LMAX>(Q, n, n, qs);
+  qr_form_q<LMAX>(Q, n, n, UR, qs);
   t_update(Q, n, n, qs, DR, first ? nullptr : TR, T2);
   copy_mat(TR, T2, n, n);
   __syncthreads();
@@ -604,7 +630,7 @@ __device__ void local_chunk_body(const Dev& d, int c, int s0, int s1, int measur
 // shared by two.  sched = [counter, abort, ..., progress[C] at kSchedHeader], zeroed first.
 template <int LMAX>
 __global__ void __launch_bounds__(HQ_THREADS) local_phase_kernel(Dev d, int measure) {
-  extern __shared__ double smraw[];
+  extern __shared__ __align__(16) double smraw[];
   __shared__ int s_task;
   const int C = d.n_chains, Q = (d.L + d.n_wrap - 1) / d.n_wrap, ntask = Q * C;
   int* counter = d.sched;
@@ -754,7 +780,7 @@ __device__ double udv_top_down_cm(const Dev& d, int c, const Smem& sm, int site,
   double* Tn = chain_work(d, c, WK_T2);
   double* Q = chain_work(d, c, WK_M1);
   double* Y = chain_work(d, c, WK_M2);
-  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint};
+  const QrScratch qs{sm.tau, sm.vs, sm.rinv, sm.perm, sm.sint, sm.wv, sm.ws};
   const double delta = expm1(-d.dtau * d.g * dx);
   HQ_TIC(cv);
   for (int s = threadIdx.x; s < L; s += HQ_THREADS) xs[s] = exp(-d.dtau * (d.g * (X[(size_t)s * n + site] + dx) - d.mu));
@@ -808,10 +834,10 @@ __device__ double udv_top_down_cm(const Dev& d, int c, const Smem& sm, int site,
     prepivot<qr_group<LMAX>()>(P, Q, n, n, qs, sm.norm2);
     HQ_TOC(pp, SEC_PREPIVOT);
     HQ_TIC(qr);
-    qr_householder<qr_group<LMAX>()>(Q, n, n, qs);
+    qr_factor<LMAX>(Q, n, n, qs);
     HQ_TOC(qr, SEC_QR);
     HQ_TIC(fq);
-    form_q<qr_group<LMAX>()>(Q, n, n, U, qs);
+    qr_form_q<LMAX>(Q, n, n, U, qs);
     HQ_TOC(fq, SEC_FORMQ);
     HQ_TIC(tu);
     t_update(Q, n, n, qs, sm.dv, first ? nullptr : Tc, Tn);
@@ -904,9 +930,9 @@ __device__ void block_move(const Dev& d, const Smem& sm, int c, int site) {
 // kSchedHeader], zeroed before the launch.
 template <int LMAX>
 __global__ void __launch_bounds__(HQ_THREADS, 2) global_phase_kernel(Dev d) {
-  extern __shared__ double smraw[];
+  extern __shared__ __align__(16) double smraw[];
   __shared__ int s_task;
-  const Smem sm = carve(d, smraw);
+  const Smem sm = carve<LMAX>(d, smraw);
   load_kinetic(d, sm);
   const int C = d.n_chains, ntask = (block_move_count(d) + (d.use_cm ? 1 : 0)) * C;
   int* counter = d.sched;
@@ -1019,7 +1045,7 @@ __global__ void __launch_bounds__(HQ_THREADS) sweep_end_kernel(Dev d, int measur
 // propagator's arithmetic does not depend on it) and take the largest shared-memory carve.
 template <int LMAX>
 __global__ void __launch_bounds__(HQ_THREADS) group_sweep_kernel(GroupDev g, int flags, int stack) {
-  extern __shared__ double smraw[];
+  extern __shared__ __align__(16) double smraw[];
   __shared__ int s_task;
   __shared__ Dev sd;
   const bool do_local = flags & HQ_LOCAL, do_global = flags & HQ_GLOBAL, meas = flags & HQ_MEASURE;
@@ -1036,7 +1062,7 @@ __global__ void __launch_bounds__(HQ_THREADS) group_sweep_kernel(GroupDev g, int
     if (e != cur) {
       if (threadIdx.x == 0) sd = g.devs[e];
       __syncthreads();
-      sm = carve(sd, smraw);
+      sm = carve<LMAX>(sd, smraw);
       load_kinetic(sd, sm);
       cur = e;
     }
@@ -1059,8 +1085,8 @@ __global__ void __launch_bounds__(HQ_THREADS) group_sweep_kernel(GroupDev g, int
 // Electronic observables from G_0 of every chain (after a stack build).
 template <int LMAX>
 __global__ void __launch_bounds__(HQ_THREADS) measure_g0_kernel(Dev d) {
-  extern __shared__ double smraw[];
-  const Smem sm = carve(d, smraw);
+  extern __shared__ __align__(16) double smraw[];
+  const Smem sm = carve<LMAX>(d, smraw);
   const int c = blockIdx.x;
   if (!d.active[c]) return;
   measure_green(d, c, sm, d.G + (size_t)c * d.n * d.n);
@@ -1132,11 +1158,6 @@ __global__ void proposals_kernel(uint32_t key0, uint32_t key1, uint32_t chain, u
 
 // ---------------------------------------------------------------- launchers
 
-static inline int lmax_of(int nx, int ny) {
-  const int m = nx > ny ? nx : ny;
-  return m <= 2 ? 2 : m <= 4 ? 4 : m <= 8 ? 8 : 16;
-}
-
 // Dynamic shared memory above the default 48 KB needs an opt-in per kernel.  The opt-in is
 // set once per kernel and device, to the device maximum: engines of different shapes share
 // kernel instantiations and run concurrently on their own streams, and changing the
@@ -1149,11 +1170,16 @@ cudaError_t opt_in_smem(const void* kernel, size_t bytes) {
   cudaError_t st = cudaGetDevice(&dev);
   if (st == cudaSuccess) st = cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (st != cudaSuccess) return st;
-  if (bytes > (size_t)cap) return cudaErrorInvalidValue;
+  // the opt-in limit covers the kernel's static shared memory too
+  cudaFuncAttributes fa;
+  st = cudaFuncGetAttributes(&fa, kernel);
+  if (st != cudaSuccess) return st;
+  const int dyn_cap = cap - (int)fa.sharedSizeBytes;
+  if (bytes > (size_t)dyn_cap) return cudaErrorInvalidValue;
   std::lock_guard<std::mutex> lock(mu);
   for (const auto& kd : done)
     if (kd.first == kernel && kd.second == dev) return cudaSuccess;
-  st = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  st = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_cap);
   if (st == cudaSuccess) done.emplace_back(kernel, dev);
   return st;
 }
@@ -1202,9 +1228,9 @@ __device__ inline void ring_propagators_smem(const Dev& d, const Smem& s) {
 
 template <int LMAX>
 __global__ void __launch_bounds__(HQ_THREADS) logdet_noalloc_kernel(Dev d, double* out) {
-  extern __shared__ double smraw[];
+  extern __shared__ __align__(16) double smraw[];
   const int c = blockIdx.x;
-  const Smem sm = carve(d, smraw);
+  const Smem sm = carve<LMAX>(d, smraw);
   ring_propagators_smem(d, sm);
   const double* X = d.X + (size_t)c * d.L * d.n;
   const double ld = udv_top_down<LMAX>(d, c, sm, X, -1, 0.0, false, nullptr);
