@@ -641,55 +641,62 @@ __device__ inline void qr_form_q(const double* P, int ld, int n, double* U, cons
 }
 
 // D[j] = |R_jj| and Tout = T' Tprev with T'(j, perm[c]) = R(j, c) / D[j] for c >= j
-// (T' = D^-1 R Pi^T).  With Tprev == nullptr, Tout = T'.  Each thread produces four
-// outputs of one row j (four independent FMA chains); lanes of a warp share j or j+1, so
-// trip counts stay nearly uniform.
+// (T' = D^-1 R Pi^T).  With Tprev == nullptr, Tout = T'.  Otherwise Tprev's rows are first
+// gathered into Bs in pivot order (Bs(c, k) = Tprev(perm[c], k); Bs is scratch, e.g. the
+// product that was just factored), so that Tout = D^-1 R Bs: upper triangular times dense, in
+// 4 x 4 register tiles.  A warp takes 8 x 4 tiles (32 rows x 16 columns) and runs its k loop
+// from its first row: R is read only at k >= row (below the diagonal P holds the reflectors).
+// Blocks go to warps round-robin in row-block-major order, which spreads the long (top) and
+// short (bottom) k ranges over the warps.
 __device__ inline void t_update(const double* P, int ld, int n, const QrScratch& s, double* D,
-                         const double* Tprev, double* Tout) {
+                                const double* Tprev, double* Tout, double* Bs) {
   for (int j = threadIdx.x; j < n; j += HQ_THREADS) {
     const double dj = fabs(P[(size_t)j * ld + j]);
     D[j] = dj;
     s.rinv[j] = 1.0 / dj;
   }
-  __syncthreads();
   if (Tprev == nullptr) {
+    __syncthreads();
     for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
       const int j = idx % n, c = idx / n;
       Tout[(size_t)s.perm[c] * ld + j] = (c >= j) ? P[(size_t)c * ld + j] * s.rinv[j] : 0.0;
     }
   } else {
-    const int nq = n >> 2;  // n is a multiple of 4
-    for (int idx = threadIdx.x; idx < n * nq; idx += HQ_THREADS) {
-      const int q = idx % nq, j = idx / nq;
-      const double* t0 = Tprev + (size_t)(4 * q) * ld;
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
-      int c = j;
-      for (; c + 1 < n; c += 2) {  // two partial sums per output halve the dependent chain
-        const double r = P[(size_t)c * ld + j], r2 = P[(size_t)(c + 1) * ld + j];
-        const int pc = s.perm[c], pd = s.perm[c + 1];
-        a0 = fma(r, t0[pc], a0);
-        a1 = fma(r, t0[ld + pc], a1);
-        a2 = fma(r, t0[2 * (size_t)ld + pc], a2);
-        a3 = fma(r, t0[3 * (size_t)ld + pc], a3);
-        b0 = fma(r2, t0[pd], b0);
-        b1 = fma(r2, t0[ld + pd], b1);
-        b2 = fma(r2, t0[2 * (size_t)ld + pd], b2);
-        b3 = fma(r2, t0[3 * (size_t)ld + pd], b3);
+    for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
+      const int c = idx % n, k = idx / n;
+      Bs[(size_t)k * ld + c] = Tprev[(size_t)k * ld + s.perm[c]];
+    }
+    __syncthreads();
+    const int tiles = n >> 2;  // n is a multiple of 4
+    const int nrb = (tiles + 7) >> 3, ncb = (tiles + 3) >> 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rt = lane & 7, ct = lane >> 3;
+    for (int blk = warp; blk < nrb * ncb; blk += HQ_WARPS) {
+      const int R0 = (blk / ncb) * 32;
+      const int r0 = R0 + 4 * rt, c0 = (blk % ncb) * 16 + 4 * ct;
+      if (r0 >= n || c0 >= n) continue;
+      double acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+      for (int k = R0; k < n; ++k) {
+        double av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = (k >= r0 + a) ? P[(size_t)k * ld + r0 + a] : 0.0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = Bs[(size_t)(c0 + b) * ld + k];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
       }
-      if (c < n) {
-        const double r = P[(size_t)c * ld + j];
-        const int pc = s.perm[c];
-        a0 = fma(r, t0[pc], a0);
-        a1 = fma(r, t0[ld + pc], a1);
-        a2 = fma(r, t0[2 * (size_t)ld + pc], a2);
-        a3 = fma(r, t0[3 * (size_t)ld + pc], a3);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const double ri = s.rinv[r0 + a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) Tout[(size_t)(c0 + b) * ld + r0 + a] = acc[a][b] * ri;
       }
-      const double ri = s.rinv[j];
-      double* o = Tout + (size_t)(4 * q) * ld + j;
-      o[0] = (a0 + b0) * ri;
-      o[ld] = (a1 + b1) * ri;
-      o[2 * (size_t)ld] = (a2 + b2) * ri;
-      o[3 * (size_t)ld] = (a3 + b3) * ri;
     }
   }
   __syncthreads();

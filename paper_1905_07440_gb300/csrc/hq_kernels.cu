@@ -198,7 +198,7 @@ __device__ double udv_top_down(const Dev& d, int c, const Smem& sm, const double
     qr_form_q<LMAX>(Q, n, n, U, qs);
     HQ_TOC(fq, SEC_FORMQ);
     HQ_TIC(tu);
-    t_update(Q, n, n, qs, sm.dv, first ? nullptr : Tc, Tn);
+    t_update(Q, n, n, qs, sm.dv, first ? nullptr : Tc, Tn, P);
     HQ_TOC(tu, SEC_TUPD);
     double* t = Tc; Tc = Tn; Tn = t;
     if (store && lo > 0) {
@@ -271,7 +271,7 @@ __device__ void udv_bottom_half(const Dev& d, int c, const Smem& sm, int m) {
     prepivot<qr_group<LMAX>()>(P, Q, n, n, qs, sm.norm2);
     qr_factor<LMAX>(Q, n, n, qs);
     qr_form_q<LMAX>(Q, n, n, UR, qs);
-    t_update(Q, n, n, qs, DR, first ? nullptr : TR, T2);
+    t_update(Q, n, n, qs, DR, first ? nullptr : TR, T2, P);
     copy_mat(TR, T2, n, n);
     __syncthreads();
   }
@@ -593,7 +593,7 @@ __device__ void local_chunk_body(const Dev& d, int c, int s0, int s1, int measur
   prepivot<qr_group<LMAX>()>(P, Q, n, n, qs, sm.norm2);
   qr_factor<LMAX>(Q, n, n, qs);
   qr_form_q<LMAX>(Q, n, n, UR, qs);
-  t_update(Q, n, n, qs, DR, first ? nullptr : TR, T2);
+  t_update(Q, n, n, qs, DR, first ? nullptr : TR, T2, P);
   copy_mat(TR, T2, n, n);
   __syncthreads();
   HQ_TOC(rq, SEC_RESTAB_QR);
@@ -840,7 +840,7 @@ __device__ double udv_top_down_cm(const Dev& d, int c, const Smem& sm, int site,
     qr_form_q<LMAX>(Q, n, n, U, qs);
     HQ_TOC(fq, SEC_FORMQ);
     HQ_TIC(tu);
-    t_update(Q, n, n, qs, sm.dv, first ? nullptr : Tc, Tn);
+    t_update(Q, n, n, qs, sm.dv, first ? nullptr : Tc, Tn, P);
     HQ_TOC(tu, SEC_TUPD);
     double* t = Tc; Tc = Tn; Tn = t;
     first = false;
