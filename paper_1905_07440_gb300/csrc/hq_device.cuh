@@ -469,7 +469,12 @@ __device__ inline void form_q(const double* P, int ld, int n, double* U, const Q
 // R above the diagonal, the unit-lower reflector vectors below it, and tau.  So the T update
 // and every other reader of the QR see the same layout.
 
-__host__ __device__ constexpr bool qr_blocked_class(int lmax) { return lmax > 8; }
+// Smallest lattice class (largest side rounded up to 2, 4, 8, 16) that takes the blocked
+// variants; a build may lower it (-DHQ_QR_BLOCKED_MIN=8) to compare the two forms.
+#ifndef HQ_QR_BLOCKED_MIN
+#define HQ_QR_BLOCKED_MIN 16
+#endif
+__host__ __device__ constexpr bool qr_blocked_class(int lmax) { return lmax >= HQ_QR_BLOCKED_MIN; }
 
 // Panel factorisation of columns j0 .. j1 - 1 (rows j .. n - 1 for column j).  Columns from
 // j1 on are not touched.
@@ -702,94 +707,204 @@ __device__ inline void t_update(const double* P, int ld, int n, const QrScratch&
   __syncthreads();
 }
 
-// ------------------------------------------------------------- LU and triangular solves
-// In-place LU with partial (row) pivoting.  piv[j] = row swapped with j at step j.
-// Returns sum_j log|U_jj| (same value in every thread).
-__device__ inline double lu_logdet(double* A, int ld, int n, int* piv, int* sint, double* red) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int j = 0; j < n; ++j) {
-    double* aj = A + (size_t)j * ld;
-    if (warp == 0) {
-      double best = -1.0;
-      int bi = j;
-      for (int r = j + lane; r < n; r += 32) {
-        const double v = fabs(aj[r]);
-        if (v > best) { best = v; bi = r; }
-      }
-#pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        const double ob = __shfl_xor_sync(HQ_FULL, best, o);
-        const int oi = __shfl_xor_sync(HQ_FULL, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (lane == 0) {
-        sint[0] = bi;
-        piv[j] = bi;
-        red[0] = 1.0 / aj[bi];  // reciprocal of the pivot, once for the CTA
-      }
-    }
-    __syncthreads();
-    const int p = sint[0];
-    if (p != j) {
-      for (int c = tid; c < n; c += HQ_THREADS) {
-        double* ac = A + (size_t)c * ld;
-        const double a = ac[j];
-        ac[j] = ac[p];
-        ac[p] = a;
-      }
-      __syncthreads();
-    }
-    const double rp = red[0];
-    for (int r = j + 1 + tid; r < n; r += HQ_THREADS) aj[r] *= rp;
-    __syncthreads();
-    const int m = n - j - 1;
-    for (int idx = tid; idx < m * m; idx += HQ_THREADS) {
-      const int r = j + 1 + idx % m, c = j + 1 + idx / m;
-      A[(size_t)c * ld + r] = fma(-aj[r], A[(size_t)c * ld + j], A[(size_t)c * ld + r]);
-    }
-    __syncthreads();
-  }
-  __syncthreads();  // red[0] is read above; block_sum reuses red
-  double a = 0.0;
-  for (int j = tid; j < n; j += HQ_THREADS) a += log(fabs(A[(size_t)j * ld + j]));
-  return block_sum(a, red);
-}
-
 // rd[j] = 1 / U_jj of the LU factors (one division per diagonal entry, not per use).
 __device__ __forceinline__ void lu_diag_recip(const double* A, int ld, int n, double* rd) {
   for (int j = threadIdx.x; j < n; j += HQ_THREADS) rd[j] = 1.0 / A[(size_t)j * ld + j];
   __syncthreads();
 }
 
-// Y <- A^-1 Y for the LU factors from lu_logdet (n right-hand sides, one warp per column);
-// rd: the reciprocals of U's diagonal (lu_diag_recip).
-__device__ inline void lu_solve(const double* A, int ld, int n, const int* piv, const double* rd, double* Y) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int c = warp; c < n; c += HQ_WARPS) {
-    double* y = Y + (size_t)c * ld;
-    if (lane == 0) {
-      for (int j = 0; j < n; ++j) {
+// ------------------------------------------------------- blocked LU and triangular solves
+// Right-looking LU with partial pivoting in panels of kLb columns (the LAPACK getrf scheme): a
+// panel is factored column by column (pivot search over the whole column, swaps and updates
+// inside the panel), its row swaps are then applied to the other columns, U12 = L11^-1 A12 is a
+// small triangular solve per column, and the trailing block takes A22 -= L21 U12 as one rank-kLb
+// update in 4 x 4 register tiles.  The column-by-column form swept the whole trailing matrix
+// once per column with three loads per multiply-add.  Layout: L unit lower, U upper, piv[j]
+// the row swapped with j at step j.
+constexpr int kLb = 16;
+
+// C(r0:r1, c0:c1) -= A(r0:r1, k0:k0+kb) B(k0:k0+kb, c0:c1), all column-major with stride ld;
+// r1 - r0 and c1 - c0 multiples of 4, kb <= kLb.  The read and written regions must not overlap.
+// No barrier at the end.
+__device__ inline void rank_update(double* C, const double* A, const double* B, int ld, int r0, int r1, int c0, int c1,
+                                   int k0, int kb) {
+  const int tr = (r1 - r0) >> 2, tc = (c1 - c0) >> 2;
+  for (int t = threadIdx.x; t < tr * tc; t += HQ_THREADS) {
+    const int r = r0 + (t % tr) * 4, c = c0 + (t / tr) * 4;
+    double acc[4][4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) acc[a][b] = C[(size_t)(c + b) * ld + r + a];
+    for (int k = k0; k < k0 + kb; ++k) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = A[(size_t)k * ld + r + a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = B[(size_t)(c + b) * ld + k];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(-av[a], bv[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) C[(size_t)(c + b) * ld + r + a] = acc[a][b];
+  }
+}
+
+// In-place blocked LU with partial pivoting; returns sum_j log|U_jj| (same value in every thread).
+__device__ inline double lu_logdet_blocked(double* A, int ld, int n, int* piv, int* sint, double* red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int p0 = 0; p0 < n; p0 += kLb) {
+    const int p1 = p0 + kLb < n ? p0 + kLb : n, kb = p1 - p0;
+    // panel: columns p0 .. p1 - 1
+    for (int j = p0; j < p1; ++j) {
+      double* aj = A + (size_t)j * ld;
+      if (warp == 0) {
+        double best = -1.0;
+        int bi = j;
+        for (int r = j + lane; r < n; r += 32) {
+          const double v = fabs(aj[r]);
+          if (v > best) { best = v; bi = r; }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          const double ob = __shfl_xor_sync(HQ_FULL, best, o);
+          const int oi = __shfl_xor_sync(HQ_FULL, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) {
+          sint[0] = bi;
+          piv[j] = bi;
+          red[0] = 1.0 / aj[bi];
+        }
+      }
+      __syncthreads();
+      const int p = sint[0];
+      if (p != j) {
+        if (tid < kb) {
+          double* ac = A + (size_t)(p0 + tid) * ld;
+          const double a = ac[j];
+          ac[j] = ac[p];
+          ac[p] = a;
+        }
+        __syncthreads();
+      }
+      const double rp = red[0];
+      for (int r = j + 1 + tid; r < n; r += HQ_THREADS) aj[r] *= rp;
+      __syncthreads();
+      const int m = n - j - 1, w = p1 - j - 1;
+      for (int idx = tid; idx < m * w; idx += HQ_THREADS) {
+        const int r = j + 1 + idx % m, c = j + 1 + idx / m;
+        A[(size_t)c * ld + r] = fma(-aj[r], A[(size_t)c * ld + j], A[(size_t)c * ld + r]);
+      }
+      __syncthreads();
+    }
+    // the panel's swaps on the other columns, then U12 = L11^-1 A12 (one column per thread)
+    for (int c = tid; c < n; c += HQ_THREADS) {
+      if (c >= p0 && c < p1) continue;
+      double* ac = A + (size_t)c * ld;
+      for (int j = p0; j < p1; ++j) {
         const int p = piv[j];
-        if (p != j) { const double a = y[j]; y[j] = y[p]; y[p] = a; }
+        if (p != j) { const double a = ac[j]; ac[j] = ac[p]; ac[p] = a; }
+      }
+      if (c >= p1) {
+        double x[kLb];
+#pragma unroll
+        for (int i = 0; i < kLb; ++i) x[i] = i < kb ? ac[p0 + i] : 0.0;
+#pragma unroll
+        for (int i = 0; i < kLb; ++i) {
+          if (i < kb) {
+            const double* li = A + (size_t)(p0 + i) * ld + p0;
+#pragma unroll
+            for (int r = i + 1; r < kLb; ++r)
+              if (r < kb) x[r] = fma(-li[r], x[i], x[r]);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < kLb; ++i)
+          if (i < kb) ac[p0 + i] = x[i];
       }
     }
-    __syncwarp();
-    for (int j = 0; j < n; ++j) {
-      const double yj = y[j];
-      const double* lj = A + (size_t)j * ld;
-      for (int r = j + 1 + lane; r < n; r += 32) y[r] = fma(-lj[r], yj, y[r]);
-      __syncwarp();
+    __syncthreads();
+    if (p1 < n) {
+      rank_update(A, A, A, ld, p1, n, p1, n, p0, kb);
+      __syncthreads();
     }
-    for (int j = n - 1; j >= 0; --j) {
-      const double* uj = A + (size_t)j * ld;
-      const double yj = y[j] * rd[j];
-      __syncwarp();
-      if (lane == 0) y[j] = yj;
-      for (int r = lane; r < j; r += 32) y[r] = fma(-uj[r], yj, y[r]);
-      __syncwarp();
+  }
+  double a = 0.0;
+  for (int j = tid; j < n; j += HQ_THREADS) a += log(fabs(A[(size_t)j * ld + j]));
+  return block_sum(a, red);
+}
+
+// Y <- A^-1 Y (n right-hand sides) for the factors of lu_logdet_blocked; rd: reciprocals of U's
+// diagonal (lu_diag_recip).  The row swaps, then L and U by blocks of kLb rows: a kLb x kLb
+// triangular solve per column (one column per thread, in registers) and a rank-kLb update of
+// the rows still to solve.
+__device__ inline void lu_solve_blocked(const double* A, int ld, int n, const int* piv, const double* rd, double* Y) {
+  const int tid = threadIdx.x;
+  for (int c = tid; c < n; c += HQ_THREADS) {
+    double* y = Y + (size_t)c * ld;
+    for (int j = 0; j < n; ++j) {
+      const int p = piv[j];
+      if (p != j) { const double a = y[j]; y[j] = y[p]; y[p] = a; }
     }
   }
   __syncthreads();
+  for (int p0 = 0; p0 < n; p0 += kLb) {
+    const int p1 = p0 + kLb < n ? p0 + kLb : n, kb = p1 - p0;
+    for (int c = tid; c < n; c += HQ_THREADS) {
+      double* y = Y + (size_t)c * ld + p0;
+      double x[kLb];
+#pragma unroll
+      for (int i = 0; i < kLb; ++i) x[i] = i < kb ? y[i] : 0.0;
+#pragma unroll
+      for (int i = 0; i < kLb; ++i) {
+        if (i < kb) {
+          const double* li = A + (size_t)(p0 + i) * ld + p0;
+#pragma unroll
+          for (int r = i + 1; r < kLb; ++r)
+            if (r < kb) x[r] = fma(-li[r], x[i], x[r]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < kLb; ++i)
+        if (i < kb) y[i] = x[i];
+    }
+    __syncthreads();
+    if (p1 < n) {
+      rank_update(Y, A, Y, ld, p1, n, 0, n, p0, kb);
+      __syncthreads();
+    }
+  }
+  for (int p0 = ((n - 1) / kLb) * kLb; p0 >= 0; p0 -= kLb) {
+    const int p1 = p0 + kLb < n ? p0 + kLb : n, kb = p1 - p0;
+    for (int c = tid; c < n; c += HQ_THREADS) {
+      double* y = Y + (size_t)c * ld + p0;
+      double x[kLb];
+#pragma unroll
+      for (int i = 0; i < kLb; ++i) x[i] = i < kb ? y[i] : 0.0;
+#pragma unroll
+      for (int i = kLb - 1; i >= 0; --i) {
+        if (i < kb) {
+          x[i] *= rd[p0 + i];
+          const double* ui = A + (size_t)(p0 + i) * ld + p0;
+#pragma unroll
+          for (int r = 0; r < i; ++r) x[r] = fma(-ui[r], x[i], x[r]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < kLb; ++i)
+        if (i < kb) y[i] = x[i];
+    }
+    __syncthreads();
+    if (p0 > 0) {
+      rank_update(Y, A, Y, ld, 0, p0, 0, n, p0, kb);
+      __syncthreads();
+    }
+  }
 }
 
 // ---------------------------------------------------------------------- CTA GEMM

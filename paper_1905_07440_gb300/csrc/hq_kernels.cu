@@ -138,10 +138,10 @@ __device__ double finish_logdet(const Dev& d, int c, const Smem& sm, const doubl
   double lsum = 0.0;
   for (int i = threadIdx.x; i < n; i += HQ_THREADS) lsum += log(fmax(sm.dv[i], 1.0));
   const double lb = block_sum(lsum, sm.red);
-  const double la = lu_logdet(A, n, n, sm.piv, sm.sint, sm.red);
+  const double la = lu_logdet_blocked(A, n, n, sm.piv, sm.sint, sm.red);
   if (G0) {
     lu_diag_recip(A, n, n, sm.rd);
-    lu_solve(A, n, n, sm.piv, sm.rd, Y);
+    lu_solve_blocked(A, n, n, sm.piv, sm.rd, Y);
     for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
       const int r = idx % n, col = idx / n;
       G0[(size_t)col * n + r] = Y[(size_t)r * n + col];
@@ -344,9 +344,9 @@ __device__ double green_two_sided(const Dev& d, int c, const Smem& sm, int l, do
     }
     for (int i = threadIdx.x; i < n; i += HQ_THREADS) lsum += log(fmax(DR[i], 1.0)) + log(fmax(DL[i], 1.0));
     __syncthreads();
-    la = lu_logdet(M2, n, n, sm.piv, sm.sint, sm.red);
+    la = lu_logdet_blocked(M2, n, n, sm.piv, sm.sint, sm.red);
     lu_diag_recip(M2, n, n, sm.rd);
-    lu_solve(M2, n, n, sm.piv, sm.rd, M3);
+    lu_solve_blocked(M2, n, n, sm.piv, sm.rd, M3);
     // M1 <- UL DLb^-1, Gf = M1 M3
     for (int idx = threadIdx.x; idx < n * n; idx += HQ_THREADS) {
       const int j = idx / n;
@@ -367,9 +367,9 @@ __device__ double green_two_sided(const Dev& d, int c, const Smem& sm, int l, do
     }
     for (int i = threadIdx.x; i < n; i += HQ_THREADS) lsum += log(fmax(DR[i], 1.0));
     __syncthreads();
-    la = lu_logdet(M2, n, n, sm.piv, sm.sint, sm.red);
+    la = lu_logdet_blocked(M2, n, n, sm.piv, sm.sint, sm.red);
     lu_diag_recip(M2, n, n, sm.rd);
-    lu_solve(M2, n, n, sm.piv, sm.rd, Gf);
+    lu_solve_blocked(M2, n, n, sm.piv, sm.rd, Gf);
   }
   return block_sum(lsum, sm.red) + la;
 }
