@@ -119,7 +119,8 @@ int hq_create(const hq_params* p, int n_chains, int first_chain, int max_series,
               void* device_arena, size_t arena_bytes, void* stream, hq_engine** out);
 
 /* Copy fields in from the host, X_host[chain][l][i] (n_chains*L*N doubles); G, the UDV
- * stack and log|det M| are recomputed before the next use.  Resets no counters. */
+ * stack and log|det M| are recomputed before the next use.  Resets no counters.
+ * Paper, "Model": the phonon field X_{i,l} on the space-time lattice. */
 int hq_set_fields(hq_engine* e, const double* X_host);
 /* Same from a device buffer of the same layout (copied on the engine's stream). */
 int hq_set_fields_device(hq_engine* e, const double* X_device);
@@ -127,19 +128,24 @@ int hq_set_fields_device(hq_engine* e, const double* X_device);
 int hq_get_fields(hq_engine* e, double* X_host);
 
 /* Run n_sweeps sweeps of every chain.  flags: HQ_LOCAL | HQ_GLOBAL | HQ_MEASURE.
- * Asynchronous on the engine's stream; returns HQ_EINVAL for bad flags, HQ_ENOMEM if
+ * Paper, "Method" (DQMC): local Metropolis moves of X_{i,l} with the determinant ratio and
+ * the fast update of G, wraps and periodic restabilisation, then one block move per site
+ * accepted on the full determinant ratio.  Asynchronous on the engine's stream; returns HQ_EINVAL for bad flags, HQ_ENOMEM if
  * more than max_series measured sweeps would be recorded. */
 int hq_sweep(hq_engine* e, int n_sweeps, unsigned flags);
 
 /* log W = 2 log|det M| - dtau S_ph and log|det M| of the current fields, one per chain
- * (host arrays of n_chains doubles; either may be NULL).  Synchronises. */
+ * (host arrays of n_chains doubles; either may be NULL).  Synchronises.
+ * Paper, "Method": the weight e^{-dtau S_ph} (det M)^2 of a configuration. */
 int hq_log_weight(hq_engine* e, double* logw_host, double* logdet_host);
 
 /* G_0 = G_L of one chain for the current fields, row-major G[i*N+j] = G_ij = <c_i c_j^+>
- * (host, N*N doubles); *slice = 0.  Synchronises. */
+ * (host, N*N doubles); *slice = 0.  Synchronises.  Paper, "Method": the equal-time
+ * Green's function (I + B_L ... B_1)^-1. */
 int hq_get_green(hq_engine* e, int chain, double* G_host, int* slice);
 
-/* Per-chain accumulated observables (host array of n_chains hq_obs).  Synchronises. */
+/* Per-chain accumulated observables (host array of n_chains hq_obs).  Synchronises.
+ * Paper, "Results": <X^2>, double occupancy and the charge structure factor S_CDW(pi, pi). */
 int hq_get_observables(hq_engine* e, hq_obs* out);
 
 /* Per-sweep series of one observable: out[chain][s] for s < *n_out (host, n_chains *
@@ -331,9 +337,11 @@ int hq_nn_attach(hq_engine* e, void* device_arena, size_t bytes, int max_batch, 
 int hq_nn_set_params(hq_engine* e, const float* theta_host);
 /* FP32 master parameters, or with bf16 != 0 the bfloat16 values the kernels use. */
 int hq_nn_get_params(hq_engine* e, float* theta_host, int bf16);
-/* F(X) of every chain's current fields (host, n_chains doubles).  Synchronises. */
+/* F(X) of every chain's current fields (host, n_chains doubles).  Synchronises.  Paper,
+ * "Local Updates": the network's effective action on local space-time patches of X. */
 int hq_nn_eval(hq_engine* e, double* F_host);
-/* Adam training (lr, beta1 0.9, beta2 0.999) of F towards targets y on samples X:
+/* Paper, "Training": fit of the network to (X, exact log-weight) pairs from the plain sampler.
+ * Adam training (lr, beta1 0.9, beta2 0.999) of F towards targets y on samples X:
  * X_device [n_samples][L][N] doubles and y_device [n_samples] doubles, device pointers of the
  * engine's lattice; loss (1/B) sum (F(X_a) - y_a)^2 per minibatch of `batch` samples; epoch
  * order from `seed`.  loss_host (optional): mean loss of each epoch.  Synchronises. */
@@ -343,7 +351,9 @@ int hq_nn_train(hq_engine* e, const double* X_device, const double* y_device, in
  * grad_host HQ_NN_PARAMS floats, loss_host one double.  Synchronises. */
 int hq_nn_gradient(hq_engine* e, const double* X_device, const double* y_device, int n_samples, float* grad_host,
                    double* loss_host);
-/* n_steps cumulative steps of every chain: n_inner network-driven sweeps (flags HQ_LOCAL:
+/* Paper, "Benchmarks": the cumulative update, accepted with p_c = [W(X')/W(X)] times the
+ * ratio of the network weights, so the chain samples the exact weight.
+ * n_steps cumulative steps of every chain: n_inner network-driven sweeps (flags HQ_LOCAL:
  * a local move at every (l, i); HQ_GLOBAL: a block move at every site, with HQ_CNN_BLOCK on
  * F_cnn), then the exact accept of the cumulative move; HQ_MEASURE also records electronic
  * observables of G_0 after each step (G_0 of the starting fields is kept, so a rejected chain
@@ -398,7 +408,8 @@ int hq_cnn_set_params(hq_engine* e, const float* theta_host);
 /* FP32 master parameters, or with bf16 != 0 the bfloat16 values the kernels use. */
 int hq_cnn_get_params(hq_engine* e, float* theta_host, int bf16);
 /* F_cnn of every chain's current fields (host, n_chains doubles); refreshes the cached
- * activations.  Synchronises. */
+ * activations.  Synchronises.  Paper, "Global Updates": the convolutional network on the
+ * (x, y, tau) field that drives block moves. */
 int hq_cnn_eval(hq_engine* e, double* F_host);
 /* Training and gradient of F_cnn, with the arguments and semantics of hq_nn_train and
  * hq_nn_gradient (targets y, minibatch loss (1/B) sum (F_cnn(X_a) - y_a)^2, Adam). */
