@@ -128,24 +128,24 @@ int hq_set_fields_device(hq_engine* e, const double* X_device);
 int hq_get_fields(hq_engine* e, double* X_host);
 
 /* Run n_sweeps sweeps of every chain.  flags: HQ_LOCAL | HQ_GLOBAL | HQ_MEASURE.
- * Paper, "Method" (DQMC): local Metropolis moves of X_{i,l} with the determinant ratio and
- * the fast update of G, wraps and periodic restabilisation, then one block move per site
- * accepted on the full determinant ratio.  Asynchronous on the engine's stream; returns HQ_EINVAL for bad flags, HQ_ENOMEM if
+ * Paper, "Determinant quantum Monte Carlo": local Metropolis moves of X_{i,l} with the
+ * determinant ratio and the fast update of G, wraps and periodic restabilisation, then one
+ * block move per site accepted on the full determinant ratio.  Asynchronous on the engine's stream; returns HQ_EINVAL for bad flags, HQ_ENOMEM if
  * more than max_series measured sweeps would be recorded. */
 int hq_sweep(hq_engine* e, int n_sweeps, unsigned flags);
 
 /* log W = 2 log|det M| - dtau S_ph and log|det M| of the current fields, one per chain
  * (host arrays of n_chains doubles; either may be NULL).  Synchronises.
- * Paper, "Method": the weight e^{-dtau S_ph} (det M)^2 of a configuration. */
+ * Paper, "Determinant quantum Monte Carlo": the weight e^{-dtau S_ph} (det M)^2. */
 int hq_log_weight(hq_engine* e, double* logw_host, double* logdet_host);
 
 /* G_0 = G_L of one chain for the current fields, row-major G[i*N+j] = G_ij = <c_i c_j^+>
- * (host, N*N doubles); *slice = 0.  Synchronises.  Paper, "Method": the equal-time
- * Green's function (I + B_L ... B_1)^-1. */
+ * (host, N*N doubles); *slice = 0.  Synchronises.  Paper, "Determinant quantum Monte
+ * Carlo": the equal-time Green's function (I + B_L ... B_1)^-1. */
 int hq_get_green(hq_engine* e, int chain, double* G_host, int* slice);
 
 /* Per-chain accumulated observables (host array of n_chains hq_obs).  Synchronises.
- * Paper, "Results": <X^2>, double occupancy and the charge structure factor S_CDW(pi, pi). */
+ * Paper, "Benchmarks": <X^2>, double occupancy and the CDW structure factor S(pi, pi). */
 int hq_get_observables(hq_engine* e, hq_obs* out);
 
 /* Per-sweep series of one observable: out[chain][s] for s < *n_out (host, n_chains *
@@ -340,7 +340,8 @@ int hq_nn_get_params(hq_engine* e, float* theta_host, int bf16);
 /* F(X) of every chain's current fields (host, n_chains doubles).  Synchronises.  Paper,
  * "Local Updates": the network's effective action on local space-time patches of X. */
 int hq_nn_eval(hq_engine* e, double* F_host);
-/* Paper, "Training": fit of the network to (X, exact log-weight) pairs from the plain sampler.
+/* Paper, "Global Updates" (training of both networks): fit to (X, exact log-weight) pairs
+ * from the plain sampler.
  * Adam training (lr, beta1 0.9, beta2 0.999) of F towards targets y on samples X:
  * X_device [n_samples][L][N] doubles and y_device [n_samples] doubles, device pointers of the
  * engine's lattice; loss (1/B) sum (F(X_a) - y_a)^2 per minibatch of `batch` samples; epoch
