@@ -1456,8 +1456,9 @@ def run_largest_learned(args):
 
 
 def run_training(args):
-    """Training protocol of the learned-proposal workload (paper, Global Updates, on the training of both networks: tens of thousands of
-    configurations of the conventional sampler with a train/test split).  Per temperature
+    """Training protocol of the learned-proposal workload (paper, Global Updates, on training
+    both networks: tens of thousands of configurations of the conventional sampler with a
+    train/test split).  Per temperature
     (beta = 8 and 16, 8x8, the headline couplings): 256 plain chains from the ordered start,
     args.train_warmup sweeps, then one snapshot (fields, exact log|det M|) per sweep; chains
     0..191 give the training set, 192..255 the held-out test set (75/25 by chain, so no test
